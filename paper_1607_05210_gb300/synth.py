@@ -1,0 +1,186 @@
+"""Seeded synthetic inputs and tree builders (no POD arithmetic lives here).
+
+Both the CUDA path and the CPU oracle consume what these functions return; this
+module contains neither Gram, eigen-, truncation nor mode arithmetic.  The inputs
+stand in for the paper's PDE snapshot data (Sec. 4), which is not available:
+
+* ``prescribed_spectrum``: X = Q diag(s) W^T + noise * N(0, 1), Q and W with
+  orthonormal columns drawn from the seed (QR of Gaussian matrices).
+* ``star_prescribed``: the 10,000-row, 8 x 100-column, sigma_j = 10^(-j/20)
+  two-level workload (shared Q, W of 200 columns, noise 1e-10).
+* ``advection_diffusion``: u(x, t) = sum_{k=1..32} a_k exp(-nu k^2 t) sin(k (x - c t))
+  on the periodic grid x_i = 2 pi i / n, a_k ~ N(0, k^-2), t_j ~ U[0, 1], nu = 1e-3,
+  c = 1.  Expanded as X = B C with B = [sin(k x), cos(k x)] (n x 64) so that large
+  matrices are produced by one matrix product on the device.
+* tree builders returning parent arrays (root has parent -1).
+"""
+from __future__ import annotations
+
+import math
+from typing import Dict, List, Optional, Tuple
+
+import numpy as np
+
+
+# ------------------------------------------------------------------ trees
+def star_tree(num_leaves: int) -> List[int]:
+    """Root 0 with leaves 1..num_leaves (distributed HAPOD, Sec. 3.2)."""
+    return [-1] + [0] * num_leaves
+
+
+def balanced_tree(arity: int, edge_depth: int, num_leaves: Optional[int] = None) -> List[int]:
+    """Balanced ``arity``-ary tree with ``arity**edge_depth`` leaf slots, the first
+    ``num_leaves`` of them used (index order); inner nodes with no leaf below are
+    removed.  Node 0 is the root; leaves are the last nodes."""
+    slots = arity ** edge_depth
+    if num_leaves is None:
+        num_leaves = slots
+    # build level by level from the root
+    levels: List[List[int]] = [[0]]
+    parent = [-1]
+    for d in range(edge_depth):
+        nxt = []
+        for p in levels[-1]:
+            for _ in range(arity):
+                parent.append(p)
+                nxt.append(len(parent) - 1)
+        levels.append(nxt)
+    leaves = levels[-1]
+    used = set(leaves[:num_leaves])
+    keep = [False] * len(parent)
+    for a in used:
+        b = a
+        while b >= 0 and not keep[b]:
+            keep[b] = True
+            b = parent[b]
+    remap = {}
+    for a in range(len(parent)):
+        if keep[a]:
+            remap[a] = len(remap)
+    return [(-1 if parent[a] < 0 else remap[parent[a]]) for a in range(len(parent)) if keep[a]]
+
+
+def chain_of_subtrees(num_subtrees: int, subtree_edge_depth: int) -> List[int]:
+    """Left-deep incremental chain (Sec. 3.2, skinny tree) whose inputs are roots of
+    balanced binary subtrees: alpha_1 = subtree_1 root, alpha_l = POD(alpha_{l-1} U
+    subtree_l root).  Node 0 is the final chain node."""
+    parent: List[int] = []
+
+    def add(p):
+        parent.append(p)
+        return len(parent) - 1
+
+    def subtree(p, depth):
+        r = add(p)
+        if depth > 0:
+            subtree(r, depth - 1)
+            subtree(r, depth - 1)
+        return r
+
+    if num_subtrees == 1:
+        subtree(-1, subtree_edge_depth)
+        return parent
+    top = add(-1)
+    cur = top
+    for l in range(num_subtrees - 1, 0, -1):
+        # cur = chain node alpha_{l+1}; children: alpha_l (or subtree_1 root) and subtree_{l+1}
+        subtree(cur, subtree_edge_depth)
+        if l == 1:
+            subtree(cur, subtree_edge_depth)
+        else:
+            cur = add(cur)
+    return parent
+
+
+def leaves_of(parent: List[int]) -> List[int]:
+    has_child = [False] * len(parent)
+    for p in parent:
+        if p >= 0:
+            has_child[p] = True
+    return [a for a in range(len(parent)) if not has_child[a]]
+
+
+# ------------------------------------------------------- prescribed spectrum
+def orthonormal(rng: np.random.Generator, n: int, k: int) -> np.ndarray:
+    """n x k matrix with orthonormal columns (QR of a Gaussian matrix)."""
+    q, r = np.linalg.qr(rng.standard_normal((n, k)))
+    return q * np.sign(np.diag(r))
+
+
+def prescribed_spectrum(n: int, m: int, sigma, seed: int, noise: float = 0.0,
+                        dtype=np.float64) -> np.ndarray:
+    """X = Q diag(sigma) W^T + noise * N(0,1), Q: n x r, W: m x r, r = len(sigma)."""
+    rng = np.random.default_rng(seed)
+    sigma = np.asarray(sigma, dtype=np.float64)
+    r = sigma.size
+    Q = orthonormal(rng, n, r)
+    W = orthonormal(rng, m, r)
+    X = (Q * sigma) @ W.T
+    if noise:
+        X = X + noise * rng.standard_normal((n, m))
+    return np.asfortranarray(X.astype(dtype))
+
+
+def star_prescribed(seed: int = 1607, n: int = 10_000, leaves: int = 8, cols: int = 100,
+                    rank: int = 200, noise: float = 1e-10) -> Tuple[List[int], Dict[int, np.ndarray], np.ndarray]:
+    """Two-level FP64 workload: n rows, ``leaves`` x ``cols`` snapshots,
+    sigma_j = 10^(-j/20), j < rank, shared Q (n x rank) and W (leaves*cols x rank)."""
+    sig = 10.0 ** (-np.arange(rank) / 20.0)
+    X = prescribed_spectrum(n, leaves * cols, sig, seed, noise)
+    parent = star_tree(leaves)
+    data = {1 + i: np.asfortranarray(X[:, i * cols:(i + 1) * cols]) for i in range(leaves)}
+    return parent, data, X
+
+
+# --------------------------------------------------- advection-diffusion snapshots
+NUM_HARMONICS = 32
+
+
+def advection_diffusion_coeffs(num_cols: int, seed: int, nu: float = 1e-3, c: float = 1.0) -> np.ndarray:
+    """Coefficient matrix C (64 x num_cols): column j holds the coefficients of
+    sin(k x) (rows 0..31) and cos(k x) (rows 32..63) of u(., t_j), from
+    sin(k(x - c t)) = sin(kx) cos(kct) - cos(kx) sin(kct).  One trajectory: the a_k
+    are drawn once per seed, the t_j uniformly on [0, 1]."""
+    rng = np.random.default_rng(seed)
+    k = np.arange(1, NUM_HARMONICS + 1, dtype=np.float64)
+    a = rng.standard_normal(NUM_HARMONICS) / k
+    t = rng.uniform(0.0, 1.0, num_cols)
+    damp = a[:, None] * np.exp(-nu * (k[:, None] ** 2) * t[None, :])
+    C = np.empty((2 * NUM_HARMONICS, num_cols))
+    C[:NUM_HARMONICS] = damp * np.cos(k[:, None] * c * t[None, :])
+    C[NUM_HARMONICS:] = -damp * np.sin(k[:, None] * c * t[None, :])
+    return C
+
+
+def fourier_basis(n: int) -> np.ndarray:
+    """B (n x 64) = [sin(k x_i), cos(k x_i)], x_i = 2 pi i / n, argument reduced
+    exactly as 2 pi ((k i) mod n) / n."""
+    i = np.arange(n, dtype=np.int64)
+    k = np.arange(1, NUM_HARMONICS + 1, dtype=np.int64)
+    ang = 2.0 * math.pi * ((i[:, None] * k[None, :]) % n) / n
+    return np.concatenate([np.sin(ang), np.cos(ang)], axis=1)
+
+
+def advection_diffusion(n: int, num_cols: int, seed: int, dtype=np.float64) -> np.ndarray:
+    """Host version: X = B C (n x num_cols), column-major."""
+    X = fourier_basis(n) @ advection_diffusion_coeffs(num_cols, seed)
+    return np.asfortranarray(X.astype(dtype))
+
+
+def advection_diffusion_device(n: int, num_cols: int, seed: int, dtype, device, col_offset: int = 0,
+                               total_cols: Optional[int] = None, out=None):
+    """Device version (torch): columns [col_offset, col_offset + num_cols) of the
+    ``total_cols``-column trajectory, as a column-major n x num_cols tensor view
+    (storage num_cols x n).  The product B C is formed in FP64 and rounded once."""
+    import torch
+
+    total = total_cols if total_cols is not None else num_cols
+    C = advection_diffusion_coeffs(total, seed)[:, col_offset:col_offset + num_cols]
+    B = torch.from_numpy(fourier_basis(n)).to(device)
+    Ct = torch.from_numpy(np.ascontiguousarray(C.T)).to(device)  # num_cols x 64
+    Xt = Ct @ B.T  # num_cols x n, row j = column j of X
+    Xt = Xt.to(dtype)
+    if out is not None:
+        out.copy_(Xt)
+        return out
+    return Xt
