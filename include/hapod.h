@@ -1,0 +1,222 @@
+/*
+ * hapod.h -- C ABI of the GB300 (sm_103a) Hierarchical Approximate POD library.
+ *
+ * Method: Himpe, Leibner, Rave, "Hierarchical Approximate Proper Orthogonal
+ * Decomposition" (arXiv 1607.05210).  At every node a of a rooted tree the
+ * library computes the truncated POD of the node's input by the method of
+ * snapshots -- Gram X^T X, symmetric eigensolve, truncation to the node's
+ * tolerance, modes X V -- and passes the singular-value-scaled modes to the
+ * parent, level by level up to the root.
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are column-major with a leading dimension (ld >= rows).  A
+ *     snapshot matrix X of a node is n x m: one column per snapshot vector.
+ *   - "device" pointers are CUDA global-memory addresses of the current device;
+ *     "host" pointers are ordinary CPU memory.  The library never takes
+ *     ownership of caller memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Work is enqueued on it; calls that return results on the host synchronise
+ *     that stream.
+ *   - Errors are returned, never thrown, and nothing aborts the process.
+ *     hapod_last_error() gives a one-line description.  After an HAPOD_ERR_*
+ *     from a context call, the context accepts only hapod_node_stats,
+ *     hapod_last_error and hapod_destroy.  HAPOD_WARN_* codes are not errors:
+ *     the results are produced and the warning is recorded.
+ *   - FP64 form: snapshots are IEEE double; all arithmetic is FP64.
+ *     Mixed form: snapshots are IEEE float; Gram and X V run on the tensor cores
+ *     as split-bf16 products (x = hi + lo, hi*hi + hi*lo + lo*hi) accumulated in
+ *     FP32 over short row chunks and summed in FP64; eigensolve, tail sums and
+ *     truncation in FP64 arithmetic on FP64 data except where stated.
+ */
+#ifndef HAPOD_H
+#define HAPOD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HAPOD_OK = 0,
+  HAPOD_ERR_INVALID = 1,      /* bad argument (null pointer, size, ld, precision) */
+  HAPOD_ERR_TREE = 2,         /* not a rooted tree (Sec. 3.1, Def. Rooted Tree) */
+  HAPOD_ERR_STATE = 3,        /* call out of order (push to a non-leaf, twice, ...) */
+  HAPOD_ERR_CUDA = 4,         /* a CUDA runtime call failed */
+  HAPOD_ERR_OOM = 5,          /* device allocation failed */
+  HAPOD_ERR_NONFINITE = 6,    /* NaN/Inf in a node's Gram matrix */
+  HAPOD_ERR_TIMEOUT = 7,      /* a bounded device-side wait ran out */
+  HAPOD_WARN_NOCONVERGE = 8,  /* Jacobi reached its sweep limit */
+  HAPOD_WARN_BELOW_FLOOR = 9  /* a kept sigma lies below the form's resolution floor */
+} hapod_status;
+
+typedef enum {
+  HAPOD_FP64 = 0,           /* double snapshots, FP64 everywhere */
+  HAPOD_MIXED_BF16X3 = 1    /* float snapshots, tensor-core split-bf16 Gram and X V */
+} hapod_precision;
+
+/*
+ * Rooted tree (Sec. 3.1, Def. Rooted Tree): node a's parent is parent[a], the
+ * root has parent -1.  Every node is a child of at most one node (Eq.
+ * treeonlyoneparent) and reaches the root (Eq. treeconnected); hapod_create
+ * checks both.  Leaves are the nodes without children; leaf_cols[a] is
+ * |D^-1(a)|, the number of snapshots assigned to leaf a (ignored for inner
+ * nodes).  Both arrays are host memory, read during hapod_create only.
+ */
+typedef struct {
+  int32_t num_nodes;
+  const int32_t* parent;
+  const int64_t* leaf_cols;
+} hapod_tree;
+
+/*
+ * Tolerances (Sec. 3.3, Thm. cor:hapod_bound).  `eps` is the global l2 target:
+ * the result satisfies sum_s ||s - P s||^2 <= eps^2 over all |S| snapshots, i.e.
+ * eps* = eps / sqrt(|S|).  Local tolerances: eps(root) = sqrt(|S|) omega eps*,
+ * eps(a) = sqrt(|S~_a|) (L_T - 1)^(-1/2) sqrt(1 - omega^2) eps* otherwise, where
+ * |S~_a| counts the snapshots below a and L_T is the depth (leaves have level 1).
+ * A single-node tree (L_T = 1) gives its root the whole budget eps.
+ * eps_override (host, num_nodes entries, or NULL) replaces eps(a) where it is not
+ * NaN; 0 makes a pass-through node (Def. truncated POD: POD(S, 0) returns the
+ * snapshots with sigma = 1).
+ * max_pending_leaves: 0 = process the tree once every leaf has been pushed (or at
+ * hapod_result); k > 0 = process as soon as k pushed leaves are waiting, which
+ * bounds the device memory held by the library for streamed input (Sec. 3.4).
+ */
+typedef struct {
+  double eps;
+  double omega;
+  const double* eps_override;
+  int32_t precision;
+  int32_t max_pending_leaves;
+} hapod_tol;
+
+typedef struct hapod_ctx hapod_ctx;
+
+/* Per-node record filled by hapod_node_stats. */
+typedef struct {
+  int64_t m;        /* input columns |S_a| (0 until the node has run) */
+  int64_t k;        /* kept modes |HAPOD(a)| (-1 until the node has run) */
+  double eps;       /* local tolerance eps(a) */
+  double tail_sq;   /* discarded sum of sigma^2 (the local POD error, Eq. pod_error) */
+  int32_t level;    /* L_T(a) */
+  int32_t sweeps;   /* Jacobi sweeps used (0 for pass-through) */
+  int32_t state;    /* 0 waiting, 1 ready, 2 done */
+  int32_t status;   /* hapod_status of this node (warnings included) */
+} hapod_node_info;
+
+/*
+ * hapod_create -- validate the tree, compute levels, |S~_a| and eps(a)
+ * (Thm. cor:hapod_bound) and return a context bound to `stream` and the current
+ * device.  n_rows is the snapshot length n (dim V).  No device compute.
+ * Errors: INVALID (null pointers, n_rows < 1, eps < 0, omega outside [0, 1],
+ * unknown precision), TREE, CUDA, OOM.  *out is NULL on error.
+ */
+hapod_status hapod_create(const hapod_tree* tree, const hapod_tol* tol, int64_t n_rows, void* stream,
+                          hapod_ctx** out);
+
+/*
+ * hapod_push -- hand leaf `leaf` its snapshots: device matrix n x ncols, leading
+ * dimension ld (elements), double for HAPOD_FP64, float for the mixed form.
+ * ncols must equal leaf_cols[leaf].  The caller keeps ownership; the library reads
+ * the matrix asynchronously on the context's stream, so it must stay valid and
+ * unchanged until that stream has passed the leaf's processing -- guaranteed once
+ * hapod_result has returned, or after the push that triggered processing
+ * (max_pending_leaves) when the caller synchronises the stream.  May launch work
+ * (Def. HAPOD: a node runs once all of its inputs exist).
+ * Errors: INVALID, STATE (not a leaf, already pushed, context poisoned), plus any
+ * error of the processing it triggers.
+ */
+hapod_status hapod_push(hapod_ctx* ctx, int32_t leaf, const void* dev_snapshots, int64_t ld, int64_t ncols);
+
+/*
+ * hapod_result -- finish every pending node and return HAPOD(root) (Def. HAPOD):
+ * *k_out = number of modes; sigma_host (host, k doubles, descending) and
+ * dev_modes (device, n x k, leading dimension ld_modes, same element type as the
+ * snapshots) receive the singular values and orthonormal modes phi_n when not
+ * NULL.  Call once with NULL buffers to learn k, then again with buffers.  For a
+ * pass-through root (eps(root) = 0) the modes are the raw inputs and sigma = 1.
+ * Synchronises the stream.  Errors: STATE (a leaf was never pushed), INVALID
+ * (ld_modes < n with dev_modes set), and processing errors.  A warning from any
+ * node is returned if no error occurred.
+ */
+hapod_status hapod_result(hapod_ctx* ctx, int64_t* k_out, double* sigma_host, void* dev_modes,
+                          int64_t ld_modes);
+
+/* Node statistics; valid at any time.  Errors: INVALID (node out of range). */
+hapod_status hapod_node_stats(const hapod_ctx* ctx, int32_t node, hapod_node_info* info);
+
+/* One-line description of the last error of ctx (or of the calling thread's last
+ * context-free call when ctx is NULL).  Never NULL; owned by the library. */
+const char* hapod_last_error(const hapod_ctx* ctx);
+
+/* Free every resource of the context (waits for its stream).  NULL is a no-op. */
+void hapod_destroy(hapod_ctx* ctx);
+
+/* ------------------------------------------------------------------------
+ * Single-node steps.  Each runs the same kernels a context uses, on one node,
+ * with caller-provided device buffers; workspace is taken from the library's
+ * stream-ordered memory pool and returned before the call completes on the
+ * stream.  `precision` selects the FP64 or the mixed form as above.
+ * ---------------------------------------------------------------------- */
+
+/*
+ * hapod_gram -- Gramian G = X^T X of the method of snapshots (Sec. 2, Remark
+ * def:method_of_snapshots: G = (s_i, s_j)_{i,j}).  X: device n x m (ld ldx),
+ * double (FP64) or float (mixed).  G: device m x m FP64, ld = m, both triangles
+ * written.  Errors: INVALID, CUDA, OOM.
+ */
+hapod_status hapod_gram(int32_t precision, int64_t n, int64_t m, const void* X, int64_t ldx, double* G,
+                        void* stream);
+
+/*
+ * hapod_eig -- eigen-decomposition G = V diag(lambda) V^T of a symmetric positive
+ * semidefinite G (device m x m FP64, ld = m), as needed by the method of snapshots
+ * (Sec. 2, Remark def:method_of_snapshots).  One-sided cyclic Jacobi with
+ * round-robin ordering, FP64 (HAPOD_FP64) or FP32 rotations (mixed form);
+ * eigenvalues are Rayleigh quotients v^T G v in FP64, sorted descending, and
+ * negative values are set to 0.  lambda: device m doubles.  V: device m x m FP64,
+ * ld = m, column j belongs to lambda[j].  *sweeps_host (may be NULL) receives the
+ * sweep count.  Synchronises the stream.  Returns WARN_NOCONVERGE if the sweep
+ * limit was reached, ERR_NONFINITE for NaN/Inf in G.
+ */
+hapod_status hapod_eig(int32_t precision, int64_t m, const double* G, double* lambda, double* V,
+                       int32_t* sweeps_host, void* stream);
+
+/*
+ * hapod_truncate -- truncation rule of the POD (Sec. 2, Def. truncated POD, with
+ * Eq. pod_error): N = min{N' in 0..m : sum_{j >= N'} lambda_j <= eps^2} (0-based
+ * j, inclusive <=) for eigenvalues lambda (device, m doubles, descending,
+ * nonnegative).  *N_host and *tail_host (the discarded sum) are host outputs;
+ * synchronises the stream.  eps == 0 returns N = m without reading lambda.
+ */
+hapod_status hapod_truncate(int64_t m, const double* lambda, double eps, int64_t* N_host, double* tail_host,
+                            void* stream);
+
+/*
+ * hapod_modes -- Y = X V[:, 0:N] diag(scale) (Sec. 2, Remark
+ * def:method_of_snapshots: phi_k = lambda_k^{-1/2} sum_i psi_{k,i} s_i; with
+ * scale = NULL this is the sigma-scaled mode sigma_k phi_k that Def. HAPOD passes
+ * to the parent, with scale_j = 1/sigma_j it is phi_j).  X: device n x m (ld ldx,
+ * double or float by precision); V: device m x >= N FP64 (ld ldv); scale: device N
+ * doubles or NULL; Y: device n x N (ld ldy), same type as X.
+ */
+hapod_status hapod_modes(int32_t precision, int64_t n, int64_t m, const void* X, int64_t ldx, const double* V,
+                         int64_t ldv, int64_t N, const double* scale, void* Y, int64_t ldy, void* stream);
+
+/*
+ * hapod_pod -- POD(S, eps) of one node (Sec. 2, Def. truncated POD): Gram,
+ * eigensolve, truncation, scaled modes.  X: device n x m (ld ldx).  Outputs:
+ * *N_host; sigma (device, capacity m doubles, first N written, descending);
+ * Y (device n x capacity m, ld ldy, first N columns = sigma_j phi_j; for eps == 0
+ * Y = X and sigma = 1); *tail_host = discarded sum of sigma^2.  Synchronises the
+ * stream.
+ */
+hapod_status hapod_pod(int32_t precision, int64_t n, int64_t m, const void* X, int64_t ldx, double eps,
+                       int64_t* N_host, double* sigma, void* Y, int64_t ldy, double* tail_host, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HAPOD_H */

@@ -1,0 +1,1045 @@
+// C ABI (include/hapod.h): context, rooted tree, tolerance split and the batch
+// scheduler that runs every ready node of the tree together.
+//
+// Tree and tolerances (Sec. 3.1 Def. Rooted Tree, Sec. 3.3 Thm.
+// cor:hapod_bound) are host FP64 arithmetic done once in hapod_create.  A node is
+// ready once all of its inputs exist (Def. HAPOD: leaf input D^-1(a), inner input
+// the union of the children's sigma-scaled modes).  All ready nodes run as one
+// batch: one grouped launch per step (Gram, eigensolve, truncation, gather,
+// modes), one host read-back of the kept ranks per batch.  A child writes its
+// modes straight into its parent's input buffer when every sibling finishes in the
+// same batch (balanced trees); otherwise it parks them in its own buffer until
+// the parent's buffer can be sized exactly.  Device memory comes from a
+// stream-ordered pool; a node's owned input is freed as soon as its modes exist
+// (Sec. 3.4, reduced memory requirements).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "hapod_internal.cuh"
+
+using namespace hapod;
+
+namespace {
+
+thread_local std::string g_thread_error = "no error";
+
+// ------------------------------------------------------------------ memory pool
+std::mutex g_pool_mu;
+std::vector<cudaMemPool_t> g_pools;
+
+cudaError_t get_pool(int dev, cudaMemPool_t* out) {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if ((int)g_pools.size() <= dev) g_pools.resize(dev + 1, nullptr);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p;
+    cudaError_t e = cudaMemPoolCreate(&p, &props);
+    if (e != cudaSuccess) return e;
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &thr);
+    g_pools[dev] = p;
+  }
+  *out = g_pools[dev];
+  return cudaSuccess;
+}
+
+struct Env {
+  int dev = 0;
+  cudaStream_t s = nullptr;
+  cudaMemPool_t pool = nullptr;
+  std::string err;
+  hapod_status code = HAPOD_OK;
+
+  bool fail(hapod_status c, const std::string& msg) {
+    if (code == HAPOD_OK || code >= HAPOD_WARN_NOCONVERGE) {
+      code = c;
+      err = msg;
+    }
+    return false;
+  }
+  bool cuda(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return true;
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? HAPOD_ERR_OOM : HAPOD_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+  }
+  void* alloc(size_t bytes, const char* what) {
+    if (bytes == 0) bytes = 16;
+    void* p = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, pool, s);
+    if (e != cudaSuccess) {
+      cuda(e, what);
+      return nullptr;
+    }
+    return p;
+  }
+  void release(void* p) {
+    if (p) cudaFreeAsync(p, s);
+  }
+  template <typename T>
+  T* upload(const std::vector<T>& v, const char* what) {
+    T* d = static_cast<T*>(alloc(sizeof(T) * std::max<size_t>(1, v.size()), what));
+    if (!d) return nullptr;
+    if (!v.empty() && !cuda(cudaMemcpyAsync(d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, s), what)) {
+      release(d);
+      return nullptr;
+    }
+    return d;
+  }
+};
+
+bool init_env(Env& env, void* stream) {
+  env.s = static_cast<cudaStream_t>(stream);
+  if (!env.cuda(cudaGetDevice(&env.dev), "cudaGetDevice")) return false;
+  return env.cuda(get_pool(env.dev, &env.pool), "memory pool");
+}
+
+bool valid_precision(int p) { return p == HAPOD_FP64 || p == HAPOD_MIXED_BF16X3; }
+size_t elem_size(int p) { return p == HAPOD_FP64 ? sizeof(double) : sizeof(float); }
+
+// ------------------------------------------------------------- batched steps
+// One node of a batch: its input and the per-node device buffers of the steps.
+struct Work {
+  const void* X = nullptr;
+  int64_t ldx = 0;
+  int64_t n = 0;
+  int64_t m = 0;
+  double eps = 0.0;
+  // device buffers
+  double* G = nullptr;
+  void* A = nullptr;
+  void* V = nullptr;
+  double* lam_tmp = nullptr;
+  double* lambda = nullptr;
+  int32_t* perm = nullptr;
+  unsigned* sync = nullptr;
+  double* sigma = nullptr;
+  double* Vk = nullptr;
+  // results
+  NodeResult res{};
+  std::vector<double> sigma_host;
+  // modes destination
+  void* Y = nullptr;
+  int64_t ldy = 0;
+  double* scale = nullptr;  // device 1/sigma (root)
+};
+
+constexpr int kMaxSweeps = 40;
+constexpr int kEigGroupMinM = 512;  // nodes at least this wide get a CTA group
+
+int eig_group_size(int64_t m, int max_coresident) {
+  if (m < kEigGroupMinM) return 1;
+  const int64_t want = (m + 63) / 64;  // ~32 pairs per CTA per step
+  return (int)std::max<int64_t>(1, std::min<int64_t>(want, max_coresident));
+}
+
+bool alloc_work(Env& env, std::vector<Work*>& ws, bool fp64) {
+  const size_t t = fp64 ? sizeof(double) : sizeof(float);
+  for (Work* w : ws) {
+    const size_t mm = (size_t)w->m * w->m;
+    w->G = (double*)env.alloc(mm * sizeof(double), "alloc G");
+    w->A = env.alloc(mm * t, "alloc Jacobi A");
+    w->V = env.alloc(mm * t, "alloc Jacobi V");
+    w->lam_tmp = (double*)env.alloc(w->m * sizeof(double), "alloc lambda");
+    w->lambda = (double*)env.alloc(w->m * sizeof(double), "alloc lambda");
+    w->perm = (int32_t*)env.alloc(w->m * sizeof(int32_t), "alloc perm");
+    w->sync = (unsigned*)env.alloc(8 * sizeof(unsigned), "alloc sync");
+    w->sigma = (double*)env.alloc(w->m * sizeof(double), "alloc sigma");
+    if (!w->G || !w->A || !w->V || !w->lam_tmp || !w->lambda || !w->perm || !w->sync || !w->sigma) return false;
+    if (!env.cuda(cudaMemsetAsync(w->sync, 0, 8 * sizeof(unsigned), env.s), "memset")) return false;
+  }
+  return true;
+}
+
+void free_work(Env& env, std::vector<Work*>& ws) {
+  for (Work* w : ws) {
+    env.release(w->G);
+    env.release(w->A);
+    env.release(w->V);
+    env.release(w->lam_tmp);
+    env.release(w->lambda);
+    env.release(w->perm);
+    env.release(w->sync);
+    env.release(w->sigma);
+    env.release(w->Vk);
+    w->G = nullptr;
+    w->A = w->V = nullptr;
+    w->lam_tmp = w->lambda = w->sigma = w->Vk = nullptr;
+    w->perm = nullptr;
+    w->sync = nullptr;
+  }
+}
+
+// K1 for every node of ws into w->G.
+bool step_gram(Env& env, int precision, std::vector<Work*>& ws) {
+  if (ws.empty()) return true;
+  const bool fp64 = precision == HAPOD_FP64;
+  std::vector<GramJob> jobs(ws.size());
+  for (size_t i = 0; i < ws.size(); ++i) {
+    GramJob& J = jobs[i];
+    memset(&J, 0, sizeof(J));
+    J.X = ws[i]->X;
+    J.ldx = ws[i]->ldx;
+    J.n = ws[i]->n;
+    J.m = (int32_t)ws[i]->m;
+    J.G = ws[i]->G;
+  }
+  int4 *items = nullptr, *reduce = nullptr;
+  GramPlan plan;
+  const int tile = fp64 ? 64 : 128;
+  plan_gram(jobs.data(), (int)jobs.size(), tile, fp64 ? 256 : 1024, fp64 ? 4 * kNumSMs : 2 * kNumSMs, &items,
+            &reduce, &plan);
+  std::vector<int4> it(items, items + plan.num_items), rd(reduce, reduce + plan.num_reduce);
+  free(items);
+  GramJob* jobs_d = env.upload(jobs, "upload gram jobs");
+  int4* items_d = env.upload(it, "upload gram items");
+  int4* red_d = env.upload(rd, "upload gram reduce");
+  double* partials = plan.partial_bytes ? (double*)env.alloc(plan.partial_bytes, "alloc gram partials") : nullptr;
+  int* errf = fp64 ? nullptr : (int*)env.alloc(sizeof(int), "alloc flag");
+  bool ok = jobs_d && items_d && red_d && (partials || !plan.partial_bytes) && (fp64 || errf);
+  if (ok) {
+    cudaError_t e;
+    if (fp64) {
+      e = launch_gram_f64(jobs_d, items_d, plan.num_items, red_d, plan.num_reduce, partials, env.s);
+    } else {
+      ok = env.cuda(cudaMemsetAsync(errf, 0, sizeof(int), env.s), "memset");
+      e = launch_gram_tc(jobs_d, items_d, plan.num_items, red_d, plan.num_reduce, partials, errf, env.s);
+    }
+    ok = ok && env.cuda(e, "gram launch");
+  }
+  env.release(jobs_d);
+  env.release(items_d);
+  env.release(red_d);
+  env.release(partials);
+  env.release(errf);
+  return ok;
+}
+
+// K2 for every node (w->G -> lambda, perm, V); results land in res_d[i].
+bool step_eig(Env& env, bool fp64, std::vector<Work*>& ws, NodeResult* res_d) {
+  if (ws.empty()) return true;
+  int per_sm = 0;
+  // the kernel is launched with eig_threads() threads; one CTA per SM is the safe co-residency bound
+  per_sm = 1;
+  int nsm = kNumSMs;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, env.dev);
+  const int max_group = std::max(1, nsm * per_sm);
+  std::vector<EigJob> jobs(ws.size());
+  std::vector<int2> small_map;
+  std::vector<std::vector<int2>> big_maps;
+  for (size_t i = 0; i < ws.size(); ++i) {
+    Work* w = ws[i];
+    EigJob& J = jobs[i];
+    J.G = w->G;
+    J.A = w->A;
+    J.V = w->V;
+    J.lam_tmp = w->lam_tmp;
+    J.lambda = w->lambda;
+    J.perm = w->perm;
+    J.sync = w->sync;
+    J.result = res_d + i;
+    J.m = (int32_t)w->m;
+    J.group = eig_group_size(w->m, max_group);
+    if (J.group == 1) {
+      small_map.push_back(make_int2((int)i, 0));
+    } else {
+      big_maps.emplace_back();
+      for (int r = 0; r < J.group; ++r) big_maps.back().push_back(make_int2((int)i, r));
+    }
+  }
+  EigJob* jobs_d = env.upload(jobs, "upload eig jobs");
+  if (!jobs_d) return false;
+  bool ok = true;
+  if (!small_map.empty()) {
+    int2* map_d = env.upload(small_map, "upload eig map");
+    ok = map_d && env.cuda(launch_eig(fp64, jobs_d, map_d, (int)small_map.size(), false, kMaxSweeps, env.s),
+                           "jacobi launch");
+    env.release(map_d);
+  }
+  for (auto& bm : big_maps) {
+    if (!ok) break;
+    int2* map_d = env.upload(bm, "upload eig map");
+    ok = map_d && env.cuda(launch_eig(fp64, jobs_d, map_d, (int)bm.size(), true, kMaxSweeps, env.s),
+                           "jacobi cooperative launch");
+    env.release(map_d);
+  }
+  env.release(jobs_d);
+  return ok;
+}
+
+bool step_truncate(Env& env, std::vector<Work*>& ws, NodeResult* res_d) {
+  if (ws.empty()) return true;
+  std::vector<TruncJob> jobs(ws.size());
+  for (size_t i = 0; i < ws.size(); ++i) {
+    jobs[i].lambda = ws[i]->lambda;
+    jobs[i].sigma = ws[i]->sigma;
+    jobs[i].result = res_d + i;
+    jobs[i].eps2 = ws[i]->eps * ws[i]->eps;
+    jobs[i].m = (int32_t)ws[i]->m;
+    jobs[i].pad = 0;
+  }
+  TruncJob* d = env.upload(jobs, "upload trunc jobs");
+  bool ok = d && env.cuda(launch_truncate(d, (int)jobs.size(), env.s), "truncate launch");
+  env.release(d);
+  return ok;
+}
+
+// Gram + eig + truncation for ws, then read back k, tail, sigma (synchronises).
+bool run_pod_front(Env& env, int precision, std::vector<Work*>& ws) {
+  if (ws.empty()) return true;
+  const bool fp64 = precision == HAPOD_FP64;
+  if (!alloc_work(env, ws, fp64)) return false;
+  NodeResult* res_d = (NodeResult*)env.alloc(sizeof(NodeResult) * ws.size(), "alloc results");
+  if (!res_d) return false;
+  bool ok = env.cuda(cudaMemsetAsync(res_d, 0, sizeof(NodeResult) * ws.size(), env.s), "memset");
+  ok = ok && step_gram(env, precision, ws);
+  ok = ok && step_eig(env, fp64, ws, res_d);
+  ok = ok && step_truncate(env, ws, res_d);
+  std::vector<NodeResult> res(ws.size());
+  if (ok)
+    ok = env.cuda(cudaMemcpyAsync(res.data(), res_d, sizeof(NodeResult) * ws.size(), cudaMemcpyDeviceToHost, env.s),
+                  "read back results");
+  for (Work* w : ws) {
+    w->sigma_host.assign((size_t)w->m, 0.0);
+    if (ok)
+      ok = env.cuda(cudaMemcpyAsync(w->sigma_host.data(), w->sigma, sizeof(double) * w->m, cudaMemcpyDeviceToHost,
+                                    env.s),
+                    "read back sigma");
+  }
+  ok = ok && env.cuda(cudaStreamSynchronize(env.s), "synchronize");
+  env.release(res_d);
+  if (!ok) return false;
+  for (size_t i = 0; i < ws.size(); ++i) {
+    ws[i]->res = res[i];
+    ws[i]->sigma_host.resize((size_t)std::max(0, res[i].k));
+    const int st = res[i].status;
+    if (st != HAPOD_OK && st < HAPOD_WARN_NOCONVERGE)
+      return env.fail((hapod_status)st, st == HAPOD_ERR_NONFINITE ? "non-finite value in a Gram matrix"
+                                                                   : "device-side wait timed out in the eigensolver");
+  }
+  return true;
+}
+
+// Gather V_k and form Y = X V_k (diag(scale)) into w->Y for every w with k > 0.
+bool run_pod_back(Env& env, int precision, std::vector<Work*>& ws) {
+  const bool fp64 = precision == HAPOD_FP64;
+  std::vector<GatherJob> gj;
+  std::vector<ModesJob> mj;
+  std::vector<Work*> act;
+  for (Work* w : ws)
+    if (w->res.k > 0 && w->Y) act.push_back(w);
+  if (act.empty()) return true;
+  for (Work* w : act) {
+    w->Vk = (double*)env.alloc(sizeof(double) * w->m * w->res.k, "alloc Vk");
+    if (!w->Vk) return false;
+    GatherJob g;
+    g.V = w->V;
+    g.perm = w->perm;
+    g.Vk = w->Vk;
+    g.m = (int32_t)w->m;
+    g.k = w->res.k;
+    gj.push_back(g);
+  }
+  GatherJob* gd = env.upload(gj, "upload gather jobs");
+  bool ok = gd && env.cuda(launch_gather(fp64, gd, (int)gj.size(), env.s), "gather launch");
+  env.release(gd);
+  if (!ok) return false;
+  const int tr = modes_tile_rows(fp64), tc = modes_tile_cols(fp64);
+  int64_t blocks = 0;
+  for (Work* w : act) {
+    ModesJob J;
+    memset(&J, 0, sizeof(J));
+    J.X = w->X;
+    J.ldx = w->ldx;
+    J.Vk = w->Vk;
+    J.ldv = w->m;
+    J.scale = w->scale;
+    J.Y = w->Y;
+    J.ldy = w->ldy;
+    J.n = w->n;
+    J.m = (int32_t)w->m;
+    J.k = w->res.k;
+    J.row_tiles = (int32_t)((w->n + tr - 1) / tr);
+    J.col_tiles = (J.k + tc - 1) / tc;
+    J.block_base = blocks;
+    blocks += (int64_t)J.row_tiles * J.col_tiles;
+    mj.push_back(J);
+  }
+  ModesJob* md = env.upload(mj, "upload modes jobs");
+  if (!md) return false;
+  if (fp64) {
+    ok = env.cuda(launch_modes_f64(md, (int)mj.size(), blocks, env.s), "modes launch");
+  } else {
+    int* errf = (int*)env.alloc(sizeof(int), "alloc flag");
+    ok = errf && env.cuda(cudaMemsetAsync(errf, 0, sizeof(int), env.s), "memset") &&
+         env.cuda(launch_modes_tc(md, (int)mj.size(), blocks, errf, env.s), "modes launch");
+    env.release(errf);
+  }
+  env.release(md);
+  return ok;
+}
+
+}  // namespace
+
+// ====================================================================== context
+struct NodeRT {
+  int32_t parent = -1;
+  std::vector<int32_t> children;
+  int32_t level = 1;
+  int64_t leaf_cols = 0;
+  int64_t acc = 0;
+  double eps = 0.0;
+  int state = 0;  // 0 waiting, 1 ready, 2 done
+  // input
+  const void* in = nullptr;
+  int64_t in_ld = 0;
+  int64_t m = 0;
+  void* in_owned = nullptr;
+  // as a parent: input buffer being filled by the children
+  void* pbuf = nullptr;
+  int64_t pfill = 0;
+  int children_done = 0;
+  // output
+  int64_t k = -1;
+  double tail = 0.0;
+  int32_t sweeps = 0;
+  int32_t status = HAPOD_OK;
+  std::vector<double> sigma;
+  void* stash = nullptr;  // own copy of the output while the parent cannot be sized
+  int64_t stash_offset = -1;
+};
+
+struct hapod_ctx {
+  Env env;
+  int64_t n = 0;
+  int precision = HAPOD_FP64;
+  size_t esize = 8;
+  std::vector<NodeRT> nodes;
+  int root = -1;
+  int LT = 1;
+  int64_t S = 0;
+  double eps_star = 0.0;
+  int max_pending = 0;
+  int pending = 0;
+  int leaves_total = 0;
+  int leaves_pushed = 0;
+  bool poisoned = false;
+  hapod_status warning = HAPOD_OK;
+  void* result = nullptr;  // n x k root modes (phi), owned
+  std::string err = "no error";
+};
+
+namespace {
+
+hapod_status ctx_fail(hapod_ctx* c) {
+  c->poisoned = true;
+  c->err = c->env.err;
+  return c->env.code;
+}
+
+// Allocate parent p's input buffer once every child's rank is known (sized
+// exactly: sum of the children's k) and move in the outputs that children of
+// earlier batches parked in their own buffers.  Returns false on failure.
+bool ensure_parent_buffer(hapod_ctx* c, int p) {
+  NodeRT& P = c->nodes[p];
+  if (P.pbuf) return true;
+  const size_t col_bytes = (size_t)c->n * c->esize;
+  int64_t cap = 0;
+  for (int ch : P.children) cap += std::max<int64_t>(0, c->nodes[ch].k);
+  if (cap == 0) return true;
+  P.pbuf = c->env.alloc(col_bytes * cap, "alloc parent input");
+  if (!P.pbuf) return false;
+  for (int ch : P.children) {
+    NodeRT& C = c->nodes[ch];
+    if (C.state == 2 && C.stash && C.k > 0) {
+      if (!c->env.cuda(cudaMemcpyAsync((char*)P.pbuf + (size_t)P.pfill * col_bytes, C.stash, C.k * col_bytes,
+                                       cudaMemcpyDeviceToDevice, c->env.s),
+                       "copy parked modes"))
+        return false;
+      P.pfill += C.k;
+      c->env.release(C.stash);
+      C.stash = nullptr;
+    }
+  }
+  return true;
+}
+
+// Where the output of node a (k > 0) goes once its rank is known: the root's
+// result buffer, its slot in the parent's input buffer when every sibling's rank
+// is known in this batch, or else a parked buffer of its own.  Returns the device
+// pointer of its first column (ld = n), or nullptr on allocation failure.
+void* place_output(hapod_ctx* c, int a, const std::vector<int>& batch_children) {
+  NodeRT& A = c->nodes[a];
+  const size_t col_bytes = (size_t)c->n * c->esize;
+  if (A.parent < 0) {
+    c->result = c->env.alloc(col_bytes * std::max<int64_t>(1, A.k), "alloc result");
+    return c->result;
+  }
+  NodeRT& P = c->nodes[A.parent];
+  if (P.children_done + batch_children[A.parent] == (int)P.children.size()) {
+    if (!ensure_parent_buffer(c, A.parent)) return nullptr;
+    void* dst = (char*)P.pbuf + (size_t)P.pfill * col_bytes;
+    P.pfill += A.k;
+    return dst;
+  }
+  A.stash = c->env.alloc(col_bytes * A.k, "alloc parked modes");
+  return A.stash;
+}
+
+bool run_batch(hapod_ctx* c, const std::vector<int>& batch) {
+  Env& env = c->env;
+  const size_t col_bytes = (size_t)c->n * c->esize;
+  std::vector<Work> works(batch.size());
+  std::vector<Work*> compute;
+  for (size_t i = 0; i < batch.size(); ++i) {
+    NodeRT& A = c->nodes[batch[i]];
+    Work& w = works[i];
+    w.X = A.in;
+    w.ldx = A.in_ld;
+    w.n = c->n;
+    w.m = A.m;
+    w.eps = A.eps;
+    if (A.eps > 0.0 && A.m > 0) compute.push_back(&w);
+  }
+  if (!run_pod_front(env, c->precision, compute)) {
+    free_work(env, compute);
+    return false;
+  }
+  // ranks known: pass-through (eps = 0) keeps all m columns with sigma = 1 (Def. truncated POD)
+  std::vector<int> batch_children(c->nodes.size(), 0);
+  for (size_t i = 0; i < batch.size(); ++i) {
+    NodeRT& A = c->nodes[batch[i]];
+    Work& w = works[i];
+    if (A.eps > 0.0 && A.m > 0) {
+      A.k = w.res.k;
+      A.tail = w.res.tail;
+      A.sweeps = w.res.sweeps;
+      A.status = w.res.status;
+      A.sigma = w.sigma_host;
+      if (A.status >= HAPOD_WARN_NOCONVERGE && c->warning == HAPOD_OK) c->warning = (hapod_status)A.status;
+    } else {
+      A.k = A.m;
+      A.tail = 0.0;
+      A.sweeps = 0;
+      A.sigma.assign((size_t)A.m, 1.0);
+    }
+    if (A.parent >= 0) batch_children[A.parent]++;
+  }
+  // output placement and modes
+  bool ok = true;
+  std::vector<double*> scales;
+  for (size_t i = 0; i < batch.size() && ok; ++i) {
+    const int a = batch[i];
+    NodeRT& A = c->nodes[a];
+    Work& w = works[i];
+    if (A.k <= 0) {
+      if (A.parent < 0) c->result = nullptr;
+      continue;
+    }
+    void* dst = place_output(c, a, batch_children);
+    if (!dst) {
+      ok = false;
+      break;
+    }
+    if (A.eps > 0.0 && A.m > 0) {
+      w.Y = dst;
+      w.ldy = c->n;
+      if (A.parent < 0) {
+        std::vector<double> inv(A.k);
+        for (int64_t j = 0; j < A.k; ++j) inv[j] = 1.0 / A.sigma[j];
+        w.scale = env.upload(inv, "upload scale");
+        if (!w.scale) ok = false;
+        scales.push_back(w.scale);
+        // resolution floor of the method of snapshots (Sec. 2 footnote: cond(G) = cond(X)^2)
+        const double u = c->precision == HAPOD_FP64 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
+        if (A.sigma[A.k - 1] < A.sigma[0] * std::sqrt((double)A.m * u)) {
+          A.status = HAPOD_WARN_BELOW_FLOOR;
+          if (c->warning == HAPOD_OK) c->warning = HAPOD_WARN_BELOW_FLOOR;
+        }
+      }
+    } else {
+      ok = env.cuda(cudaMemcpy2DAsync(dst, col_bytes, A.in, (size_t)A.in_ld * c->esize, col_bytes, (size_t)A.m,
+                                      cudaMemcpyDeviceToDevice, env.s),
+                    "copy pass-through snapshots");
+    }
+  }
+  if (ok) ok = run_pod_back(env, c->precision, compute);
+  free_work(env, compute);
+  for (double* s : scales) env.release(s);
+  if (!ok) return false;
+  // bookkeeping: free owned inputs, mark done, promote parents
+  for (size_t i = 0; i < batch.size(); ++i) {
+    NodeRT& A = c->nodes[batch[i]];
+    if (A.in_owned) {
+      env.release(A.in_owned);
+      A.in_owned = nullptr;
+    }
+    A.in = nullptr;
+    A.state = 2;
+  }
+  for (size_t i = 0; i < batch.size(); ++i) {
+    NodeRT& A = c->nodes[batch[i]];
+    if (A.parent < 0) continue;
+    NodeRT& P = c->nodes[A.parent];
+    P.children_done++;
+    if (P.children_done == (int)P.children.size()) {
+      if (!ensure_parent_buffer(c, A.parent)) return false;  // last children may all have kept 0 modes
+      P.state = 1;
+      P.in = P.pbuf;
+      P.in_owned = P.pbuf;
+      P.in_ld = c->n;
+      P.m = P.pfill;
+      P.pbuf = nullptr;
+    }
+  }
+  return true;
+}
+
+hapod_status run_ready(hapod_ctx* c) {
+  for (;;) {
+    std::vector<int> batch;
+    for (int a = 0; a < (int)c->nodes.size(); ++a)
+      if (c->nodes[a].state == 1) batch.push_back(a);
+    if (batch.empty()) break;
+    for (int a : batch)
+      if (c->nodes[a].children.empty()) c->pending--;
+    if (!run_batch(c, batch)) return ctx_fail(c);
+  }
+  return HAPOD_OK;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+extern "C" {
+
+hapod_status hapod_create(const hapod_tree* tree, const hapod_tol* tol, int64_t n_rows, void* stream,
+                          hapod_ctx** out) {
+  if (out) *out = nullptr;
+  if (!tree || !tol || !out || !tree->parent || !tree->leaf_cols || tree->num_nodes < 1 || n_rows < 1) {
+    g_thread_error = "hapod_create: null argument or non-positive size";
+    return HAPOD_ERR_INVALID;
+  }
+  if (!(tol->eps >= 0.0) || !(tol->omega >= 0.0 && tol->omega <= 1.0) || !valid_precision(tol->precision) ||
+      tol->max_pending_leaves < 0) {
+    g_thread_error = "hapod_create: eps < 0, omega outside [0, 1], unknown precision or negative max_pending_leaves";
+    return HAPOD_ERR_INVALID;
+  }
+  const int N = tree->num_nodes;
+  hapod_ctx* c = new (std::nothrow) hapod_ctx();
+  if (!c) {
+    g_thread_error = "hapod_create: out of host memory";
+    return HAPOD_ERR_OOM;
+  }
+  c->nodes.resize(N);
+  // Def. Rooted Tree: one root, each node a child of at most one node (parent array), all reach the root
+  for (int a = 0; a < N; ++a) {
+    const int p = tree->parent[a];
+    if (p < -1 || p >= N || p == a) {
+      g_thread_error = "hapod_create: parent index out of range";
+      delete c;
+      return HAPOD_ERR_TREE;
+    }
+    c->nodes[a].parent = p;
+    if (p < 0) {
+      if (c->root >= 0) {
+        g_thread_error = "hapod_create: more than one root";
+        delete c;
+        return HAPOD_ERR_TREE;
+      }
+      c->root = a;
+    } else {
+      c->nodes[p].children.push_back(a);
+    }
+  }
+  if (c->root < 0) {
+    g_thread_error = "hapod_create: no root (parent == -1)";
+    delete c;
+    return HAPOD_ERR_TREE;
+  }
+  // connectivity (Eq. treeconnected): post-order from the root must reach all nodes
+  std::vector<int> order;
+  order.reserve(N);
+  {
+    std::vector<std::pair<int, bool>> st{{c->root, false}};
+    std::vector<char> seen(N, 0);
+    while (!st.empty()) {
+      auto [a, done] = st.back();
+      st.pop_back();
+      if (done) {
+        order.push_back(a);
+        continue;
+      }
+      if (seen[a]) continue;
+      seen[a] = 1;
+      st.push_back({a, true});
+      for (int ch : c->nodes[a].children) st.push_back({ch, false});
+    }
+    if ((int)order.size() != N) {
+      g_thread_error = "hapod_create: some nodes do not reach the root (cycle or disconnected)";
+      delete c;
+      return HAPOD_ERR_TREE;
+    }
+  }
+  // levels L_T(a) and |S~_a| (post-order)
+  for (int a : order) {
+    NodeRT& A = c->nodes[a];
+    if (A.children.empty()) {
+      A.level = 1;
+      if (tree->leaf_cols[a] < 0) {
+        g_thread_error = "hapod_create: negative leaf_cols";
+        delete c;
+        return HAPOD_ERR_INVALID;
+      }
+      A.leaf_cols = tree->leaf_cols[a];
+      A.acc = A.leaf_cols;
+      c->leaves_total++;
+    } else {
+      int lv = 0;
+      int64_t acc = 0;
+      for (int ch : A.children) {
+        lv = std::max(lv, c->nodes[ch].level);
+        acc += c->nodes[ch].acc;
+      }
+      A.level = lv + 1;
+      A.acc = acc;
+    }
+  }
+  c->LT = c->nodes[c->root].level;
+  c->S = c->nodes[c->root].acc;
+  c->eps_star = c->S > 0 ? tol->eps / std::sqrt((double)c->S) : 0.0;
+  // Thm. cor:hapod_bound; a single-node tree gives its root the whole budget
+  for (int a = 0; a < N; ++a) {
+    NodeRT& A = c->nodes[a];
+    if (a == c->root)
+      A.eps = std::sqrt((double)A.acc) * (c->LT > 1 ? tol->omega : 1.0) * c->eps_star;
+    else
+      A.eps = std::sqrt((double)A.acc) / std::sqrt((double)(c->LT - 1)) *
+              std::sqrt(std::max(0.0, 1.0 - tol->omega * tol->omega)) * c->eps_star;
+    if (tol->eps_override && !std::isnan(tol->eps_override[a])) {
+      if (!(tol->eps_override[a] >= 0.0)) {
+        g_thread_error = "hapod_create: negative eps_override";
+        delete c;
+        return HAPOD_ERR_INVALID;
+      }
+      A.eps = tol->eps_override[a];
+    }
+  }
+  c->n = n_rows;
+  c->precision = tol->precision;
+  c->esize = elem_size(tol->precision);
+  c->max_pending = tol->max_pending_leaves;
+  if (!init_env(c->env, stream)) {
+    g_thread_error = c->env.err;
+    hapod_status st = c->env.code;
+    delete c;
+    return st;
+  }
+  *out = c;
+  return HAPOD_OK;
+}
+
+hapod_status hapod_push(hapod_ctx* c, int32_t leaf, const void* dev_snapshots, int64_t ld, int64_t ncols) {
+  if (!c) return HAPOD_ERR_INVALID;
+  if (c->poisoned) return HAPOD_ERR_STATE;
+  if (leaf < 0 || leaf >= (int)c->nodes.size()) {
+    c->err = "hapod_push: node index out of range";
+    return HAPOD_ERR_INVALID;
+  }
+  NodeRT& A = c->nodes[leaf];
+  if (!A.children.empty()) {
+    c->err = "hapod_push: node is not a leaf";
+    return HAPOD_ERR_STATE;
+  }
+  if (A.state != 0) {
+    c->err = "hapod_push: leaf already pushed";
+    return HAPOD_ERR_STATE;
+  }
+  if (ncols != A.leaf_cols || (ncols > 0 && (!dev_snapshots || ld < c->n))) {
+    c->err = "hapod_push: ncols differs from leaf_cols, null pointer or ld < n";
+    return HAPOD_ERR_INVALID;
+  }
+  A.in = dev_snapshots;
+  A.in_ld = ld;
+  A.m = ncols;
+  A.state = 1;
+  c->leaves_pushed++;
+  c->pending++;
+  const bool all = c->leaves_pushed == c->leaves_total;
+  if (all || (c->max_pending > 0 && c->pending >= c->max_pending)) {
+    hapod_status st = run_ready(c);
+    if (st != HAPOD_OK) return st;
+  }
+  return HAPOD_OK;
+}
+
+hapod_status hapod_result(hapod_ctx* c, int64_t* k_out, double* sigma_host, void* dev_modes, int64_t ld_modes) {
+  if (!c || !k_out) return HAPOD_ERR_INVALID;
+  if (c->poisoned) return HAPOD_ERR_STATE;
+  if (c->leaves_pushed != c->leaves_total) {
+    c->err = "hapod_result: not every leaf has been pushed";
+    return HAPOD_ERR_STATE;
+  }
+  hapod_status st = run_ready(c);
+  if (st != HAPOD_OK) return st;
+  NodeRT& R = c->nodes[c->root];
+  if (R.state != 2) {
+    c->err = "hapod_result: root not finished";
+    return HAPOD_ERR_STATE;
+  }
+  *k_out = R.k;
+  if (dev_modes && R.k > 0) {
+    if (ld_modes < c->n) {
+      c->err = "hapod_result: ld_modes < n";
+      return HAPOD_ERR_INVALID;
+    }
+    const size_t col_bytes = (size_t)c->n * c->esize;
+    if (!c->env.cuda(cudaMemcpy2DAsync(dev_modes, (size_t)ld_modes * c->esize, c->result, col_bytes, col_bytes,
+                                       (size_t)R.k, cudaMemcpyDeviceToDevice, c->env.s),
+                     "copy result"))
+      return ctx_fail(c);
+  }
+  if (sigma_host && R.k > 0) memcpy(sigma_host, R.sigma.data(), sizeof(double) * R.k);
+  if (!c->env.cuda(cudaStreamSynchronize(c->env.s), "synchronize")) return ctx_fail(c);
+  return c->warning;
+}
+
+hapod_status hapod_node_stats(const hapod_ctx* c, int32_t node, hapod_node_info* info) {
+  if (!c || !info || node < 0 || node >= (int)c->nodes.size()) return HAPOD_ERR_INVALID;
+  const NodeRT& A = c->nodes[node];
+  info->m = A.state == 2 ? A.m : 0;
+  info->k = A.state == 2 ? A.k : -1;
+  info->eps = A.eps;
+  info->tail_sq = A.tail;
+  info->level = A.level;
+  info->sweeps = A.sweeps;
+  info->state = A.state;
+  info->status = A.status;
+  return HAPOD_OK;
+}
+
+const char* hapod_last_error(const hapod_ctx* c) { return c ? c->err.c_str() : g_thread_error.c_str(); }
+
+void hapod_destroy(hapod_ctx* c) {
+  if (!c) return;
+  Env& env = c->env;
+  for (NodeRT& A : c->nodes) {
+    if (A.in_owned) env.release(A.in_owned);
+    if (A.pbuf) env.release(A.pbuf);
+    if (A.stash) env.release(A.stash);
+  }
+  env.release(c->result);
+  cudaStreamSynchronize(env.s);
+  if (env.pool) cudaMemPoolTrimTo(env.pool, 0);
+  delete c;
+}
+
+// ------------------------------------------------------------- single-node steps
+static hapod_status step_error(Env& env) {
+  g_thread_error = env.err;
+  return env.code;
+}
+
+hapod_status hapod_gram(int32_t precision, int64_t n, int64_t m, const void* X, int64_t ldx, double* G,
+                        void* stream) {
+  if (!valid_precision(precision) || n < 0 || m < 0 || ldx < n || (m > 0 && (!X || !G)) || m > INT32_MAX) {
+    g_thread_error = "hapod_gram: invalid argument";
+    return HAPOD_ERR_INVALID;
+  }
+  if (m == 0) return HAPOD_OK;
+  Env env;
+  if (!init_env(env, stream)) return step_error(env);
+  if (n == 0) {
+    if (!env.cuda(cudaMemsetAsync(G, 0, sizeof(double) * m * m, env.s), "memset")) return step_error(env);
+    return HAPOD_OK;
+  }
+  Work w;
+  w.X = X;
+  w.ldx = ldx;
+  w.n = n;
+  w.m = m;
+  w.G = G;
+  std::vector<Work*> ws{&w};
+  if (!step_gram(env, precision, ws)) return step_error(env);
+  return HAPOD_OK;
+}
+
+hapod_status hapod_eig(int32_t precision, int64_t m, const double* G, double* lambda, double* V, int32_t* sweeps_host,
+                       void* stream) {
+  if (!valid_precision(precision) || m < 0 || m > INT32_MAX || (m > 0 && (!G || !lambda || !V))) {
+    g_thread_error = "hapod_eig: invalid argument";
+    return HAPOD_ERR_INVALID;
+  }
+  if (sweeps_host) *sweeps_host = 0;
+  if (m == 0) return HAPOD_OK;
+  Env env;
+  if (!init_env(env, stream)) return step_error(env);
+  const bool fp64 = precision == HAPOD_FP64;
+  Work w;
+  w.m = m;
+  std::vector<Work*> ws{&w};
+  if (!alloc_work(env, ws, fp64)) {
+    free_work(env, ws);
+    return step_error(env);
+  }
+  NodeResult* res_d = (NodeResult*)env.alloc(sizeof(NodeResult), "alloc result");
+  bool ok = res_d && env.cuda(cudaMemsetAsync(res_d, 0, sizeof(NodeResult), env.s), "memset") &&
+            env.cuda(cudaMemcpyAsync(w.G, G, sizeof(double) * m * m, cudaMemcpyDeviceToDevice, env.s), "copy G") &&
+            step_eig(env, fp64, ws, res_d);
+  if (ok) {
+    GatherJob g;
+    g.V = w.V;
+    g.perm = w.perm;
+    g.Vk = V;
+    g.m = (int32_t)m;
+    g.k = (int32_t)m;
+    std::vector<GatherJob> gj{g};
+    GatherJob* gd = env.upload(gj, "upload gather");
+    ok = gd && env.cuda(launch_gather(fp64, gd, 1, env.s), "gather launch") &&
+         env.cuda(cudaMemcpyAsync(lambda, w.lambda, sizeof(double) * m, cudaMemcpyDeviceToDevice, env.s), "copy");
+    env.release(gd);
+  }
+  NodeResult r{};
+  if (ok) ok = env.cuda(cudaMemcpyAsync(&r, res_d, sizeof(r), cudaMemcpyDeviceToHost, env.s), "read back");
+  env.release(res_d);
+  free_work(env, ws);
+  ok = env.cuda(cudaStreamSynchronize(env.s), "synchronize") && ok;
+  if (!ok) return step_error(env);
+  if (sweeps_host) *sweeps_host = r.sweeps;
+  if (r.status != HAPOD_OK) g_thread_error = "hapod_eig: see status";
+  return (hapod_status)r.status;
+}
+
+hapod_status hapod_truncate(int64_t m, const double* lambda, double eps, int64_t* N_host, double* tail_host,
+                            void* stream) {
+  if (m < 0 || m > INT32_MAX || !(eps >= 0.0) || !N_host || (m > 0 && eps > 0.0 && !lambda)) {
+    g_thread_error = "hapod_truncate: invalid argument";
+    return HAPOD_ERR_INVALID;
+  }
+  if (eps == 0.0 || m == 0) {
+    *N_host = m;
+    if (tail_host) *tail_host = 0.0;
+    return HAPOD_OK;
+  }
+  Env env;
+  if (!init_env(env, stream)) return step_error(env);
+  Work w;
+  w.m = m;
+  w.eps = eps;
+  w.lambda = const_cast<double*>(lambda);
+  w.sigma = (double*)env.alloc(sizeof(double) * m, "alloc sigma");
+  NodeResult* res_d = (NodeResult*)env.alloc(sizeof(NodeResult), "alloc result");
+  std::vector<Work*> ws{&w};
+  NodeResult r{};
+  bool ok = w.sigma && res_d && env.cuda(cudaMemsetAsync(res_d, 0, sizeof(NodeResult), env.s), "memset") &&
+            step_truncate(env, ws, res_d) &&
+            env.cuda(cudaMemcpyAsync(&r, res_d, sizeof(r), cudaMemcpyDeviceToHost, env.s), "read back");
+  env.release(w.sigma);
+  env.release(res_d);
+  ok = env.cuda(cudaStreamSynchronize(env.s), "synchronize") && ok;
+  if (!ok) return step_error(env);
+  *N_host = r.k;
+  if (tail_host) *tail_host = r.tail;
+  return HAPOD_OK;
+}
+
+hapod_status hapod_modes(int32_t precision, int64_t n, int64_t m, const void* X, int64_t ldx, const double* V,
+                         int64_t ldv, int64_t N, const double* scale, void* Y, int64_t ldy, void* stream) {
+  if (!valid_precision(precision) || n < 0 || m < 0 || N < 0 || N > m || ldx < n || ldv < m || ldy < n ||
+      m > INT32_MAX || (N > 0 && n > 0 && (!X || !V || !Y))) {
+    g_thread_error = "hapod_modes: invalid argument";
+    return HAPOD_ERR_INVALID;
+  }
+  if (N == 0 || n == 0) return HAPOD_OK;
+  Env env;
+  if (!init_env(env, stream)) return step_error(env);
+  const bool fp64 = precision == HAPOD_FP64;
+  const int tr = modes_tile_rows(fp64), tc = modes_tile_cols(fp64);
+  ModesJob J;
+  memset(&J, 0, sizeof(J));
+  J.X = X;
+  J.ldx = ldx;
+  J.Vk = V;
+  J.ldv = ldv;
+  J.scale = scale;
+  J.Y = Y;
+  J.ldy = ldy;
+  J.n = n;
+  J.m = (int32_t)m;
+  J.k = (int32_t)N;
+  J.row_tiles = (int32_t)((n + tr - 1) / tr);
+  J.col_tiles = (int32_t)((N + tc - 1) / tc);
+  J.block_base = 0;
+  std::vector<ModesJob> mj{J};
+  ModesJob* md = env.upload(mj, "upload modes job");
+  if (!md) return step_error(env);
+  const int64_t blocks = (int64_t)J.row_tiles * J.col_tiles;
+  bool ok;
+  if (fp64) {
+    ok = env.cuda(launch_modes_f64(md, 1, blocks, env.s), "modes launch");
+  } else {
+    int* errf = (int*)env.alloc(sizeof(int), "alloc flag");
+    ok = errf && env.cuda(cudaMemsetAsync(errf, 0, sizeof(int), env.s), "memset") &&
+         env.cuda(launch_modes_tc(md, 1, blocks, errf, env.s), "modes launch");
+    env.release(errf);
+  }
+  env.release(md);
+  if (!ok) return step_error(env);
+  return HAPOD_OK;
+}
+
+hapod_status hapod_pod(int32_t precision, int64_t n, int64_t m, const void* X, int64_t ldx, double eps,
+                       int64_t* N_host, double* sigma, void* Y, int64_t ldy, double* tail_host, void* stream) {
+  if (!valid_precision(precision) || n < 1 || m < 0 || m > INT32_MAX || ldx < n || ldy < n || !(eps >= 0.0) ||
+      !N_host || (m > 0 && (!X || !Y || !sigma))) {
+    g_thread_error = "hapod_pod: invalid argument";
+    return HAPOD_ERR_INVALID;
+  }
+  Env env;
+  if (!init_env(env, stream)) return step_error(env);
+  const size_t es = elem_size(precision);
+  if (eps == 0.0 || m == 0) {  // POD(S, 0) = {(1, s)}
+    *N_host = m;
+    if (tail_host) *tail_host = 0.0;
+    if (m == 0) return HAPOD_OK;
+    std::vector<double> ones((size_t)m, 1.0);
+    bool ok = env.cuda(cudaMemcpyAsync(sigma, ones.data(), sizeof(double) * m, cudaMemcpyHostToDevice, env.s), "copy") &&
+              env.cuda(cudaMemcpy2DAsync(Y, ldy * es, X, ldx * es, n * es, m, cudaMemcpyDeviceToDevice, env.s),
+                       "copy") &&
+              env.cuda(cudaStreamSynchronize(env.s), "synchronize");
+    return ok ? HAPOD_OK : step_error(env);
+  }
+  Work w;
+  w.X = X;
+  w.ldx = ldx;
+  w.n = n;
+  w.m = m;
+  w.eps = eps;
+  std::vector<Work*> ws{&w};
+  bool ok = run_pod_front(env, precision, ws);
+  if (ok && w.res.k > 0) {
+    w.Y = Y;
+    w.ldy = ldy;
+    ok = env.cuda(cudaMemcpyAsync(sigma, w.sigma, sizeof(double) * w.res.k, cudaMemcpyDeviceToDevice, env.s),
+                  "copy sigma") &&
+         run_pod_back(env, precision, ws);
+  }
+  free_work(env, ws);
+  ok = env.cuda(cudaStreamSynchronize(env.s), "synchronize") && ok;
+  if (!ok) return step_error(env);
+  *N_host = w.res.k;
+  if (tail_host) *tail_host = w.res.tail;
+  return (hapod_status)(w.res.status >= HAPOD_WARN_NOCONVERGE ? w.res.status : HAPOD_OK);
+}
+
+}  // extern "C"

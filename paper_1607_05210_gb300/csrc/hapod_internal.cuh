@@ -1,0 +1,125 @@
+// Internal declarations shared by the CUDA translation units of libhapod.
+// Not part of the public ABI (that is include/hapod.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/hapod.h"
+
+namespace hapod {
+
+constexpr int kNumSMs = 152;  // GB300: 2 dies x 76 SMs (used only as a sizing hint)
+
+// Per-node result record written by the device, read back once per batch.
+struct NodeResult {
+  int32_t k;        // kept modes
+  int32_t sweeps;   // Jacobi sweeps
+  int32_t status;   // hapod_status
+  int32_t pad;
+  double tail;      // discarded sum of lambda
+  double trace;     // trace(G)
+};
+
+// ---------------------------------------------------------------- Gram (K1)
+// One job = one node's Gram matrix.  Work items are (job, ti, tj, split): the
+// tile (ti, tj) with ti <= tj of G over the row range of `split`.
+struct GramJob {
+  const void* X;
+  int64_t ldx;
+  int64_t n;
+  int64_t rows_per_split;
+  double* G;        // m x m, ld = m
+  int64_t item_base;
+  int32_t m;
+  int32_t tiles;    // tiles per dimension
+  int32_t splits;
+  int32_t pad;
+};
+
+struct GramPlan {
+  int tile;             // tile edge (64 FP64, 128 tensor-core)
+  int num_items;
+  int num_reduce;       // tiles that need a split-K reduction
+  size_t partial_bytes; // workspace for split partials
+};
+
+// Builds the item list on the host; jobs[] must have X, ldx, n, m, G set.
+// Fills tiles, splits, rows_per_split, item_base; items (int4: job, ti, tj, split)
+// and reduce list (int4: job, ti, tj, first item) are appended to the vectors.
+void plan_gram(GramJob* jobs, int njobs, int tile, int min_rows_per_split, int target_items,
+               int4** items, int4** reduce, GramPlan* plan);
+
+// Sum split partials of each reduce-list tile in split order; both triangles.
+cudaError_t launch_gram_reduce(int tile, const GramJob* jobs_dev, const int4* reduce_dev, int num_reduce,
+                               const double* partials, cudaStream_t s);
+cudaError_t launch_gram_f64(const GramJob* jobs_dev, const int4* items_dev, int num_items, const int4* reduce_dev,
+                            int num_reduce, double* partials, cudaStream_t s);
+// Mixed form (tcgen05, split-bf16).  Returns cudaErrorNotSupported if the
+// device cannot run it.
+cudaError_t launch_gram_tc(const GramJob* jobs_dev, const int4* items_dev, int num_items, const int4* reduce_dev,
+                           int num_reduce, double* partials, int* err_flag, cudaStream_t s);
+
+// ---------------------------------------------------------------- eig (K2)
+struct EigJob {
+  const double* G;     // m x m FP64 input (not modified)
+  void* A;             // m x m work (T), becomes G V
+  void* V;             // m x m work (T), eigenvectors (unsorted)
+  double* lam_tmp;     // m, unsorted Rayleigh quotients
+  double* lambda;      // m, sorted descending, clamped >= 0
+  int32_t* perm;       // m, sorted position -> column of V
+  unsigned* sync;      // 8 words, zeroed: barrier count, generation, sweep flags x3, abort
+  NodeResult* result;
+  int32_t m;
+  int32_t group;       // CTAs cooperating on this job
+};
+// Blocks: block_map[b] = (job, rank in group).  Jobs with group > 1 need a
+// cooperative launch (co-residency); launch_eig handles that.
+cudaError_t launch_eig(bool fp64, const EigJob* jobs_dev, const int2* block_map_dev, int num_blocks,
+                       bool cooperative, int max_sweeps, cudaStream_t s);
+int eig_threads();
+
+// ---------------------------------------------------------------- truncation (K3)
+struct TruncJob {
+  const double* lambda;  // m, descending
+  double* sigma;         // out: sqrt(lambda_j), j < k
+  NodeResult* result;    // out: k, tail
+  double eps2;
+  int32_t m;
+  int32_t pad;
+};
+cudaError_t launch_truncate(const TruncJob* jobs_dev, int njobs, cudaStream_t s);
+
+// ---------------------------------------------------------------- modes (K4)
+// Gather Vk[:, j] = V[:, perm[j]] (FP64), j < k, ld of Vk = m.
+struct GatherJob {
+  const void* V;       // m x m (T)
+  const int32_t* perm;
+  double* Vk;
+  int32_t m;
+  int32_t k;
+};
+cudaError_t launch_gather(bool fp64_src, const GatherJob* jobs_dev, int njobs, cudaStream_t s);
+
+struct ModesJob {
+  const void* X;        // n x m, ld ldx
+  const double* Vk;     // m x k, ld ldv
+  const double* scale;  // k or null (root: 1 / sigma)
+  void* Y;              // n x k, ld ldy
+  int64_t ldx;
+  int64_t ldv;
+  int64_t ldy;
+  int64_t n;
+  int64_t block_base;   // first block of this job
+  int32_t m;
+  int32_t k;
+  int32_t row_tiles;
+  int32_t col_tiles;
+};
+cudaError_t launch_modes_f64(const ModesJob* jobs_dev, int njobs, int64_t total_blocks, cudaStream_t s);
+cudaError_t launch_modes_tc(const ModesJob* jobs_dev, int njobs, int64_t total_blocks, int* err_flag,
+                            cudaStream_t s);
+int modes_tile_rows(bool fp64);
+int modes_tile_cols(bool fp64);
+
+}  // namespace hapod

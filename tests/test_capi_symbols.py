@@ -1,0 +1,71 @@
+"""The C-ABI library loads and exports every symbol include/hapod.h declares (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "hapod.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hapod_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_1607_05210_gb300 import build
+
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("hapod_create", "hapod_push", "hapod_result", "hapod_destroy", "hapod_node_stats", "hapod_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_loads_and_names_match(lib_path):
+    from paper_1607_05210_gb300 import hapod as H
+
+    assert set(H.EXPORTED) <= set(_declared())
+    for n in H.EXPORTED:
+        assert callable(getattr(H, n))
+
+
+def test_invalid_arguments_are_rejected_without_a_gpu(lib_path):
+    """Argument validation happens on the host before any CUDA call."""
+    from paper_1607_05210_gb300 import hapod as H
+
+    lib = H._lib
+    out = ctypes.c_void_p()
+    assert lib.hapod_create(None, None, 10, None, ctypes.byref(out)) == H.HAPOD_ERR_INVALID
+    assert "null" in H.hapod_last_error()
+    # two roots -> not a rooted tree
+    par = (ctypes.c_int32 * 3)(-1, -1, 0)
+    cols = (ctypes.c_int64 * 3)(5, 5, 5)
+    tree = H.hapod_tree(3, par, cols)
+    tol = H.hapod_tol(1e-3, 0.5, None, 0, 0)
+    assert lib.hapod_create(ctypes.byref(tree), ctypes.byref(tol), 10, None, ctypes.byref(out)) == H.HAPOD_ERR_TREE
+    # a cycle 1 -> 2 -> 1 not connected to the root
+    par = (ctypes.c_int32 * 3)(-1, 2, 1)
+    tree = H.hapod_tree(3, par, cols)
+    assert lib.hapod_create(ctypes.byref(tree), ctypes.byref(tol), 10, None, ctypes.byref(out)) == H.HAPOD_ERR_TREE
+    # omega outside [0, 1]
+    par = (ctypes.c_int32 * 3)(-1, 0, 0)
+    tree = H.hapod_tree(3, par, cols)
+    bad = H.hapod_tol(1e-3, 1.5, None, 0, 0)
+    assert lib.hapod_create(ctypes.byref(tree), ctypes.byref(bad), 10, None, ctypes.byref(out)) == H.HAPOD_ERR_INVALID
+    assert out.value is None
+    # step entry points
+    assert lib.hapod_gram(7, 10, 3, None, 10, None, None) == H.HAPOD_ERR_INVALID
+    assert lib.hapod_truncate(4, None, -1.0, None, None, None) == H.HAPOD_ERR_INVALID
