@@ -1,0 +1,425 @@
+#!/usr/bin/env python
+"""HAPOD throughput on one GB300: snapshot columns/s and algorithmic GB/s.
+
+Workload (synthetic, seeded): n = 2^20 rows, 64 leaves x 256 snapshot columns of
+the advection-diffusion trajectory u(x, t) = sum_k a_k exp(-nu k^2 t) sin(k(x - c t))
+(32 harmonics, a_k ~ N(0, k^-2), nu = 1e-3, c = 1, t ~ U[0, 1]), balanced binary
+tree of edge depth 6 (L_T = 7), eps = 1e-5 relative (sum_s ||s - P s||^2 <=
+(1e-5 ||X||_F)^2), omega = 0.5.  The inputs (137 GB in FP64, 69 GB in FP32) are
+generated on the device before timing and are larger than L2, so no flush is
+needed between steps.
+
+A step is one full HAPOD through the C ABI: create, push every leaf, result,
+destroy.  The mixed form (FP32 snapshots, tensor-core split-bf16 Gram and modes)
+is the headline when it is available; the FP64 form is reported beside it.
+
+--impl reference times the CPU FP64 oracle on the host cores on a bounded sample
+of the same workload (there is no other reference implementation of the method).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_ROWS = 1 << 20
+LEAVES = 64
+COLS = 256
+SEED = 1607052102
+EPS_REL = 1e-5
+OMEGA = 0.5
+TREE_DEPTH = 6
+METRIC = "HAPOD snapshot columns/s at stated error (eps = 1e-5 rel, omega = 0.5)"
+UNIT = "columns/s"
+WORKLOAD = ("advection-diffusion HAPOD, n=2^20 rows, 64 leaves x 256 snapshots (16384 columns), "
+            "balanced binary tree L_T=7, eps=1e-5 rel, omega=0.5")
+ORACLE_SAMPLE_ROWS = N_ROWS // 16
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p["bf16_tflops"]), "measured"
+    except Exception:
+        return 6800.0, 1900.0, "fallback"
+
+
+FP64_PEAK_TFLOPS = 1.25  # nominal FP64 rate of GB300 (CUDA cores and tensor cores alike)
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.QUERY}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- inputs
+def make_inputs(dtype, device):
+    import numpy as np
+    import torch
+
+    from paper_1607_05210_gb300 import synth
+
+    B = torch.from_numpy(synth.fourier_basis(N_ROWS)).to(device)  # n x 64
+    C = synth.advection_diffusion_coeffs(LEAVES * COLS, SEED)     # 64 x |S|
+    bufs, fro2 = [], 0.0
+    for j in range(LEAVES):
+        Ct = torch.from_numpy(np.ascontiguousarray(C[:, j * COLS:(j + 1) * COLS].T)).to(device)
+        Xt = (Ct @ B.T).to(dtype)  # COLS x n: row i = snapshot i (column-major n x COLS)
+        fro2 += float(torch.sum(Xt.double() ** 2))
+        bufs.append(Xt)
+        del Ct
+    del B
+    torch.cuda.synchronize()
+    return bufs, fro2
+
+
+def tree():
+    from paper_1607_05210_gb300 import synth
+
+    parent = synth.balanced_tree(2, TREE_DEPTH)
+    leaves = synth.leaves_of(parent)
+    cols = [0] * len(parent)
+    for a in leaves:
+        cols[a] = COLS
+    return parent, leaves, cols
+
+
+# ----------------------------------------------------------------- our arm
+def run_form(H, precision, bufs, fro2, steps, warmup, stream, dist_ctx):
+    import torch
+
+    parent, leaves, cols = tree()
+    eps = EPS_REL * math.sqrt(fro2)
+    launches = [0]
+    info = {}
+
+    def step(profile):
+        ctx = H.hapod_create(parent, cols, eps, OMEGA, N_ROWS, precision, stream=stream,
+                             flags=H.HAPOD_FLAG_PROFILE if profile else 0)
+        for i, a in enumerate(leaves):
+            H.hapod_push(ctx, a, bufs[i].t())
+        s, U, st = H.hapod_result(ctx, device=bufs[0].device)
+        if profile:
+            prof = H.hapod_profile(ctx)
+            for k, v in prof.items():
+                d = info.setdefault(k, {"ms": 0.0, "launches": 0, "bytes": 0.0, "flops": 0.0})
+                for f in d:
+                    d[f] += v[f]
+            launches[0] += sum(v["launches"] for v in prof.values())
+            info["_nodes"] = [H.hapod_node_stats(ctx, a) for a in range(len(parent))]
+            info["_k"] = int(s.numel())
+            info["_status"] = int(st)
+        H.hapod_destroy(ctx)
+        return s
+
+    for _ in range(warmup):
+        step(False)
+    torch.cuda.synchronize()
+    dist_ctx.barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for _ in range(steps):
+            step(True)
+        ev1.record(stream)
+    torch.cuda.synchronize()
+    dist_ctx.barrier()
+    ms = ev0.elapsed_time(ev1) / steps
+    ms = dist_ctx.max(ms)
+    # algorithmic bytes of the whole HAPOD (b n (2 m + k) per node)
+    es = 8 if precision == H.HAPOD_FP64 else 4
+    alg_bytes = sum(es * N_ROWS * (2 * st_["m"] + max(0, st_["k"])) for st_ in info["_nodes"] if st_["m"] > 0)
+    per = {k: {f: v[f] / steps for f in v} for k, v in info.items() if not k.startswith("_")}
+    return {"ms": ms, "alg_bytes": alg_bytes, "steps": per, "launches_per_step": launches[0] // steps,
+            "k": info["_k"], "status": info["_status"],
+            "max_inner_k": max(st_["k"] for st_ in info["_nodes"] if st_["level"] > 1 and st_["level"] < 7),
+            "leaf_k": max(st_["k"] for st_ in info["_nodes"] if st_["level"] == 1)}
+
+
+def run_e2e(H, precision, host_bufs, dev_bufs, fro2, steps, stream):
+    """Same HAPOD through the public API from pinned host buffers: H2D of every leaf and
+    D2H of the result (sigma, modes) inside the timed region."""
+    import torch
+
+    parent, leaves, cols = tree()
+    eps = EPS_REL * math.sqrt(fro2)
+    h2d = sum(b.numel() * b.element_size() for b in host_bufs)
+    d2h = [0]
+
+    def step():
+        ctx = H.hapod_create(parent, cols, eps, OMEGA, N_ROWS, precision, stream=stream)
+        for i, a in enumerate(leaves):
+            dev_bufs[i].copy_(host_bufs[i], non_blocking=True)
+            H.hapod_push(ctx, a, dev_bufs[i].t())
+        s, U, st = H.hapod_result(ctx, device=dev_bufs[0].device)
+        Uh = U.cpu()
+        d2h[0] = Uh.numel() * Uh.element_size() + s.numel() * 8
+        H.hapod_destroy(ctx)
+
+    step()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for _ in range(steps):
+            step()
+        ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / steps
+    return {"value": LEAVES * COLS / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h[0],
+            "ms_per_step": ms}
+
+
+def roofline(res, precision, H, hbm, bf16):
+    steps = res["steps"]
+    dom = max((k for k in steps if steps[k]["launches"] > 0), key=lambda k: steps[k]["ms"])
+    d = steps[dom]
+    if precision == H.HAPOD_FP64 and dom in ("gram", "modes"):
+        ach = d["flops"] / (d["ms"] / 1e3) / 1e12
+        return dom, {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                     "kernel": f"{dom} (FP64 FMA pipe; peak = nominal GB300 FP64 rate)"}
+    if dom in ("gram", "modes"):
+        ach = d["bytes"] / (d["ms"] / 1e3) / 1e9
+        return dom, {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                     "traffic": None, "kernel": dom}
+    return dom, {"bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None,
+                 "kernel": dom}
+
+
+# ----------------------------------------------------------------- oracle
+def oracle_sample():
+    """A 256-column leaf of the same trajectory type at n/16 rows, FP64, with the leaf
+    tolerance of the tree (Thm. cor:hapod_bound) computed from the sample's own RMS
+    snapshot norm."""
+    import oracle
+    from paper_1607_05210_gb300 import synth
+
+    X = synth.advection_diffusion(ORACLE_SAMPLE_ROWS, COLS, SEED)
+    parent, leaves, cols = tree()
+    eps_star = EPS_REL * math.sqrt(float((X * X).sum()) / COLS)
+    return X, oracle.tolerances(parent, cols, eps_star, OMEGA)[leaves[0]]
+
+
+def time_oracle(steps: int, warmup: int):
+    import oracle
+
+    X, eps_leaf = oracle_sample()
+    for _ in range(warmup):
+        oracle.pod(X, eps_leaf)
+    t = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        oracle.pod(X, eps_leaf)
+        t.append(time.perf_counter() - t0)
+    sec = statistics.median(t)
+    # cols/s of a full-length leaf: the oracle's cost is linear in the rows (QR + n-length reflectors)
+    value = COLS / (sec * (N_ROWS / ORACLE_SAMPLE_ROWS))
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return value, sec, cores
+
+
+# ----------------------------------------------------------------- distributed
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+
+            dist.init_process_group("nccl" if self._cuda() else "gloo")
+            self.pg = dist
+
+    @staticmethod
+    def _cuda():
+        import torch
+
+        return torch.cuda.is_available()
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, v: float) -> float:
+        if not self.pg:
+            return v
+        import torch
+
+        t = torch.tensor([v], dtype=torch.float64, device="cuda" if self._cuda() else "cpu")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--forms", default="mixed,fp64", help="comma list; the first available is the headline")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+    dist_ctx = Dist()
+
+    if args.impl == "reference":
+        if dist_ctx.rank != 0:
+            dist_ctx.close()
+            return
+        value, sec, cores = time_oracle(args.steps, args.warmup)
+        sample = (f"oracle POD (Householder QR + one-sided Jacobi, FP64) of one 256-column leaf at n/16 = "
+                  f"{ORACLE_SAMPLE_ROWS} rows per step, {sec:.2f} s; columns/s scaled to full-length leaves")
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic", "config": {"workload": WORKLOAD, "form": "cpu oracle"},
+                          "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                           "sample": sample},
+                          "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        dist_ctx.close()
+        return
+
+    import torch
+
+    torch.cuda.set_device(dist_ctx.local)
+    device = torch.device("cuda", dist_ctx.local)
+    from paper_1607_05210_gb300 import hapod as H
+
+    hbm, bf16, peak_src = _peaks()
+    stream = torch.cuda.Stream(device)
+    results = {}
+    forms = [f.strip() for f in args.forms.split(",") if f.strip()]
+    clocks = None
+    e2e = None
+    for form in forms:
+        precision = H.HAPOD_MIXED_BF16X3 if form == "mixed" else H.HAPOD_FP64
+        dtype = torch.float32 if form == "mixed" else torch.float64
+        bufs, fro2 = make_inputs(dtype, device)
+        sampler = ClockSampler(dist_ctx.local) if not results else None
+        try:
+            res = run_form(H, precision, bufs, fro2, args.steps, args.warmup, stream, dist_ctx)
+        except H.HapodError as e:
+            if sampler:
+                sampler.stop()
+            results[form] = {"unavailable": str(e)}
+            del bufs
+            torch.cuda.empty_cache()
+            continue
+        if sampler:
+            clocks = sampler.stop()
+        res["precision"] = precision
+        results[form] = res
+        if e2e is None and not args.no_e2e:
+            try:
+                host = [torch.empty_like(b, device="cpu").pin_memory() for b in bufs]
+                for h, b in zip(host, bufs):
+                    h.copy_(b)
+                e2e = run_e2e(H, precision, host, bufs, fro2, max(1, min(args.steps, 2)), stream)
+                e2e["form"] = form
+                del host
+            except (RuntimeError, MemoryError) as ex:
+                e2e = {"value": None, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                       "note": f"host buffers unavailable: {str(ex)[:120]}"}
+        del bufs
+        torch.cuda.empty_cache()
+
+    head_form = next((f for f in forms if "ms" in results.get(f, {})), None)
+    if head_form is None:
+        raise SystemExit(f"no form ran: {results}")
+    head = results[head_form]
+    total_cols = LEAVES * COLS * dist_ctx.world
+    value = total_cols / (head["ms"] / 1e3)
+    dom, roof = roofline(head, head["precision"], H, hbm, bf16)
+    roof["peak_source"] = peak_src if roof["bound"] == "hbm" else "nominal"
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist_ctx.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if head["precision"] == H.HAPOD_FP64 else "f32 in / bf16x3 tensor-core products / f64 sums",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "form": head_form, "parallelism": f"replicas x{dist_ctx.world}",
+                   "l2": "inputs larger than L2 (no flush needed)"},
+        "gb_per_s": head["alg_bytes"] / (head["ms"] / 1e3) / 1e9 * dist_ctx.world,
+        "roofline": roof,
+        "gpu_launches": head["launches_per_step"] * args.steps,
+        "clocks": clocks,
+        "e2e": e2e,
+        "result": {"k_root": head["k"], "max_leaf_k": head["leaf_k"], "max_inner_k": head["max_inner_k"],
+                   "status": head["status"]},
+        "step_ms": {k: v["ms"] for k, v in head["steps"].items()},
+        "forms": {f: ({"value": total_cols / (r["ms"] / 1e3), "ms_per_step": r["ms"],
+                       "gb_per_s": r["alg_bytes"] / (r["ms"] / 1e3) / 1e9 * dist_ctx.world,
+                       "step_ms": {k: v["ms"] for k, v in r["steps"].items()}} if "ms" in r else r)
+                  for f, r in results.items()},
+    }
+    if dist_ctx.rank == 0 and dist_ctx.world == 1 and not args.no_cpu_baseline:
+        v, sec, cores = time_oracle(1, 0)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"one 256-column leaf at n/16 rows ({sec:.2f} s), scaled to full leaves"}
+    if dist_ctx.rank == 0:
+        print(json.dumps(line))
+    dist_ctx.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -82,6 +82,7 @@ typedef struct {
  * max_pending_leaves: 0 = process the tree once every leaf has been pushed (or at
  * hapod_result); k > 0 = process as soon as k pushed leaves are waiting, which
  * bounds the device memory held by the library for streamed input (Sec. 3.4).
+ * flags: see HAPOD_FLAG_PROFILE below.
  */
 typedef struct {
   double eps;
@@ -89,7 +90,12 @@ typedef struct {
   const double* eps_override;
   int32_t precision;
   int32_t max_pending_leaves;
+  int32_t flags;  /* HAPOD_FLAG_* bits */
 } hapod_tol;
+
+/* flags: HAPOD_FLAG_PROFILE records CUDA events on the context's stream around
+ * every kernel launch so that hapod_profile can report per-step device time. */
+#define HAPOD_FLAG_PROFILE 1
 
 typedef struct hapod_ctx hapod_ctx;
 
@@ -142,6 +148,24 @@ hapod_status hapod_push(hapod_ctx* ctx, int32_t leaf, const void* dev_snapshots,
  */
 hapod_status hapod_result(hapod_ctx* ctx, int64_t* k_out, double* sigma_host, void* dev_modes,
                           int64_t ld_modes);
+
+/* Per-step accounting of a context created with HAPOD_FLAG_PROFILE.  Index:
+ * 0 Gram, 1 eigensolve, 2 truncation, 3 eigenvector gather, 4 modes, 5 copies
+ * (pass-through inputs and parked child outputs).  ms = summed device time
+ * between CUDA events recorded on the context stream around the step's launches;
+ * launches = kernel launches; bytes/flops = algorithmic volume of the step as
+ * defined by the method (Gram: b n m bytes and n m (m + 1) flops per node; modes:
+ * b n (m + k) bytes and 2 n m k flops; b = element size), zero where not defined. */
+typedef struct {
+  double ms[6];
+  int64_t launches[6];
+  double bytes[6];
+  double flops[6];
+} hapod_profile_info;
+
+/* Accumulated profile since hapod_create (zeros without HAPOD_FLAG_PROFILE).
+ * Synchronises the context stream.  Errors: INVALID. */
+hapod_status hapod_profile(hapod_ctx* ctx, hapod_profile_info* info);
 
 /* Node statistics; valid at any time.  Errors: INVALID (node out of range). */
 hapod_status hapod_node_stats(const hapod_ctx* ctx, int32_t node, hapod_node_info* info);

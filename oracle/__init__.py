@@ -9,7 +9,7 @@ Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 (brute-force SVD on tiny inputs, prescribed spectra, the advection-diffusion
 closed form, the theorems of Sec. 3.3 and hand-derived tolerance values).
 """
-from .hapod import (  # noqa: F401
+from .core import (  # noqa: F401
     gram,
     svd,
     pod,

@@ -53,7 +53,48 @@ cudaError_t get_pool(int dev, cudaMemPool_t* out) {
   return cudaSuccess;
 }
 
+// Per-step CUDA-event accounting (HAPOD_FLAG_PROFILE).
+struct Prof {
+  struct Rec {
+    int step;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> spare;
+  hapod_profile_info acc;
+  Prof() { memset(&acc, 0, sizeof(acc)); }
+  cudaEvent_t get() {
+    if (!spare.empty()) {
+      cudaEvent_t e = spare.back();
+      spare.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  // call after the stream has been synchronised
+  void resolve() {
+    for (Rec& r : pending) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) acc.ms[r.step] += ms;
+      spare.push_back(r.a);
+      spare.push_back(r.b);
+    }
+    pending.clear();
+    cudaGetLastError();
+  }
+  ~Prof() {
+    for (Rec& r : pending) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    for (cudaEvent_t e : spare) cudaEventDestroy(e);
+  }
+};
+
 struct Env {
+  Prof* prof = nullptr;
   int dev = 0;
   cudaStream_t s = nullptr;
   cudaMemPool_t pool = nullptr;
@@ -85,6 +126,23 @@ struct Env {
   }
   void release(void* p) {
     if (p) cudaFreeAsync(p, s);
+  }
+  // profiling brackets around a step's launches (no-ops without a profiler)
+  cudaEvent_t tic() {
+    if (!prof) return nullptr;
+    cudaEvent_t e = prof->get();
+    if (e) cudaEventRecord(e, s);
+    return e;
+  }
+  void toc(cudaEvent_t a, int step, int launches, double bytes, double flops) {
+    if (!prof || !a) return;
+    cudaEvent_t b = prof->get();
+    if (!b) return;
+    cudaEventRecord(b, s);
+    prof->pending.push_back({step, a, b});
+    prof->acc.launches[step] += launches;
+    prof->acc.bytes[step] += bytes;
+    prof->acc.flops[step] += flops;
   }
   template <typename T>
   T* upload(const std::vector<T>& v, const char* what) {
@@ -209,12 +267,18 @@ bool step_gram(Env& env, int precision, std::vector<Work*>& ws) {
   bool ok = jobs_d && items_d && red_d && (partials || !plan.partial_bytes) && (fp64 || errf);
   if (ok) {
     cudaError_t e;
-    if (fp64) {
-      e = launch_gram_f64(jobs_d, items_d, plan.num_items, red_d, plan.num_reduce, partials, env.s);
-    } else {
-      ok = env.cuda(cudaMemsetAsync(errf, 0, sizeof(int), env.s), "memset");
-      e = launch_gram_tc(jobs_d, items_d, plan.num_items, red_d, plan.num_reduce, partials, errf, env.s);
+    if (!fp64) ok = env.cuda(cudaMemsetAsync(errf, 0, sizeof(int), env.s), "memset");
+    double bytes = 0, flops = 0;
+    for (Work* w : ws) {
+      bytes += (double)elem_size(precision) * w->n * w->m;
+      flops += (double)w->n * w->m * (w->m + 1);
     }
+    cudaEvent_t t0 = env.tic();
+    if (fp64)
+      e = launch_gram_f64(jobs_d, items_d, plan.num_items, red_d, plan.num_reduce, partials, env.s);
+    else
+      e = launch_gram_tc(jobs_d, items_d, plan.num_items, red_d, plan.num_reduce, partials, errf, env.s);
+    env.toc(t0, 0, 1 + (plan.num_reduce > 0), bytes, flops);
     ok = ok && env.cuda(e, "gram launch");
   }
   env.release(jobs_d);
@@ -260,6 +324,7 @@ bool step_eig(Env& env, bool fp64, std::vector<Work*>& ws, NodeResult* res_d) {
   EigJob* jobs_d = env.upload(jobs, "upload eig jobs");
   if (!jobs_d) return false;
   bool ok = true;
+  cudaEvent_t t0 = env.tic();
   if (!small_map.empty()) {
     int2* map_d = env.upload(small_map, "upload eig map");
     ok = map_d && env.cuda(launch_eig(fp64, jobs_d, map_d, (int)small_map.size(), false, kMaxSweeps, env.s),
@@ -273,6 +338,7 @@ bool step_eig(Env& env, bool fp64, std::vector<Work*>& ws, NodeResult* res_d) {
                            "jacobi cooperative launch");
     env.release(map_d);
   }
+  env.toc(t0, 1, (small_map.empty() ? 0 : 1) + (int)big_maps.size(), 0.0, 0.0);
   env.release(jobs_d);
   return ok;
 }
@@ -289,7 +355,9 @@ bool step_truncate(Env& env, std::vector<Work*>& ws, NodeResult* res_d) {
     jobs[i].pad = 0;
   }
   TruncJob* d = env.upload(jobs, "upload trunc jobs");
+  cudaEvent_t t0 = env.tic();
   bool ok = d && env.cuda(launch_truncate(d, (int)jobs.size(), env.s), "truncate launch");
+  env.toc(t0, 2, 1, 0.0, 0.0);
   env.release(d);
   return ok;
 }
@@ -351,7 +419,9 @@ bool run_pod_back(Env& env, int precision, std::vector<Work*>& ws) {
     gj.push_back(g);
   }
   GatherJob* gd = env.upload(gj, "upload gather jobs");
+  cudaEvent_t tg = env.tic();
   bool ok = gd && env.cuda(launch_gather(fp64, gd, (int)gj.size(), env.s), "gather launch");
+  env.toc(tg, 3, 1, 0.0, 0.0);
   env.release(gd);
   if (!ok) return false;
   const int tr = modes_tile_rows(fp64), tc = modes_tile_cols(fp64);
@@ -377,12 +447,22 @@ bool run_pod_back(Env& env, int precision, std::vector<Work*>& ws) {
   }
   ModesJob* md = env.upload(mj, "upload modes jobs");
   if (!md) return false;
+  double bytes = 0, flops = 0;
+  const size_t es = fp64 ? sizeof(double) : sizeof(float);
+  for (Work* w : act) {
+    bytes += (double)es * w->n * (w->m + w->res.k);
+    flops += 2.0 * w->n * w->m * w->res.k;
+  }
   if (fp64) {
+    cudaEvent_t t0 = env.tic();
     ok = env.cuda(launch_modes_f64(md, (int)mj.size(), blocks, env.s), "modes launch");
+    env.toc(t0, 4, 1, bytes, flops);
   } else {
     int* errf = (int*)env.alloc(sizeof(int), "alloc flag");
-    ok = errf && env.cuda(cudaMemsetAsync(errf, 0, sizeof(int), env.s), "memset") &&
-         env.cuda(launch_modes_tc(md, (int)mj.size(), blocks, errf, env.s), "modes launch");
+    ok = errf && env.cuda(cudaMemsetAsync(errf, 0, sizeof(int), env.s), "memset");
+    cudaEvent_t t0 = env.tic();
+    ok = ok && env.cuda(launch_modes_tc(md, (int)mj.size(), blocks, errf, env.s), "modes launch");
+    env.toc(t0, 4, 1, bytes, flops);
     env.release(errf);
   }
   env.release(md);
@@ -421,6 +501,7 @@ struct NodeRT {
 
 struct hapod_ctx {
   Env env;
+  Prof* prof = nullptr;
   int64_t n = 0;
   int precision = HAPOD_FP64;
   size_t esize = 8;
@@ -568,9 +649,11 @@ bool run_batch(hapod_ctx* c, const std::vector<int>& batch) {
         }
       }
     } else {
+      cudaEvent_t t0 = env.tic();
       ok = env.cuda(cudaMemcpy2DAsync(dst, col_bytes, A.in, (size_t)A.in_ld * c->esize, col_bytes, (size_t)A.m,
                                       cudaMemcpyDeviceToDevice, env.s),
                     "copy pass-through snapshots");
+      env.toc(t0, 5, 0, 2.0 * col_bytes * A.m, 0.0);
     }
   }
   if (ok) ok = run_pod_back(env, c->precision, compute);
@@ -739,9 +822,14 @@ hapod_status hapod_create(const hapod_tree* tree, const hapod_tol* tol, int64_t 
   c->precision = tol->precision;
   c->esize = elem_size(tol->precision);
   c->max_pending = tol->max_pending_leaves;
+  if (tol->flags & HAPOD_FLAG_PROFILE) {
+    c->prof = new (std::nothrow) Prof();
+    c->env.prof = c->prof;
+  }
   if (!init_env(c->env, stream)) {
     g_thread_error = c->env.err;
     hapod_status st = c->env.code;
+    delete c->prof;
     delete c;
     return st;
   }
@@ -811,7 +899,18 @@ hapod_status hapod_result(hapod_ctx* c, int64_t* k_out, double* sigma_host, void
   }
   if (sigma_host && R.k > 0) memcpy(sigma_host, R.sigma.data(), sizeof(double) * R.k);
   if (!c->env.cuda(cudaStreamSynchronize(c->env.s), "synchronize")) return ctx_fail(c);
+  if (c->prof) c->prof->resolve();
   return c->warning;
+}
+
+hapod_status hapod_profile(hapod_ctx* c, hapod_profile_info* info) {
+  if (!c || !info) return HAPOD_ERR_INVALID;
+  memset(info, 0, sizeof(*info));
+  if (!c->prof) return HAPOD_OK;
+  if (!c->env.cuda(cudaStreamSynchronize(c->env.s), "synchronize")) return ctx_fail(c);
+  c->prof->resolve();
+  *info = c->prof->acc;
+  return HAPOD_OK;
 }
 
 hapod_status hapod_node_stats(const hapod_ctx* c, int32_t node, hapod_node_info* info) {
@@ -841,6 +940,7 @@ void hapod_destroy(hapod_ctx* c) {
   env.release(c->result);
   cudaStreamSynchronize(env.s);
   if (env.pool) cudaMemPoolTrimTo(env.pool, 0);
+  delete c->prof;
   delete c;
 }
 

@@ -49,7 +49,16 @@ class hapod_tree(ctypes.Structure):
 class hapod_tol(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("omega", ctypes.c_double),
                 ("eps_override", ctypes.POINTER(ctypes.c_double)), ("precision", ctypes.c_int32),
-                ("max_pending_leaves", ctypes.c_int32)]
+                ("max_pending_leaves", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+HAPOD_FLAG_PROFILE = 1
+PROFILE_STEPS = ("gram", "eig", "truncate", "gather", "modes", "copy")
+
+
+class hapod_profile_info(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 6), ("launches", ctypes.c_int64 * 6), ("bytes", ctypes.c_double * 6),
+                ("flops", ctypes.c_double * 6)]
 
 
 class hapod_node_info(ctypes.Structure):
@@ -75,6 +84,7 @@ def _load() -> ctypes.CDLL:
         "hapod_push": ([vp, i32, vp, i64, i64], i32),
         "hapod_result": ([vp, pi64, pd, vp, i64], i32),
         "hapod_node_stats": ([vp, i32, ctypes.POINTER(hapod_node_info)], i32),
+        "hapod_profile": ([vp, ctypes.POINTER(hapod_profile_info)], i32),
         "hapod_last_error": ([vp], ctypes.c_char_p),
         "hapod_destroy": ([vp], None),
         "hapod_gram": ([i32, i64, i64, vp, i64, vp, vp], i32),
@@ -91,7 +101,8 @@ def _load() -> ctypes.CDLL:
 
 
 _lib = _load()
-EXPORTED = ("hapod_create", "hapod_push", "hapod_result", "hapod_node_stats", "hapod_last_error", "hapod_destroy",
+EXPORTED = ("hapod_create", "hapod_push", "hapod_result", "hapod_node_stats", "hapod_profile", "hapod_last_error",
+            "hapod_destroy",
             "hapod_gram", "hapod_eig", "hapod_truncate", "hapod_modes", "hapod_pod")
 
 
@@ -126,7 +137,7 @@ class Context:
 
     def __init__(self, parent: Sequence[int], leaf_cols: Sequence[int], eps: float, omega: float, n_rows: int,
                  precision: int = HAPOD_FP64, eps_override: Optional[Sequence[float]] = None,
-                 max_pending_leaves: int = 0, stream: Optional[torch.cuda.Stream] = None):
+                 max_pending_leaves: int = 0, stream: Optional[torch.cuda.Stream] = None, flags: int = 0):
         N = len(parent)
         self._parent = (ctypes.c_int32 * N)(*parent)
         self._cols = (ctypes.c_int64 * N)(*[int(c) for c in leaf_cols])
@@ -134,7 +145,7 @@ class Context:
         tree = hapod_tree(N, self._parent, self._cols)
         tol = hapod_tol(float(eps), float(omega),
                         ctypes.cast(self._ovr, ctypes.POINTER(ctypes.c_double)) if self._ovr else None,
-                        int(precision), int(max_pending_leaves))
+                        int(precision), int(max_pending_leaves), int(flags))
         self.precision = precision
         self.n = int(n_rows)
         self.stream = stream
@@ -155,8 +166,8 @@ class Context:
 
 
 def hapod_create(parent, leaf_cols, eps, omega, n_rows, precision=HAPOD_FP64, eps_override=None,
-                 max_pending_leaves=0, stream=None) -> Context:
-    return Context(parent, leaf_cols, eps, omega, n_rows, precision, eps_override, max_pending_leaves, stream)
+                 max_pending_leaves=0, stream=None, flags=0) -> Context:
+    return Context(parent, leaf_cols, eps, omega, n_rows, precision, eps_override, max_pending_leaves, stream, flags)
 
 
 def hapod_push(ctx: Context, leaf: int, X: torch.Tensor) -> int:
@@ -188,6 +199,14 @@ def hapod_node_stats(ctx: Context, node: int) -> dict:
     info = hapod_node_info()
     _check(_lib.hapod_node_stats(ctx.ctx, int(node), ctypes.byref(info)), ctx.ctx)
     return {f: getattr(info, f) for f, _ in hapod_node_info._fields_}
+
+
+def hapod_profile(ctx: Context) -> dict:
+    """Per-step device time (ms), launches and algorithmic bytes/flops (HAPOD_FLAG_PROFILE)."""
+    info = hapod_profile_info()
+    _check(_lib.hapod_profile(ctx.ctx, ctypes.byref(info)), ctx.ctx)
+    return {name: {"ms": info.ms[i], "launches": info.launches[i], "bytes": info.bytes[i], "flops": info.flops[i]}
+            for i, name in enumerate(PROFILE_STEPS)}
 
 
 def hapod_last_error(ctx: Optional[Context] = None) -> str:

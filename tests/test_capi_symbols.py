@@ -54,7 +54,7 @@ def test_invalid_arguments_are_rejected_without_a_gpu(lib_path):
     par = (ctypes.c_int32 * 3)(-1, -1, 0)
     cols = (ctypes.c_int64 * 3)(5, 5, 5)
     tree = H.hapod_tree(3, par, cols)
-    tol = H.hapod_tol(1e-3, 0.5, None, 0, 0)
+    tol = H.hapod_tol(1e-3, 0.5, None, 0, 0, 0)
     assert lib.hapod_create(ctypes.byref(tree), ctypes.byref(tol), 10, None, ctypes.byref(out)) == H.HAPOD_ERR_TREE
     # a cycle 1 -> 2 -> 1 not connected to the root
     par = (ctypes.c_int32 * 3)(-1, 2, 1)
@@ -63,7 +63,7 @@ def test_invalid_arguments_are_rejected_without_a_gpu(lib_path):
     # omega outside [0, 1]
     par = (ctypes.c_int32 * 3)(-1, 0, 0)
     tree = H.hapod_tree(3, par, cols)
-    bad = H.hapod_tol(1e-3, 1.5, None, 0, 0)
+    bad = H.hapod_tol(1e-3, 1.5, None, 0, 0, 0)
     assert lib.hapod_create(ctypes.byref(tree), ctypes.byref(bad), 10, None, ctypes.byref(out)) == H.HAPOD_ERR_INVALID
     assert out.value is None
     # step entry points

@@ -303,7 +303,7 @@ def test_planted_mistakes_are_caught(monkeypatch):
     wrong = [e * math.sqrt(LT - 1) if p >= 0 else e for e, p in zip(eps, parent)]
     assert sum(e * e for e in wrong) > S * eps_star ** 2
     # (2) dropping one kept mode breaks Thm. hapod_bound at the root
-    real_pod = oracle.hapod.__globals__["pod"]
+    real_pod = oracle.core.pod
 
     def short_pod(Xa, e):
         r = real_pod(Xa, e)
@@ -313,7 +313,7 @@ def test_planted_mistakes_are_caught(monkeypatch):
             r.Y = r.Y[:, :-1]
         return r
 
-    monkeypatch.setitem(oracle.hapod.__globals__, "pod", short_pod)
+    monkeypatch.setattr(oracle.core, "pod", short_pod)
     res = oracle.hapod(parent, data, eps, keep_all=True)
     Q = res[0].Y / res[0].sigma
     assert oracle.projection_error(X, Q) > sum(e * e for e in eps)
