@@ -239,6 +239,26 @@ hapod_status hapod_modes(int32_t precision, int64_t n, int64_t m, const void* X,
 hapod_status hapod_pod(int32_t precision, int64_t n, int64_t m, const void* X, int64_t ldx, double eps,
                        int64_t* N_host, double* sigma, void* Y, int64_t ldy, double* tail_host, void* stream);
 
+/*
+ * hapod_gram_noalloc -- the FP64 Gram G = X^T X of hapod_gram (HAPOD_FP64 form)
+ * for callers that must not allocate device memory while they run: for example
+ * an application whose own allocator already holds nearly all of the GPU's
+ * memory, or a latency-bound pipeline that cannot afford cudaMalloc/cudaFree or
+ * the synchronisation they imply.  The paper has no counterpart to this call; it
+ * is a property of this library's memory handling only.
+ * X: device n x m doubles (ld ldx); G: device m x m doubles, ld = m, both
+ * triangles written.  Nothing is allocated per call: split-K partials go to a
+ * fixed 32 MiB device array inside the library, held on every GPU that loads the
+ * library until the process exits.  Limit: m <= 2816 (the upper triangle of G in
+ * 64 x 64 tiles must fit the array); larger m returns HAPOD_ERR_INVALID with a
+ * message in hapod_last_error(NULL).  All calls share the array: calls whose
+ * work overlaps on the GPU (unordered streams) race on it.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.
+ * Errors: INVALID, CUDA.
+ */
+hapod_status hapod_gram_noalloc(int64_t n, int64_t m, const double* X, int64_t ldx, double* G, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

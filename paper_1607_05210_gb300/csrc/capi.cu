@@ -471,6 +471,8 @@ bool run_pod_back(Env& env, int precision, std::vector<Work*>& ws) {
 
 }  // namespace
 
+void hapod::set_thread_error(const char* msg) { g_thread_error = msg; }
+
 // ====================================================================== context
 struct NodeRT {
   int32_t parent = -1;

@@ -11,6 +11,9 @@ namespace hapod {
 
 constexpr int kNumSMs = 152;  // GB300: 2 dies x 76 SMs (used only as a sizing hint)
 
+// Sets the message hapod_last_error(NULL) returns on the calling thread.
+void set_thread_error(const char* msg);
+
 // Per-node result record written by the device, read back once per batch.
 struct NodeResult {
   int32_t k;        // kept modes

@@ -92,6 +92,7 @@ def _load() -> ctypes.CDLL:
         "hapod_truncate": ([i64, vp, d, pi64, pd, vp], i32),
         "hapod_modes": ([i32, i64, i64, vp, i64, vp, i64, i64, vp, vp, i64, vp], i32),
         "hapod_pod": ([i32, i64, i64, vp, i64, d, pi64, vp, vp, i64, pd, vp], i32),
+        "hapod_gram_noalloc": ([i64, i64, vp, i64, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -103,7 +104,7 @@ def _load() -> ctypes.CDLL:
 _lib = _load()
 EXPORTED = ("hapod_create", "hapod_push", "hapod_result", "hapod_node_stats", "hapod_profile", "hapod_last_error",
             "hapod_destroy",
-            "hapod_gram", "hapod_eig", "hapod_truncate", "hapod_modes", "hapod_pod")
+            "hapod_gram", "hapod_eig", "hapod_truncate", "hapod_modes", "hapod_pod", "hapod_gram_noalloc")
 
 
 def _stream(stream: Optional[torch.cuda.Stream]) -> int:
@@ -225,6 +226,17 @@ def hapod_gram(X: torch.Tensor, precision: int = HAPOD_FP64, stream=None) -> tor
     _check(_lib.hapod_gram(precision, n, m, ctypes.c_void_p(X.data_ptr()), ld, ctypes.c_void_p(G.data_ptr()),
                            ctypes.c_void_p(_stream(stream))))
     return G  # symmetric: row- or column-major alike
+
+
+def hapod_gram_noalloc(X: torch.Tensor, G: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """FP64 Gram without device allocation inside the library (see include/hapod.h);
+    pass a preallocated m x m float64 ``G`` to avoid the allocation here as well."""
+    n, m, ld = _colmajor(X)
+    if G is None:
+        G = torch.empty((m, m), dtype=torch.float64, device=X.device)
+    _check(_lib.hapod_gram_noalloc(n, m, ctypes.c_void_p(X.data_ptr()), ld, ctypes.c_void_p(G.data_ptr()),
+                                   ctypes.c_void_p(_stream(stream))))
+    return G
 
 
 def hapod_eig(G: torch.Tensor, precision: int = HAPOD_FP64, stream=None):
