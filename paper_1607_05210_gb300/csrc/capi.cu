@@ -95,6 +95,7 @@ struct Prof {
 
 struct Env {
   Prof* prof = nullptr;
+  int* err_dev = nullptr;  // bounded-wait error flag of the tensor-core kernels (per batch)
   int dev = 0;
   cudaStream_t s = nullptr;
   cudaMemPool_t pool = nullptr;
@@ -170,6 +171,7 @@ size_t elem_size(int p) { return p == HAPOD_FP64 ? sizeof(double) : sizeof(float
 struct Work {
   const void* X = nullptr;
   int64_t ldx = 0;
+  void* X_tmp = nullptr;  // 16-byte aligned copy for TMA when the input is not
   int64_t n = 0;
   int64_t m = 0;
   double eps = 0.0;
@@ -230,6 +232,8 @@ void free_work(Env& env, std::vector<Work*>& ws) {
     env.release(w->sync);
     env.release(w->sigma);
     env.release(w->Vk);
+    env.release(w->X_tmp);
+    w->X_tmp = nullptr;
     w->G = nullptr;
     w->A = w->V = nullptr;
     w->lam_tmp = w->lambda = w->sigma = w->Vk = nullptr;
@@ -255,19 +259,29 @@ bool step_gram(Env& env, int precision, std::vector<Work*>& ws) {
   int4 *items = nullptr, *reduce = nullptr;
   GramPlan plan;
   const int tile = fp64 ? 64 : 128;
-  plan_gram(jobs.data(), (int)jobs.size(), tile, fp64 ? 256 : 1024, fp64 ? 4 * kNumSMs : 2 * kNumSMs, &items,
-            &reduce, &plan);
+  // concurrent CTAs: four 256-thread FP64 CTAs per SM, one tensor-core CTA per SM;
+  // items of at least 256 (FP64) / 2048 (tensor-core) rows
+  plan_gram(jobs.data(), (int)jobs.size(), tile, fp64 ? 256 : 2048, fp64 ? 4 * kNumSMs : kNumSMs, &items, &reduce,
+            &plan, !fp64);
   std::vector<int4> it(items, items + plan.num_items), rd(reduce, reduce + plan.num_reduce);
   free(items);
+  std::vector<CUtensorMap> maps;
+  if (!fp64) {
+    maps.resize(ws.size());
+    for (size_t i = 0; i < ws.size(); ++i)
+      if (!encode_colmajor_f32(&maps[i], ws[i]->X, ws[i]->n, ws[i]->m, ws[i]->ldx, gram_tc_rows_per_stage(), 128,
+                               true))
+        return env.fail(HAPOD_ERR_CUDA, "cuTensorMapEncodeTiled failed for a Gram input");
+  }
   GramJob* jobs_d = env.upload(jobs, "upload gram jobs");
   int4* items_d = env.upload(it, "upload gram items");
   int4* red_d = env.upload(rd, "upload gram reduce");
+  CUtensorMap* maps_d = fp64 ? nullptr : env.upload(maps, "upload tensor maps");
   double* partials = plan.partial_bytes ? (double*)env.alloc(plan.partial_bytes, "alloc gram partials") : nullptr;
-  int* errf = fp64 ? nullptr : (int*)env.alloc(sizeof(int), "alloc flag");
-  bool ok = jobs_d && items_d && red_d && (partials || !plan.partial_bytes) && (fp64 || errf);
+  int* errf = fp64 ? nullptr : env.err_dev;
+  bool ok = jobs_d && items_d && red_d && (partials || !plan.partial_bytes) && (fp64 || (errf && maps_d));
   if (ok) {
     cudaError_t e;
-    if (!fp64) ok = env.cuda(cudaMemsetAsync(errf, 0, sizeof(int), env.s), "memset");
     double bytes = 0, flops = 0;
     for (Work* w : ws) {
       bytes += (double)elem_size(precision) * w->n * w->m;
@@ -277,15 +291,15 @@ bool step_gram(Env& env, int precision, std::vector<Work*>& ws) {
     if (fp64)
       e = launch_gram_f64(jobs_d, items_d, plan.num_items, red_d, plan.num_reduce, partials, env.s);
     else
-      e = launch_gram_tc(jobs_d, items_d, plan.num_items, red_d, plan.num_reduce, partials, errf, env.s);
+      e = launch_gram_tc(jobs_d, maps_d, items_d, plan.num_items, red_d, plan.num_reduce, partials, errf, env.s);
     env.toc(t0, 0, 1 + (plan.num_reduce > 0), bytes, flops);
     ok = ok && env.cuda(e, "gram launch");
   }
   env.release(jobs_d);
   env.release(items_d);
   env.release(red_d);
+  env.release(maps_d);
   env.release(partials);
-  env.release(errf);
   return ok;
 }
 
@@ -367,16 +381,34 @@ bool run_pod_front(Env& env, int precision, std::vector<Work*>& ws) {
   if (ws.empty()) return true;
   const bool fp64 = precision == HAPOD_FP64;
   if (!alloc_work(env, ws, fp64)) return false;
-  NodeResult* res_d = (NodeResult*)env.alloc(sizeof(NodeResult) * ws.size(), "alloc results");
+  if (!fp64) {
+    // TMA reads need a 16-byte aligned base and pitch; copy the rare input that has neither
+    for (Work* w : ws) {
+      if (tma_compatible_f32(w->X, w->ldx)) continue;
+      const int64_t ld = (w->n + 31) / 32 * 32;
+      w->X_tmp = env.alloc(sizeof(float) * ld * w->m, "alloc aligned input");
+      if (!w->X_tmp) return false;
+      if (!env.cuda(cudaMemcpy2DAsync(w->X_tmp, ld * sizeof(float), w->X, w->ldx * sizeof(float),
+                                      w->n * sizeof(float), w->m, cudaMemcpyDeviceToDevice, env.s),
+                    "copy input for TMA"))
+        return false;
+      w->X = w->X_tmp;
+      w->ldx = ld;
+    }
+  }
+  NodeResult* res_d = (NodeResult*)env.alloc(sizeof(NodeResult) * ws.size() + sizeof(int) * 4, "alloc results");
   if (!res_d) return false;
-  bool ok = env.cuda(cudaMemsetAsync(res_d, 0, sizeof(NodeResult) * ws.size(), env.s), "memset");
+  env.err_dev = reinterpret_cast<int*>(res_d + ws.size());
+  bool ok = env.cuda(cudaMemsetAsync(res_d, 0, sizeof(NodeResult) * ws.size() + sizeof(int) * 4, env.s), "memset");
   ok = ok && step_gram(env, precision, ws);
   ok = ok && step_eig(env, fp64, ws, res_d);
   ok = ok && step_truncate(env, ws, res_d);
   std::vector<NodeResult> res(ws.size());
+  int dev_err = 0;
   if (ok)
     ok = env.cuda(cudaMemcpyAsync(res.data(), res_d, sizeof(NodeResult) * ws.size(), cudaMemcpyDeviceToHost, env.s),
-                  "read back results");
+                  "read back results") &&
+         env.cuda(cudaMemcpyAsync(&dev_err, env.err_dev, sizeof(int), cudaMemcpyDeviceToHost, env.s), "read back flag");
   for (Work* w : ws) {
     w->sigma_host.assign((size_t)w->m, 0.0);
     if (ok)
@@ -386,7 +418,9 @@ bool run_pod_front(Env& env, int precision, std::vector<Work*>& ws) {
   }
   ok = ok && env.cuda(cudaStreamSynchronize(env.s), "synchronize");
   env.release(res_d);
+  env.err_dev = nullptr;
   if (!ok) return false;
+  if (dev_err) return env.fail(HAPOD_ERR_TIMEOUT, "device-side wait timed out in the tensor-core Gram kernel");
   for (size_t i = 0; i < ws.size(); ++i) {
     ws[i]->res = res[i];
     ws[i]->sigma_host.resize((size_t)std::max(0, res[i].k));
@@ -424,7 +458,10 @@ bool run_pod_back(Env& env, int precision, std::vector<Work*>& ws) {
   env.toc(tg, 3, 1, 0.0, 0.0);
   env.release(gd);
   if (!ok) return false;
-  const int tr = modes_tile_rows(fp64), tc = modes_tile_cols(fp64);
+  int max_k = 0;
+  for (Work* w : act) max_k = std::max(max_k, w->res.k);
+  const int tr = fp64 ? modes_tile_rows(true) : modes_mixed_rows_per_block(max_k);
+  const int tc = fp64 ? modes_tile_cols(true) : modes_mixed_tile_cols(max_k);
   int64_t blocks = 0;
   for (Work* w : act) {
     ModesJob J;
@@ -458,12 +495,9 @@ bool run_pod_back(Env& env, int precision, std::vector<Work*>& ws) {
     ok = env.cuda(launch_modes_f64(md, (int)mj.size(), blocks, env.s), "modes launch");
     env.toc(t0, 4, 1, bytes, flops);
   } else {
-    int* errf = (int*)env.alloc(sizeof(int), "alloc flag");
-    ok = errf && env.cuda(cudaMemsetAsync(errf, 0, sizeof(int), env.s), "memset");
     cudaEvent_t t0 = env.tic();
-    ok = ok && env.cuda(launch_modes_tc(md, (int)mj.size(), blocks, errf, env.s), "modes launch");
+    ok = env.cuda(launch_modes_mixed(md, (int)mj.size(), blocks, tc, env.s), "modes launch");
     env.toc(t0, 4, 1, bytes, flops);
-    env.release(errf);
   }
   env.release(md);
   return ok;
@@ -505,6 +539,7 @@ struct hapod_ctx {
   Env env;
   Prof* prof = nullptr;
   int64_t n = 0;
+  int64_t ldn = 0;  // leading dimension of library-owned node buffers (n rounded up to 32)
   int precision = HAPOD_FP64;
   size_t esize = 8;
   std::vector<NodeRT> nodes;
@@ -536,7 +571,7 @@ hapod_status ctx_fail(hapod_ctx* c) {
 bool ensure_parent_buffer(hapod_ctx* c, int p) {
   NodeRT& P = c->nodes[p];
   if (P.pbuf) return true;
-  const size_t col_bytes = (size_t)c->n * c->esize;
+  const size_t col_bytes = (size_t)c->ldn * c->esize;
   int64_t cap = 0;
   for (int ch : P.children) cap += std::max<int64_t>(0, c->nodes[ch].k);
   if (cap == 0) return true;
@@ -563,7 +598,7 @@ bool ensure_parent_buffer(hapod_ctx* c, int p) {
 // pointer of its first column (ld = n), or nullptr on allocation failure.
 void* place_output(hapod_ctx* c, int a, const std::vector<int>& batch_children) {
   NodeRT& A = c->nodes[a];
-  const size_t col_bytes = (size_t)c->n * c->esize;
+  const size_t col_bytes = (size_t)c->ldn * c->esize;
   if (A.parent < 0) {
     c->result = c->env.alloc(col_bytes * std::max<int64_t>(1, A.k), "alloc result");
     return c->result;
@@ -581,7 +616,8 @@ void* place_output(hapod_ctx* c, int a, const std::vector<int>& batch_children) 
 
 bool run_batch(hapod_ctx* c, const std::vector<int>& batch) {
   Env& env = c->env;
-  const size_t col_bytes = (size_t)c->n * c->esize;
+  const size_t col_bytes = (size_t)c->n * c->esize;    // bytes of one column
+  const size_t pitch = (size_t)c->ldn * c->esize;      // column pitch of library buffers
   std::vector<Work> works(batch.size());
   std::vector<Work*> compute;
   for (size_t i = 0; i < batch.size(); ++i) {
@@ -636,7 +672,7 @@ bool run_batch(hapod_ctx* c, const std::vector<int>& batch) {
     }
     if (A.eps > 0.0 && A.m > 0) {
       w.Y = dst;
-      w.ldy = c->n;
+      w.ldy = c->ldn;
       if (A.parent < 0) {
         std::vector<double> inv(A.k);
         for (int64_t j = 0; j < A.k; ++j) inv[j] = 1.0 / A.sigma[j];
@@ -652,7 +688,7 @@ bool run_batch(hapod_ctx* c, const std::vector<int>& batch) {
       }
     } else {
       cudaEvent_t t0 = env.tic();
-      ok = env.cuda(cudaMemcpy2DAsync(dst, col_bytes, A.in, (size_t)A.in_ld * c->esize, col_bytes, (size_t)A.m,
+      ok = env.cuda(cudaMemcpy2DAsync(dst, pitch, A.in, (size_t)A.in_ld * c->esize, col_bytes, (size_t)A.m,
                                       cudaMemcpyDeviceToDevice, env.s),
                     "copy pass-through snapshots");
       env.toc(t0, 5, 0, 2.0 * col_bytes * A.m, 0.0);
@@ -682,7 +718,7 @@ bool run_batch(hapod_ctx* c, const std::vector<int>& batch) {
       P.state = 1;
       P.in = P.pbuf;
       P.in_owned = P.pbuf;
-      P.in_ld = c->n;
+      P.in_ld = c->ldn;
       P.m = P.pfill;
       P.pbuf = nullptr;
     }
@@ -821,6 +857,7 @@ hapod_status hapod_create(const hapod_tree* tree, const hapod_tol* tol, int64_t 
     }
   }
   c->n = n_rows;
+  c->ldn = (n_rows + 31) / 32 * 32;
   c->precision = tol->precision;
   c->esize = elem_size(tol->precision);
   c->max_pending = tol->max_pending_leaves;
@@ -894,7 +931,8 @@ hapod_status hapod_result(hapod_ctx* c, int64_t* k_out, double* sigma_host, void
       return HAPOD_ERR_INVALID;
     }
     const size_t col_bytes = (size_t)c->n * c->esize;
-    if (!c->env.cuda(cudaMemcpy2DAsync(dev_modes, (size_t)ld_modes * c->esize, c->result, col_bytes, col_bytes,
+    if (!c->env.cuda(cudaMemcpy2DAsync(dev_modes, (size_t)ld_modes * c->esize, c->result, (size_t)c->ldn * c->esize,
+                                       col_bytes,
                                        (size_t)R.k, cudaMemcpyDeviceToDevice, c->env.s),
                      "copy result"))
       return ctx_fail(c);
@@ -972,7 +1010,34 @@ hapod_status hapod_gram(int32_t precision, int64_t n, int64_t m, const void* X, 
   w.m = m;
   w.G = G;
   std::vector<Work*> ws{&w};
-  if (!step_gram(env, precision, ws)) return step_error(env);
+  if (precision == HAPOD_FP64) {
+    if (!step_gram(env, precision, ws)) return step_error(env);
+    return HAPOD_OK;
+  }
+  // mixed form: aligned input for TMA, device error flag read back here
+  bool ok = true;
+  if (!tma_compatible_f32(X, ldx)) {
+    const int64_t ld = (n + 31) / 32 * 32;
+    w.X_tmp = env.alloc(sizeof(float) * ld * m, "alloc aligned input");
+    ok = w.X_tmp && env.cuda(cudaMemcpy2DAsync(w.X_tmp, ld * sizeof(float), X, ldx * sizeof(float),
+                                               n * sizeof(float), m, cudaMemcpyDeviceToDevice, env.s),
+                             "copy input for TMA");
+    w.X = w.X_tmp;
+    w.ldx = ld;
+  }
+  env.err_dev = ok ? (int*)env.alloc(sizeof(int), "alloc flag") : nullptr;
+  ok = ok && env.err_dev && env.cuda(cudaMemsetAsync(env.err_dev, 0, sizeof(int), env.s), "memset") &&
+       step_gram(env, precision, ws);
+  int dev_err = 0;
+  if (ok) ok = env.cuda(cudaMemcpyAsync(&dev_err, env.err_dev, sizeof(int), cudaMemcpyDeviceToHost, env.s), "read flag");
+  env.release(env.err_dev);
+  env.release(w.X_tmp);
+  ok = env.cuda(cudaStreamSynchronize(env.s), "synchronize") && ok;
+  if (!ok) return step_error(env);
+  if (dev_err) {
+    g_thread_error = "hapod_gram: device-side wait timed out";
+    return HAPOD_ERR_TIMEOUT;
+  }
   return HAPOD_OK;
 }
 
@@ -1066,7 +1131,8 @@ hapod_status hapod_modes(int32_t precision, int64_t n, int64_t m, const void* X,
   Env env;
   if (!init_env(env, stream)) return step_error(env);
   const bool fp64 = precision == HAPOD_FP64;
-  const int tr = modes_tile_rows(fp64), tc = modes_tile_cols(fp64);
+  const int tr = fp64 ? modes_tile_rows(true) : modes_mixed_rows_per_block((int)N);
+  const int tc = fp64 ? modes_tile_cols(true) : modes_mixed_tile_cols((int)N);
   ModesJob J;
   memset(&J, 0, sizeof(J));
   J.X = X;
@@ -1087,14 +1153,10 @@ hapod_status hapod_modes(int32_t precision, int64_t n, int64_t m, const void* X,
   if (!md) return step_error(env);
   const int64_t blocks = (int64_t)J.row_tiles * J.col_tiles;
   bool ok;
-  if (fp64) {
+  if (fp64)
     ok = env.cuda(launch_modes_f64(md, 1, blocks, env.s), "modes launch");
-  } else {
-    int* errf = (int*)env.alloc(sizeof(int), "alloc flag");
-    ok = errf && env.cuda(cudaMemsetAsync(errf, 0, sizeof(int), env.s), "memset") &&
-         env.cuda(launch_modes_tc(md, 1, blocks, errf, env.s), "modes launch");
-    env.release(errf);
-  }
+  else
+    ok = env.cuda(launch_modes_mixed(md, 1, blocks, tc, env.s), "modes launch");
   env.release(md);
   if (!ok) return step_error(env);
   return HAPOD_OK;

@@ -15,15 +15,31 @@
 namespace hapod {
 
 void plan_gram(GramJob* jobs, int njobs, int tile, int min_rows_per_split, int target_items, int4** items_out,
-               int4** reduce_out, GramPlan* plan) {
+               int4** reduce_out, GramPlan* plan, bool split_major) {
   int64_t total_tiles = 0;
   for (int j = 0; j < njobs; ++j) {
     const int t = (jobs[j].m + tile - 1) / tile;
     jobs[j].tiles = t;
     total_tiles += (int64_t)t * (t + 1) / 2;
   }
-  // one split count for the batch, enough items to fill the GPU a few times
-  int64_t splits = total_tiles > 0 ? (target_items + total_tiles - 1) / total_tiles : 1;
+  // one split count for the batch: `target_items` is the number of CTAs that run at
+  // once; choose s minimising (waves of tiles * s items) / s, i.e. the time of the
+  // batch when every item costs 1/s, so that no nearly empty last wave is left over
+  int64_t max_n = 1;
+  for (int j = 0; j < njobs; ++j) max_n = std::max<int64_t>(max_n, jobs[j].n);
+  const int64_t s_cap =
+      std::max<int64_t>(1, std::min<int64_t>(max_n / std::max(1, min_rows_per_split),
+                                             total_tiles > 0 ? 8 * (int64_t)target_items / total_tiles + 1 : 1));
+  int64_t splits = 1;
+  double best = 1e300;
+  for (int64_t s = 1; s <= s_cap && total_tiles > 0; ++s) {
+    const double waves = (double)((total_tiles * s + target_items - 1) / target_items);
+    const double cost = waves / (double)s;
+    if (cost < best * (1.0 - 1e-9)) {
+      best = cost;
+      splits = s;
+    }
+  }
   std::vector<int4> items, reduce;
   int64_t item = 0;
   for (int j = 0; j < njobs; ++j) {
@@ -31,7 +47,7 @@ void plan_gram(GramJob* jobs, int njobs, int tile, int min_rows_per_split, int t
     const int64_t max_splits = std::max<int64_t>(1, J.n / std::max(1, min_rows_per_split));
     int64_t s = std::max<int64_t>(1, std::min(splits, max_splits));
     int64_t rps = (J.n + s - 1) / s;
-    rps = ((rps + 31) / 32) * 32;
+    rps = ((rps + 63) / 64) * 64;  // whole 64-row stages (tensor-core form) / 32-row chunks (FP64)
     s = std::max<int64_t>(1, (J.n + rps - 1) / rps);
     J.splits = (int32_t)s;
     J.rows_per_split = rps;
@@ -42,6 +58,11 @@ void plan_gram(GramJob* jobs, int njobs, int tile, int min_rows_per_split, int t
         for (int sp = 0; sp < s; ++sp) items.push_back(make_int4(j, ti, tj, sp));
         item += s;
       }
+  }
+  if (split_major) {
+    // consecutive items = the tiles of one row range, so that CTAs running together
+    // share their column panels through L2 (the partial slot is not the item index)
+    std::stable_sort(items.begin(), items.end(), [](const int4& a, const int4& b) { return a.w < b.w; });
   }
   plan->tile = tile;
   plan->num_items = (int)items.size();
@@ -134,15 +155,23 @@ __global__ void __launch_bounds__(256) gram_f64_tiles(const GramJob* __restrict_
 }  // namespace
 
 // Sum the split partials of one tile in split order and write both triangles.
-// Shared by both Gram forms (tile = 64 or 128).
+// Shared by both Gram forms (tile = 64 or 128).  Each tile is spread over
+// kReduceChunks CTAs (a contiguous slice of its elements each) so that a tile with
+// many splits does not serialise on one SM.
+constexpr int kReduceChunks = 16;
+
 template <int TILE>
 __global__ void __launch_bounds__(256) gram_reduce(const GramJob* __restrict__ jobs, const int4* __restrict__ reduce,
                                                    const double* __restrict__ partials) {
-  const int4 rd = reduce[blockIdx.x];
+  const int4 rd = reduce[blockIdx.x / kReduceChunks];
+  const int chunk = blockIdx.x % kReduceChunks;
   const GramJob J = jobs[rd.x];
   const int i0 = rd.y * TILE, j0 = rd.z * TILE;
-  for (int e = threadIdx.x; e < TILE * TILE; e += blockDim.x) {
+  const bool diag = rd.y == rd.z;
+  constexpr int kPer = TILE * TILE / kReduceChunks;
+  for (int e = chunk * kPer + threadIdx.x; e < (chunk + 1) * kPer; e += blockDim.x) {
     const int a = e / TILE, b = e % TILE;
+    if (diag && a > b) continue;  // one writer per symmetric pair: G stays exactly symmetric
     double s = 0.0;
     for (int sp = 0; sp < J.splits; ++sp) s += partials[((size_t)rd.w + sp) * TILE * TILE + e];
     const int gi = i0 + a, gj = j0 + b;
@@ -156,10 +185,11 @@ __global__ void __launch_bounds__(256) gram_reduce(const GramJob* __restrict__ j
 cudaError_t launch_gram_reduce(int tile, const GramJob* jobs_dev, const int4* reduce_dev, int num_reduce,
                                const double* partials, cudaStream_t s) {
   if (num_reduce <= 0) return cudaSuccess;
+  const unsigned grid = (unsigned)num_reduce * kReduceChunks;
   if (tile == 64)
-    gram_reduce<64><<<num_reduce, 256, 0, s>>>(jobs_dev, reduce_dev, partials);
+    gram_reduce<64><<<grid, 256, 0, s>>>(jobs_dev, reduce_dev, partials);
   else if (tile == 128)
-    gram_reduce<128><<<num_reduce, 256, 0, s>>>(jobs_dev, reduce_dev, partials);
+    gram_reduce<128><<<grid, 256, 0, s>>>(jobs_dev, reduce_dev, partials);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();

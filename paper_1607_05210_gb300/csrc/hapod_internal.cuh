@@ -2,6 +2,7 @@
 // Not part of the public ABI (that is include/hapod.h).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -50,18 +51,28 @@ struct GramPlan {
 // Builds the item list on the host; jobs[] must have X, ldx, n, m, G set.
 // Fills tiles, splits, rows_per_split, item_base; items (int4: job, ti, tj, split)
 // and reduce list (int4: job, ti, tj, first item) are appended to the vectors.
+// With split_major the items are ordered by split first (the partial of item
+// (job, ti, tj, split) then lives in slot job.item_base + tile_index * splits + split,
+// tile_index the row-major index of (ti, tj) in the upper triangle); otherwise the
+// slot is the item's own index.
 void plan_gram(GramJob* jobs, int njobs, int tile, int min_rows_per_split, int target_items,
-               int4** items, int4** reduce, GramPlan* plan);
+               int4** items, int4** reduce, GramPlan* plan, bool split_major = false);
 
 // Sum split partials of each reduce-list tile in split order; both triangles.
 cudaError_t launch_gram_reduce(int tile, const GramJob* jobs_dev, const int4* reduce_dev, int num_reduce,
                                const double* partials, cudaStream_t s);
 cudaError_t launch_gram_f64(const GramJob* jobs_dev, const int4* items_dev, int num_items, const int4* reduce_dev,
                             int num_reduce, double* partials, cudaStream_t s);
-// Mixed form (tcgen05, split-bf16).  Returns cudaErrorNotSupported if the
-// device cannot run it.
-cudaError_t launch_gram_tc(const GramJob* jobs_dev, const int4* items_dev, int num_items, const int4* reduce_dev,
-                           int num_reduce, double* partials, int* err_flag, cudaStream_t s);
+// Mixed form (tcgen05 kind::tf32, hi/lo split); maps_dev[j] is the TMA map of job j's
+// X (FP32, box gram_tc_rows_per_stage() rows x 128 columns, 128-byte swizzle);
+// items/reduce as for the FP64 form with tile 128, split-major order.
+cudaError_t launch_gram_tc(const GramJob* jobs_dev, const CUtensorMap* maps_dev, const int4* items_dev, int num_items,
+                           const int4* reduce_dev, int num_reduce, double* partials, int* err_flag, cudaStream_t s);
+int gram_tc_rows_per_stage();
+// TMA needs a 16-byte aligned base and a row pitch that is a multiple of 16 bytes.
+bool tma_compatible_f32(const void* base, int64_t ld);
+bool encode_colmajor_f32(CUtensorMap* out, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows,
+                         int box_cols, bool swizzle128);
 
 // ---------------------------------------------------------------- eig (K2)
 struct EigJob {
@@ -120,8 +131,11 @@ struct ModesJob {
   int32_t col_tiles;
 };
 cudaError_t launch_modes_f64(const ModesJob* jobs_dev, int njobs, int64_t total_blocks, cudaStream_t s);
-cudaError_t launch_modes_tc(const ModesJob* jobs_dev, int njobs, int64_t total_blocks, int* err_flag,
-                            cudaStream_t s);
+// Mixed form (FP32 in/out): one launch covers jobs whose k fit the mode tile kt
+// (kt = modes_mixed_tile_cols(max k)); row tiles are modes_mixed_rows_per_block(max k).
+cudaError_t launch_modes_mixed(const ModesJob* jobs_dev, int njobs, int64_t total_blocks, int kt, cudaStream_t s);
+int modes_mixed_tile_cols(int k);
+int modes_mixed_rows_per_block(int k);
 int modes_tile_rows(bool fp64);
 int modes_tile_cols(bool fp64);
 
