@@ -196,13 +196,17 @@ hapod_status hapod_gram(int32_t precision, int64_t n, int64_t m, const void* X, 
 /*
  * hapod_eig -- eigen-decomposition G = V diag(lambda) V^T of a symmetric positive
  * semidefinite G (device m x m FP64, ld = m), as needed by the method of snapshots
- * (Sec. 2, Remark def:method_of_snapshots).  One-sided cyclic Jacobi with
- * round-robin ordering, FP64 (HAPOD_FP64) or FP32 rotations (mixed form);
- * eigenvalues are Rayleigh quotients v^T G v in FP64, sorted descending, and
- * negative values are set to 0.  lambda: device m doubles.  V: device m x m FP64,
- * ld = m, column j belongs to lambda[j].  *sweeps_host (may be NULL) receives the
- * sweep count.  Synchronises the stream.  Returns WARN_NOCONVERGE if the sweep
- * limit was reached, ERR_NONFINITE for NaN/Inf in G.
+ * (Sec. 2, Remark def:method_of_snapshots).  A diagonally pivoted Cholesky
+ * G = L L^T + S (FP64) stops at the numerical rank r, once trace(S) <= m 2^-53
+ * trace(G) (FP64 form) or 1e-7 trace(G) (mixed form); one-sided Jacobi with
+ * round-robin ordering on the r columns of L (FP64 or FP32 rotations) then gives
+ * L L^T = W W^T with orthogonal columns w_j: eigenvector u_j = w_j / ||w_j||,
+ * eigenvalue lambda_j = u_j^T G u_j in FP64.  lambda: device m doubles, descending,
+ * zero beyond r.
+ * V: device m x m FP64, ld = m, column j belongs to lambda[j]; columns j >= r are
+ * zero.  *sweeps_host (may be NULL) receives the sweep count.  Synchronises the
+ * stream.  Returns WARN_NOCONVERGE if the sweep limit was reached, ERR_NONFINITE
+ * for NaN/Inf in G, ERR_INVALID for m > 13000.
  */
 hapod_status hapod_eig(int32_t precision, int64_t m, const double* G, double* lambda, double* V,
                        int32_t* sweeps_host, void* stream);

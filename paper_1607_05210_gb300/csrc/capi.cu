@@ -182,7 +182,6 @@ struct Work {
   double* lam_tmp = nullptr;
   double* lambda = nullptr;
   int32_t* perm = nullptr;
-  unsigned* sync = nullptr;
   double* sigma = nullptr;
   double* Vk = nullptr;
   // results
@@ -195,28 +194,19 @@ struct Work {
 };
 
 constexpr int kMaxSweeps = 40;
-constexpr int kEigGroupMinM = 512;  // nodes at least this wide get a CTA group
-
-int eig_group_size(int64_t m, int max_coresident) {
-  if (m < kEigGroupMinM) return 1;
-  const int64_t want = (m + 63) / 64;  // ~32 pairs per CTA per step
-  return (int)std::max<int64_t>(1, std::min<int64_t>(want, max_coresident));
-}
 
 bool alloc_work(Env& env, std::vector<Work*>& ws, bool fp64) {
   const size_t t = fp64 ? sizeof(double) : sizeof(float);
   for (Work* w : ws) {
     const size_t mm = (size_t)w->m * w->m;
     w->G = (double*)env.alloc(mm * sizeof(double), "alloc G");
-    w->A = env.alloc(mm * t, "alloc Jacobi A");
-    w->V = env.alloc(mm * t, "alloc Jacobi V");
+    w->A = env.alloc(mm * sizeof(double), "alloc Cholesky factor");
+    w->V = env.alloc(mm * t, "alloc eigenvectors");
     w->lam_tmp = (double*)env.alloc(w->m * sizeof(double), "alloc lambda");
     w->lambda = (double*)env.alloc(w->m * sizeof(double), "alloc lambda");
     w->perm = (int32_t*)env.alloc(w->m * sizeof(int32_t), "alloc perm");
-    w->sync = (unsigned*)env.alloc(8 * sizeof(unsigned), "alloc sync");
     w->sigma = (double*)env.alloc(w->m * sizeof(double), "alloc sigma");
-    if (!w->G || !w->A || !w->V || !w->lam_tmp || !w->lambda || !w->perm || !w->sync || !w->sigma) return false;
-    if (!env.cuda(cudaMemsetAsync(w->sync, 0, 8 * sizeof(unsigned), env.s), "memset")) return false;
+    if (!w->G || !w->A || !w->V || !w->lam_tmp || !w->lambda || !w->perm || !w->sigma) return false;
   }
   return true;
 }
@@ -229,7 +219,6 @@ void free_work(Env& env, std::vector<Work*>& ws) {
     env.release(w->lam_tmp);
     env.release(w->lambda);
     env.release(w->perm);
-    env.release(w->sync);
     env.release(w->sigma);
     env.release(w->Vk);
     env.release(w->X_tmp);
@@ -238,7 +227,6 @@ void free_work(Env& env, std::vector<Work*>& ws) {
     w->A = w->V = nullptr;
     w->lam_tmp = w->lambda = w->sigma = w->Vk = nullptr;
     w->perm = nullptr;
-    w->sync = nullptr;
   }
 }
 
@@ -306,53 +294,29 @@ bool step_gram(Env& env, int precision, std::vector<Work*>& ws) {
 // K2 for every node (w->G -> lambda, perm, V); results land in res_d[i].
 bool step_eig(Env& env, bool fp64, std::vector<Work*>& ws, NodeResult* res_d) {
   if (ws.empty()) return true;
-  int per_sm = 0;
-  // the kernel is launched with eig_threads() threads; one CTA per SM is the safe co-residency bound
-  per_sm = 1;
-  int nsm = kNumSMs;
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, env.dev);
-  const int max_group = std::max(1, nsm * per_sm);
   std::vector<EigJob> jobs(ws.size());
-  std::vector<int2> small_map;
-  std::vector<std::vector<int2>> big_maps;
+  int max_m = 1;
   for (size_t i = 0; i < ws.size(); ++i) {
     Work* w = ws[i];
+    if (w->m > kEigMaxM) return env.fail(HAPOD_ERR_INVALID, "node wider than the eigensolver supports (13000 columns)");
     EigJob& J = jobs[i];
+    memset(&J, 0, sizeof(J));
     J.G = w->G;
     J.A = w->A;
     J.V = w->V;
     J.lam_tmp = w->lam_tmp;
     J.lambda = w->lambda;
     J.perm = w->perm;
-    J.sync = w->sync;
     J.result = res_d + i;
+    J.eps2 = w->eps * w->eps;
     J.m = (int32_t)w->m;
-    J.group = eig_group_size(w->m, max_group);
-    if (J.group == 1) {
-      small_map.push_back(make_int2((int)i, 0));
-    } else {
-      big_maps.emplace_back();
-      for (int r = 0; r < J.group; ++r) big_maps.back().push_back(make_int2((int)i, r));
-    }
+    max_m = std::max(max_m, (int)w->m);
   }
   EigJob* jobs_d = env.upload(jobs, "upload eig jobs");
   if (!jobs_d) return false;
-  bool ok = true;
   cudaEvent_t t0 = env.tic();
-  if (!small_map.empty()) {
-    int2* map_d = env.upload(small_map, "upload eig map");
-    ok = map_d && env.cuda(launch_eig(fp64, jobs_d, map_d, (int)small_map.size(), false, kMaxSweeps, env.s),
-                           "jacobi launch");
-    env.release(map_d);
-  }
-  for (auto& bm : big_maps) {
-    if (!ok) break;
-    int2* map_d = env.upload(bm, "upload eig map");
-    ok = map_d && env.cuda(launch_eig(fp64, jobs_d, map_d, (int)bm.size(), true, kMaxSweeps, env.s),
-                           "jacobi cooperative launch");
-    env.release(map_d);
-  }
-  env.toc(t0, 1, (small_map.empty() ? 0 : 1) + (int)big_maps.size(), 0.0, 0.0);
+  bool ok = env.cuda(launch_eig(fp64, jobs_d, (int)jobs.size(), max_m, kMaxSweeps, env.s), "eigensolver launch");
+  env.toc(t0, 1, 1, 0.0, 0.0);
   env.release(jobs_d);
   return ok;
 }

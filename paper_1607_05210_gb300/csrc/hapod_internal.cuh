@@ -20,9 +20,10 @@ struct NodeResult {
   int32_t k;        // kept modes
   int32_t sweeps;   // Jacobi sweeps
   int32_t status;   // hapod_status
-  int32_t pad;
-  double tail;      // discarded sum of lambda
+  int32_t rank;     // numerical rank found by the pivoted Cholesky
+  double tail;      // discarded sum of lambda (including resid)
   double trace;     // trace(G)
+  double resid;     // trace of the Schur complement left by the pivoted Cholesky
 };
 
 // ---------------------------------------------------------------- Gram (K1)
@@ -77,21 +78,21 @@ bool encode_colmajor_f32(CUtensorMap* out, const void* base, int64_t rows, int64
 // ---------------------------------------------------------------- eig (K2)
 struct EigJob {
   const double* G;     // m x m FP64 input (not modified)
-  void* A;             // m x m work (T), becomes G V
-  void* V;             // m x m work (T), eigenvectors (unsorted)
-  double* lam_tmp;     // m, unsorted Rayleigh quotients
+  void* A;             // m x m FP64 work: pivoted Cholesky factor L
+  void* V;             // m x m work (T): rotated columns, then eigenvectors (unsorted)
+  double* lam_tmp;     // m, unsorted eigenvalues
   double* lambda;      // m, sorted descending, clamped >= 0
   int32_t* perm;       // m, sorted position -> column of V
-  unsigned* sync;      // 8 words, zeroed: barrier count, generation, sweep flags x3, abort
   NodeResult* result;
+  double eps2;         // the node's eps^2 (caps the factorisation's stopping residual)
   int32_t m;
-  int32_t group;       // CTAs cooperating on this job
+  int32_t pad;
 };
-// Blocks: block_map[b] = (job, rank in group).  Jobs with group > 1 need a
-// cooperative launch (co-residency); launch_eig handles that.
-cudaError_t launch_eig(bool fp64, const EigJob* jobs_dev, const int2* block_map_dev, int num_blocks,
-                       bool cooperative, int max_sweeps, cudaStream_t s);
+// One CTA per job; max_m sizes the dynamic shared memory (eig_smem_bytes).
+cudaError_t launch_eig(bool fp64, const EigJob* jobs_dev, int njobs, int max_m, int max_sweeps, cudaStream_t s);
 int eig_threads();
+size_t eig_smem_bytes(int m);
+constexpr int kEigMaxM = 13000;  // dynamic shared memory bound of the eigensolver
 
 // ---------------------------------------------------------------- truncation (K3)
 struct TruncJob {

@@ -1,34 +1,33 @@
 // K2: eigen-decomposition of a node's Gramian G (Sec. 2, Remark
-// def:method_of_snapshots: lambda_k, psi_k of G give the POD).
+// def:method_of_snapshots: lambda_k, psi_k of G give the POD), one CTA per node.
 //
-// Method: one-sided cyclic Jacobi applied to the columns of A := G / trace(G).
-// Plane rotations from the right orthogonalise the columns, A J = G V with V the
-// accumulated rotations; once the columns of G V are mutually orthogonal,
-// V^T G^2 V is diagonal, so V diagonalises the PSD matrix G.  The eigenvalues are
-// taken as Rayleigh quotients lambda_j = v_j^T (G v_j) accumulated in FP64.
-// Pairs follow the round-robin ("circle") ordering: in step t every index is in
-// exactly one pair, so the m/2 rotations of a step touch disjoint columns and run
-// concurrently, one warp per pair; a sweep is m' - 1 steps (m' = m rounded up to
-// even).  A pair is rotated while |a_p.a_q| > tol ||a_p|| ||a_q|| with
-// tol = m * unit roundoff of T; columns whose squared norm is below
-// (1e-3 u)^2 trace(G)^2, far under the rounding level, are treated as zero.
-//
-// T = double for the FP64 form; T = float for the mixed form (FP32 rotations on
-// the FP64-accumulated Gram; the Rayleigh quotients are still FP64 sums).
-//
-// Several CTAs may cooperate on one large node (group > 1): they share the pair
-// list of each step and meet at a software grid barrier whose spin is bounded
-// (~2 s); a timeout sets HAPOD_ERR_TIMEOUT and every CTA returns.  Such groups
-// are launched cooperatively so that all their CTAs are co-resident.
-#include <cooperative_groups.h>
-
+// 1. Rank-revealing factorisation (FP64): diagonally pivoted Cholesky
+//    G = L L^T + S, choosing at step k the largest remaining diagonal of the Schur
+//    complement S and stopping once trace(S) (the sum of its diagonal, S being PSD)
+//    is below min(tol * trace(G), 1e-2 eps^2) (tol * trace(G) without an eps),
+//    tol = the rounding level of the
+//    form's Gram (m 2^-53 for FP64, 1e-7 for the tensor-core form).  trace(S) is
+//    returned as `resid` and added to every tail of the truncation, so the dropped
+//    part is accounted for exactly: no eigenvalue of G exceeds that of L L^T by more
+//    than ||S|| <= trace(S).
+// 2. One-sided Jacobi (Hestenes) on the r columns of L in precision T: plane
+//    rotations from the right make the columns mutually orthogonal, L J = W.  Then
+//    L L^T = W W^T, so the eigenvectors of L L^T are u_j = w_j / ||w_j|| (no
+//    rotation matrix has to be accumulated); the eigenvalues are taken as FP64
+//    Rayleigh quotients u_j^T G u_j with the original G.  Pairs follow the round-robin ("circle") ordering, one warp per
+//    pair, all pairs of a step concurrently; a pair is rotated while
+//    |w_p . w_q| > tol ||w_p|| ||w_q||, tol = m * unit roundoff of T.
+// For the exponentially decaying spectra of snapshot data r is a few tens, so the
+// eigensolve costs O(m r^2) per sweep instead of the O(m^3) of a Jacobi sweep on G.
+// Output: lambda descending (clamped >= 0, zero beyond r), V (T, m x m) with
+// column j = w_j / ||w_j|| for j < r and zero otherwise, perm = sorted order.
 #include "hapod_internal.cuh"
 
 namespace hapod {
 namespace {
 
-constexpr int kThreads = 1024;
-constexpr long long kSpinBudget = 4000000000LL;  // clock64 cycles (~2 s)
+constexpr int kThreads = 512;
+constexpr int kWarps = kThreads / 32;
 
 template <typename T>
 struct Unit;
@@ -64,131 +63,156 @@ __device__ __forceinline__ void rr_pair(int t, int k, int mp, int& p, int& q) {
   }
 }
 
-// Group barrier over `nblocks` CTAs: sync[0] = arrival count, sync[1] =
-// generation, sync[7] = abort.  Returns false if the wait ran out or another CTA
-// aborted; the caller then returns.
-__device__ bool group_barrier(unsigned* sync, unsigned nblocks, NodeResult* res) {
-  __shared__ int ok;
+// Block-wide argmax of d[i] over unchosen i (ties: lowest index) and the block sum
+// of the positive d[i]; every thread receives the results.
+__device__ void argmax_block(const double* d, const unsigned char* chosen, int m, int& p, double& dmax, double& dsum,
+                             double* red_v, int* red_i, double* red_s) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double best = -1.0, sum = 0.0;
+  int bi = -1;
+  for (int i = tid; i < m; i += blockDim.x) {
+    if (chosen[i]) continue;
+    const double v = d[i];
+    if (v > 0.0) sum += v;
+    if (v > best) {
+      best = v;
+      bi = i;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ov > best || (ov == best && oi >= 0 && (bi < 0 || oi < bi))) {
+      best = ov;
+      bi = oi;
+    }
+    sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  }
+  if (lane == 0) {
+    red_v[warp] = best;
+    red_i[warp] = bi;
+    red_s[warp] = sum;
+  }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    ok = 1;
-    volatile unsigned* vgen = sync + 1;
-    volatile unsigned* vabort = sync + 7;
-    const unsigned gen = *vgen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(sync, 1u);
-    if (arrived == nblocks - 1) {
-      sync[0] = 0;
-      __threadfence();
-      atomicAdd(sync + 1, 1u);
-    } else {
-      const long long t0 = clock64();
-      while (*vgen == gen) {
-        if (*vabort) {
-          ok = 0;
-          break;
-        }
-        if (clock64() - t0 > kSpinBudget) {
-          atomicExch(sync + 7, 1u);
-          res->status = HAPOD_ERR_TIMEOUT;
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
+  if (tid == 0) {
+    double b = -1.0, s = 0.0;
+    int i = -1;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      s += red_s[w];
+      if (red_v[w] > b || (red_v[w] == b && red_i[w] >= 0 && (i < 0 || red_i[w] < i))) {
+        b = red_v[w];
+        i = red_i[w];
       }
     }
-    __threadfence();
-    if (*vabort) ok = 0;
+    red_v[0] = b;
+    red_i[0] = i;
+    red_s[0] = s;
   }
   __syncthreads();
-  return ok != 0;
-}
-
-__device__ __forceinline__ bool sync_all(int group, unsigned* sync, NodeResult* res) {
-  if (group == 1) {
-    __syncthreads();
-    return true;
-  }
-  return group_barrier(sync, (unsigned)group, res);
+  p = red_i[0];
+  dmax = red_v[0];
+  dsum = red_s[0];
+  __syncthreads();
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) jacobi_kernel(const EigJob* __restrict__ jobs,
-                                                          const int2* __restrict__ block_map, int max_sweeps) {
-  const int2 bm = block_map[blockIdx.x];
-  const EigJob J = jobs[bm.x];
-  const int rank = bm.y, group = J.group, m = J.m;
+__global__ void __launch_bounds__(kThreads) chol_jacobi_kernel(const EigJob* __restrict__ jobs, int max_sweeps) {
+  const EigJob J = jobs[blockIdx.x];
+  const int m = J.m;
   if (m <= 0) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nwarps_blk = blockDim.x >> 5;
   const double* __restrict__ G = J.G;
-  T* A = static_cast<T*>(J.A);
-  T* V = static_cast<T*>(J.V);
+  double* L = static_cast<double*>(J.A);  // m x m FP64 (first r columns used)
+  T* W = static_cast<T*>(J.V);           // m x m in T: rotated columns, then eigenvectors
   NodeResult* res = J.result;
-
-  // trace (every CTA computes it; m reads)
-  __shared__ double red[32];
+  extern __shared__ double shm[];
+  double* d = shm;                                                         // m
+  double* rowp = shm + m;                                                  // m (row p of L)
+  unsigned char* chosen = reinterpret_cast<unsigned char*>(shm + 2 * m);  // m
+  __shared__ double red_v[kWarps], red_s[kWarps];
+  __shared__ int red_i[kWarps];
   __shared__ int flag_sh;
-  double tr = 0.0;
-  for (int i = tid; i < m; i += blockDim.x) tr += G[(size_t)i * m + i];
-  tr = warp_sum(tr);
-  if (lane == 0) red[warp] = tr;
-  __syncthreads();
-  if (warp == 0) {
-    double v = lane < nwarps_blk ? red[lane] : 0.0;
-    v = warp_sum(v);
-    if (lane == 0) red[0] = v;
-  }
-  __syncthreads();
-  tr = red[0];
-  if (!isfinite(tr) || tr <= 0.0) {
-    // NaN/Inf, or G = 0 (a PSD matrix with zero trace): nothing to rotate
-    if (rank == 0) {
-      for (int i = tid; i < m; i += blockDim.x) {
-        J.lambda[i] = 0.0;
-        J.perm[i] = i;
-      }
-      for (size_t e = tid; e < (size_t)m * m; e += blockDim.x) V[e] = (e % (m + 1) == 0) ? T(1) : T(0);
-      if (tid == 0) {
-        res->sweeps = 0;
-        res->trace = tr;
-        if (!isfinite(tr)) res->status = HAPOD_ERR_NONFINITE;
-      }
-    }
-    return;
-  }
-  const double inv = 1.0 / tr;
-  {
-    const size_t total = (size_t)m * m;
-    const size_t stride = (size_t)group * blockDim.x;
-    for (size_t e = (size_t)rank * blockDim.x + tid; e < total; e += stride) {
-      A[e] = (T)(G[e] * inv);
-      V[e] = (e % (m + 1) == 0) ? T(1) : T(0);
-    }
-  }
-  if (!sync_all(group, J.sync, res)) return;
 
-  const int mp = m + (m & 1), npairs = mp / 2;
-  const int gwarp = rank * nwarps_blk + warp, nwarps = group * nwarps_blk;
-  const T tol = (T)m * Unit<T>::eps();
-  const T negligible = T(1e-6) * Unit<T>::eps() * Unit<T>::eps();  // ||A||_F <= trace(A) = 1
-  int sweep = 0;
-  bool converged = false;
-  for (sweep = 1; sweep <= max_sweeps; ++sweep) {
+  // ---------------- pivoted Cholesky (FP64)
+  if (tid == 0) flag_sh = 0;
+  __syncthreads();
+  for (int i = tid; i < m; i += blockDim.x) {
+    const double gi = G[(size_t)i * m + i];
+    if (!isfinite(gi)) flag_sh = 1;  // NaN/Inf in a column of X reaches its diagonal entry
+    d[i] = gi;
+    chosen[i] = 0;
+  }
+  __syncthreads();
+  int p0;
+  double dmax0, trace;
+  argmax_block(d, chosen, m, p0, dmax0, trace, red_v, red_i, red_s);
+  const bool finite = flag_sh == 0 && isfinite(trace) && isfinite(dmax0);
+  __syncthreads();
+  if (!finite && tid == 0) res->status = HAPOD_ERR_NONFINITE;
+  const double tol = (sizeof(T) == sizeof(double)) ? (double)m * 1.1102230246251565e-16 : 1e-7;
+  const double stop_round = tol * (trace > 0.0 ? trace : 0.0);
+  const double stop = J.eps2 > 0.0 ? fmin(stop_round, 1e-2 * J.eps2) : stop_round;
+  int r = 0;
+  double resid = finite && trace > 0.0 ? trace : 0.0;
+  if (finite && trace > 0.0) {
+    for (int k = 0; k < m; ++k) {
+      int p;
+      double dmax, dsum;
+      argmax_block(d, chosen, m, p, dmax, dsum, red_v, red_i, red_s);
+      resid = dsum;
+      if (p < 0 || !(dmax > 0.0) || dsum <= stop) break;
+      for (int j = tid; j < k; j += blockDim.x) rowp[j] = L[(size_t)j * m + p];  // row p of L
+      __syncthreads();
+      const double piv = sqrt(dmax);
+      const double inv = 1.0 / piv;
+      for (int i = tid; i < m; i += blockDim.x) {
+        double v;
+        if (i == p) {
+          v = piv;
+        } else if (chosen[i]) {
+          v = 0.0;
+        } else {
+          double s = G[(size_t)p * m + i];
+          for (int j = 0; j < k; ++j) s -= L[(size_t)j * m + i] * rowp[j];
+          v = s * inv;
+          d[i] -= v * v;
+        }
+        L[(size_t)k * m + i] = v;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        chosen[p] = 1;
+        d[p] = 0.0;
+      }
+      __syncthreads();
+      r = k + 1;
+      resid = 0.0;
+    }
+  }
+
+  // ---------------- one-sided Jacobi on the r columns (precision T)
+  for (size_t e = tid; e < (size_t)m * m; e += blockDim.x) W[e] = e < (size_t)r * m ? (T)L[e] : T(0);
+  __syncthreads();
+  const int rp = r + (r & 1), npairs = rp / 2;
+  const T rtol = (T)m * Unit<T>::eps();
+  int sweeps = 0;
+  bool converged = (r <= 1);
+  while (!converged && sweeps < max_sweeps) {
+    ++sweeps;
     if (tid == 0) flag_sh = 0;
-    if (group > 1 && rank == 0 && tid == 0) J.sync[2 + (sweep + 1) % 3] = 0u;
     __syncthreads();
     int rotated = 0;
-    for (int t = 0; t < mp - 1; ++t) {
-      for (int k = gwarp; k < npairs; k += nwarps) {
+    for (int t = 0; t < rp - 1; ++t) {
+      for (int k = warp; k < npairs; k += kWarps) {
         int p, q;
-        rr_pair(t, k, mp, p, q);
-        if (p >= m || q >= m) continue;
-        T* ap = A + (size_t)p * m;
-        T* aq = A + (size_t)q * m;
+        rr_pair(t, k, rp, p, q);
+        if (p >= r || q >= r) continue;
+        T* wp = W + (size_t)p * m;
+        T* wq = W + (size_t)q * m;
         T al = 0, be = 0, ga = 0;
         for (int i = lane; i < m; i += 32) {
-          const T x = ap[i], y = aq[i];
+          const T x = wp[i], y = wq[i];
           al = fma(x, x, al);
           be = fma(y, y, be);
           ga = fma(x, y, ga);
@@ -196,8 +220,7 @@ __global__ void __launch_bounds__(kThreads) jacobi_kernel(const EigJob* __restri
         al = warp_sum(al);
         be = warp_sum(be);
         ga = warp_sum(ga);
-        if (ga == T(0) || al <= negligible || be <= negligible) continue;
-        if (fabs(ga) <= tol * sqrt(al * be)) continue;
+        if (ga == T(0) || !(fabs(ga) > rtol * sqrt(al * be))) continue;
         rotated = 1;
         const T zeta = (be - al) / (T(2) * ga);
         // smaller root of t^2 + 2 zeta t - 1 = 0; 1/(2 zeta) once zeta^2 would overflow
@@ -206,60 +229,65 @@ __global__ void __launch_bounds__(kThreads) jacobi_kernel(const EigJob* __restri
         const T c = T(1) / sqrt(T(1) + tt * tt);
         const T s = c * tt;
         for (int i = lane; i < m; i += 32) {
-          const T x = ap[i], y = aq[i];
-          ap[i] = c * x - s * y;
-          aq[i] = s * x + c * y;
-        }
-        T* vp = V + (size_t)p * m;
-        T* vq = V + (size_t)q * m;
-        for (int i = lane; i < m; i += 32) {
-          const T x = vp[i], y = vq[i];
-          vp[i] = c * x - s * y;
-          vq[i] = s * x + c * y;
+          const T x = wp[i], y = wq[i];
+          wp[i] = c * x - s * y;
+          wq[i] = s * x + c * y;
         }
       }
-      if (!sync_all(group, J.sync, res)) return;
+      __syncthreads();
     }
     if (rotated && lane == 0) flag_sh = 1;
     __syncthreads();
-    if (group == 1) {
-      converged = (flag_sh == 0);
-    } else {
-      if (tid == 0 && flag_sh) atomicOr(J.sync + 2 + sweep % 3, 1u);
-      if (!group_barrier(J.sync, (unsigned)group, res)) return;
-      if (tid == 0) flag_sh = ((volatile unsigned*)J.sync)[2 + sweep % 3] != 0u;
-      __syncthreads();
-      converged = (flag_sh == 0);
-    }
-    __syncthreads();  // every thread has read flag_sh before the next sweep resets it
-    if (converged) break;
+    converged = (flag_sh == 0);
+    __syncthreads();
   }
 
-  // Rayleigh quotients lambda_j = v_j . (G v_j), FP64 sums, one warp per column
-  for (int j = gwarp; j < m; j += nwarps) {
-    const T* vj = V + (size_t)j * m;
-    const T* aj = A + (size_t)j * m;
+  // ---------------- normalised eigenvectors u_j = w_j / ||w_j||, then FP64 Rayleigh
+  // quotients lambda_j = u_j^T G u_j against the original G (second order in the
+  // eigenvector error, so the rounding of L and of the rotations enters squared)
+  for (int j = warp; j < m; j += kWarps) {
     double s = 0.0;
-    for (int i = lane; i < m; i += 32) s += (double)vj[i] * (double)aj[i];
-    s = warp_sum(s);
-    if (lane == 0) J.lam_tmp[j] = s * tr;
+    if (j < r) {
+      const T* wj = W + (size_t)j * m;
+      for (int i = lane; i < m; i += 32) s += (double)wj[i] * (double)wj[i];
+      s = warp_sum(s);
+    }
+    if (j < r && s > 0.0) {
+      const double inv = 1.0 / sqrt(s);
+      T* wj = W + (size_t)j * m;
+      for (int i = lane; i < m; i += 32) wj[i] = (T)((double)wj[i] * inv);
+    }
   }
-  if (!sync_all(group, J.sync, res)) return;
-  if (rank != 0) return;
-  // rank sort, descending, ties by index
+  __syncthreads();
+  for (int j = warp; j < m; j += kWarps) {
+    double acc = 0.0;
+    if (j < r) {
+      const T* uj = W + (size_t)j * m;
+      for (int i = lane; i < m; i += 32) {
+        double gi = 0.0;  // (G u_j)_i; G symmetric, column-major
+        for (int l = 0; l < m; ++l) gi = fma(G[(size_t)l * m + i], (double)uj[l], gi);
+        acc = fma((double)uj[i], gi, acc);
+      }
+      acc = warp_sum(acc);
+    }
+    if (lane == 0) J.lam_tmp[j] = acc;
+  }
+  __syncthreads();
   for (int j = tid; j < m; j += blockDim.x) {
     const double lj = J.lam_tmp[j];
-    int r = 0;
+    int rank = 0;
     for (int i = 0; i < m; ++i) {
       const double li = J.lam_tmp[i];
-      r += (li > lj) || (li == lj && i < j);
+      rank += (li > lj) || (li == lj && i < j);
     }
-    J.lambda[r] = lj > 0.0 ? lj : 0.0;
-    J.perm[r] = j;
+    J.lambda[rank] = lj > 0.0 ? lj : 0.0;
+    J.perm[rank] = j;
   }
   if (tid == 0) {
-    res->sweeps = converged ? sweep : max_sweeps;
-    res->trace = tr;
+    res->sweeps = sweeps;
+    res->trace = trace;
+    res->rank = r;
+    res->resid = resid;
     if (!converged && res->status == HAPOD_OK) res->status = HAPOD_WARN_NOCONVERGE;
   }
 }
@@ -268,13 +296,18 @@ __global__ void __launch_bounds__(kThreads) jacobi_kernel(const EigJob* __restri
 
 int eig_threads() { return kThreads; }
 
-cudaError_t launch_eig(bool fp64, const EigJob* jobs_dev, const int2* block_map_dev, int num_blocks,
-                       bool cooperative, int max_sweeps, cudaStream_t s) {
-  if (num_blocks <= 0) return cudaSuccess;
-  void* args[] = {(void*)&jobs_dev, (void*)&block_map_dev, (void*)&max_sweeps};
-  const void* fn = fp64 ? (const void*)jacobi_kernel<double> : (const void*)jacobi_kernel<float>;
-  if (cooperative) return cudaLaunchCooperativeKernel(fn, dim3(num_blocks), dim3(kThreads), args, 0, s);
-  return cudaLaunchKernel(fn, dim3(num_blocks), dim3(kThreads), args, 0, s);
+size_t eig_smem_bytes(int m) { return (size_t)m * (2 * sizeof(double) + 1) + 16; }
+
+cudaError_t launch_eig(bool fp64, const EigJob* jobs_dev, int njobs, int max_m, int max_sweeps, cudaStream_t s) {
+  if (njobs <= 0) return cudaSuccess;
+  const size_t smem = eig_smem_bytes(max_m);
+  const void* fn = fp64 ? (const void*)chol_jacobi_kernel<double> : (const void*)chol_jacobi_kernel<float>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  void* args[] = {(void*)&jobs_dev, (void*)&max_sweeps};
+  return cudaLaunchKernel(fn, dim3(njobs), dim3(kThreads), args, smem, s);
 }
 
 }  // namespace hapod

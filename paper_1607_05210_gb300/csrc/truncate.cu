@@ -1,6 +1,8 @@
 // K3: truncation rule of the POD (Sec. 2, Def. truncated POD and Eq. pod_error):
 // N = min{N' : sum_{j >= N'} lambda_j <= eps^2}, lambda descending (0-based j,
-// inclusive <=), and sigma_j = sqrt(lambda_j) for the kept j < N.
+// inclusive <=), and sigma_j = sqrt(lambda_j) for the kept j < N.  Every tail also
+// carries the residual the eigensolver's factorisation left out (result->resid),
+// so the rank is never smaller than the complete spectrum requires.
 //
 // One warp per node.  Lane l owns a contiguous chunk of the eigenvalues; chunk
 // sums are Kahan-compensated, a suffix scan over lanes (warp shuffles) gives the
@@ -18,6 +20,7 @@ __global__ void __launch_bounds__(128) truncate_kernel(const TruncJob* __restric
   if (w >= njobs) return;
   const TruncJob J = jobs[w];
   const int m = J.m;
+  const double resid = J.result->resid;
   const int chunk = (m + 31) / 32;
   const int b = min(m, lane * chunk), e = min(m, b + chunk);
   // Kahan sum of the chunk, smallest first
@@ -35,10 +38,10 @@ __global__ void __launch_bounds__(128) truncate_kernel(const TruncJob* __restric
     const double v = __shfl_down_sync(0xffffffffu, incl, o);
     if (lane + o < 32) incl += v;
   }
-  const double after = incl - s;
+  const double after = incl - s + resid;
   // walk the chunk: tail(j) = after + sum_{i in [j, e)} lambda_i
-  int first = m;  // tail(m) = 0 <= eps^2 always
-  double tail_first = 0.0;
+  int first = m;  // keep everything unless a shorter prefix qualifies
+  double tail_first = resid;
   double run = after, rc = 0.0;
   if (run <= J.eps2 && e > b) {
     first = e;
@@ -69,7 +72,7 @@ __global__ void __launch_bounds__(128) truncate_kernel(const TruncJob* __restric
   for (int j = lane; j < k; j += 32) J.sigma[j] = sqrt(J.lambda[j]);
   if (lane == 0) {
     J.result->k = k;
-    J.result->tail = (k == m) ? 0.0 : tk;
+    J.result->tail = tk;
   }
 }
 
