@@ -424,8 +424,8 @@ bool run_pod_back(Env& env, int precision, std::vector<Work*>& ws) {
   if (!ok) return false;
   int max_k = 0;
   for (Work* w : act) max_k = std::max(max_k, w->res.k);
-  const int tr = fp64 ? modes_tile_rows(true) : modes_mixed_rows_per_block(max_k);
-  const int tc = fp64 ? modes_tile_cols(true) : modes_mixed_tile_cols(max_k);
+  const int tr = fp64 ? modes_f64_tile_rows(max_k) : modes_mixed_rows_per_block(max_k);
+  const int tc = fp64 ? modes_f64_tile_cols(max_k) : modes_mixed_tile_cols(max_k);
   int64_t blocks = 0;
   for (Work* w : act) {
     ModesJob J;
@@ -456,11 +456,13 @@ bool run_pod_back(Env& env, int precision, std::vector<Work*>& ws) {
   }
   if (fp64) {
     cudaEvent_t t0 = env.tic();
-    ok = env.cuda(launch_modes_f64(md, (int)mj.size(), blocks, env.s), "modes launch");
+    ok = env.cuda(launch_modes_f64(md, (int)mj.size(), blocks, tc, env.s), "modes launch");
     env.toc(t0, 4, 1, bytes, flops);
   } else {
+    bool vec = true;
+    for (const ModesJob& J : mj) vec = vec && tma_compatible_f32(J.X, J.ldx) && tma_compatible_f32(J.Y, J.ldy);
     cudaEvent_t t0 = env.tic();
-    ok = env.cuda(launch_modes_mixed(md, (int)mj.size(), blocks, tc, env.s), "modes launch");
+    ok = env.cuda(launch_modes_mixed(md, (int)mj.size(), blocks, tc, vec, env.s), "modes launch");
     env.toc(t0, 4, 1, bytes, flops);
   }
   env.release(md);
@@ -1095,8 +1097,8 @@ hapod_status hapod_modes(int32_t precision, int64_t n, int64_t m, const void* X,
   Env env;
   if (!init_env(env, stream)) return step_error(env);
   const bool fp64 = precision == HAPOD_FP64;
-  const int tr = fp64 ? modes_tile_rows(true) : modes_mixed_rows_per_block((int)N);
-  const int tc = fp64 ? modes_tile_cols(true) : modes_mixed_tile_cols((int)N);
+  const int tr = fp64 ? modes_f64_tile_rows((int)N) : modes_mixed_rows_per_block((int)N);
+  const int tc = fp64 ? modes_f64_tile_cols((int)N) : modes_mixed_tile_cols((int)N);
   ModesJob J;
   memset(&J, 0, sizeof(J));
   J.X = X;
@@ -1118,9 +1120,10 @@ hapod_status hapod_modes(int32_t precision, int64_t n, int64_t m, const void* X,
   const int64_t blocks = (int64_t)J.row_tiles * J.col_tiles;
   bool ok;
   if (fp64)
-    ok = env.cuda(launch_modes_f64(md, 1, blocks, env.s), "modes launch");
+    ok = env.cuda(launch_modes_f64(md, 1, blocks, tc, env.s), "modes launch");
   else
-    ok = env.cuda(launch_modes_mixed(md, 1, blocks, tc, env.s), "modes launch");
+    ok = env.cuda(launch_modes_mixed(md, 1, blocks, tc, tma_compatible_f32(X, ldx) && tma_compatible_f32(Y, ldy), env.s),
+                  "modes launch");
   env.release(md);
   if (!ok) return step_error(env);
   return HAPOD_OK;

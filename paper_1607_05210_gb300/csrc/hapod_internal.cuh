@@ -131,13 +131,16 @@ struct ModesJob {
   int32_t row_tiles;
   int32_t col_tiles;
 };
-cudaError_t launch_modes_f64(const ModesJob* jobs_dev, int njobs, int64_t total_blocks, cudaStream_t s);
+// FP64 form: tile_cols = modes_f64_tile_cols(max k), row tiles modes_f64_tile_rows(max k).
+cudaError_t launch_modes_f64(const ModesJob* jobs_dev, int njobs, int64_t total_blocks, int tile_cols, cudaStream_t s);
+int modes_f64_tile_cols(int k);
+int modes_f64_tile_rows(int k);
 // Mixed form (FP32 in/out): one launch covers jobs whose k fit the mode tile kt
 // (kt = modes_mixed_tile_cols(max k)); row tiles are modes_mixed_rows_per_block(max k).
-cudaError_t launch_modes_mixed(const ModesJob* jobs_dev, int njobs, int64_t total_blocks, int kt, cudaStream_t s);
+// vec: every job's X, Y bases are 16-byte aligned and ldx, ldy multiples of 4.
+cudaError_t launch_modes_mixed(const ModesJob* jobs_dev, int njobs, int64_t total_blocks, int kt, bool vec,
+                               cudaStream_t s);
 int modes_mixed_tile_cols(int k);
 int modes_mixed_rows_per_block(int k);
-int modes_tile_rows(bool fp64);
-int modes_tile_cols(bool fp64);
 
 }  // namespace hapod

@@ -4,16 +4,17 @@
 // by 1/sigma_j to return phi_j.  Also the gather V_k[:, j] = V[:, perm[j]] that
 // orders the eigenvectors by descending eigenvalue.
 //
-// Tile: 64 rows x 64 modes per CTA, K (= m) in chunks of 32.  Columns of X are
-// contiguous, so a warp reads 32 consecutive rows of one column; thread t owns
-// rows t%16 + 16i and modes t/16 + 16j, so each store instruction writes 16
+// Tile: ROWS x COLS (rows x modes) per CTA with COLS = 16, 32 or 64 chosen from the
+// largest kept rank of the launch (ROWS = 4096 / COLS), so a rank of ~20 does not
+// pay for 64-wide tiles; K (= m) in chunks of 16.  Columns of X are contiguous, so a
+// warp reads 32 consecutive rows of one column; every store instruction writes
 // consecutive rows of one output column.  Bound by the FP64 pipe on GB300.
 #include "hapod_internal.cuh"
 
 namespace hapod {
 namespace {
 
-constexpr int kRows = 64, kCols = 64, kBK = 32;
+constexpr int kBK = 16;
 
 template <typename T>
 __global__ void gather_kernel(const GatherJob* __restrict__ jobs) {
@@ -35,7 +36,12 @@ __device__ __forceinline__ int find_job(const ModesJob* jobs, int njobs, int64_t
   return lo;
 }
 
+// ROWS x COLS output tile, 256 threads as (ROWS/4) x (COLS/4), 4 x 4 outputs each:
+// thread t owns rows t % (ROWS/4) + (ROWS/4) p and modes t / (ROWS/4) + (COLS/4) q.
+template <int ROWS, int COLS>
 __global__ void __launch_bounds__(256) modes_f64_kernel(const ModesJob* __restrict__ jobs, int njobs) {
+  constexpr int TR = ROWS / 4, TC = COLS / 4;
+  static_assert(TR * TC == 256, "256 threads");
   const int64_t b = blockIdx.x + (int64_t)blockIdx.y * gridDim.x;
   const int jb = find_job(jobs, njobs, b);
   const ModesJob J = jobs[jb];
@@ -43,15 +49,15 @@ __global__ void __launch_bounds__(256) modes_f64_kernel(const ModesJob* __restri
   if (local >= (int64_t)J.row_tiles * J.col_tiles) return;
   const int64_t rt = local % J.row_tiles;
   const int ct = (int)(local / J.row_tiles);
-  const int64_t r0 = rt * kRows;
-  const int c0 = ct * kCols;
+  const int64_t r0 = rt * ROWS;
+  const int c0 = ct * COLS;
   const double* __restrict__ X = static_cast<const double*>(J.X);
   double* __restrict__ Y = static_cast<double*>(J.Y);
 
-  __shared__ double Xs[kBK][kRows + 1];
-  __shared__ double Vs[kBK][kCols + 1];
+  __shared__ double Xs[kBK][ROWS + 1];
+  __shared__ double Vs[kBK][COLS + 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int tr = tid & 15, tc = tid >> 4;
+  const int tr = tid % TR, tc = tid / TR;
   double acc[4][4];
 #pragma unroll
   for (int p = 0; p < 4; ++p)
@@ -59,17 +65,17 @@ __global__ void __launch_bounds__(256) modes_f64_kernel(const ModesJob* __restri
     for (int q = 0; q < 4; ++q) acc[p][q] = 0.0;
 
   for (int k0 = 0; k0 < J.m; k0 += kBK) {
-    // X tile: kBK columns x 64 rows; warp w loads columns w, w+8, ...; two rows per lane
+    // X tile: kBK columns x ROWS rows; warp w loads columns w, w + 8 (lanes along rows)
     for (int c = warp; c < kBK; c += 8) {
       const int col = k0 + c;
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
+      for (int h = 0; h < ROWS / 32; ++h) {
         const int64_t r = r0 + lane + 32 * h;
         Xs[c][lane + 32 * h] = (col < J.m && r < J.n) ? X[(size_t)col * J.ldx + r] : 0.0;
       }
     }
-    // V tile: kBK rows (k) x 64 modes
-    for (int e = tid; e < kBK * kCols; e += 256) {
+    // V tile: kBK rows (k) x COLS modes
+    for (int e = tid; e < kBK * COLS; e += 256) {
       const int kk = e % kBK, j = e / kBK;
       const int row = k0 + kk, col = c0 + j;
       Vs[kk][j] = (row < J.m && col < J.k) ? J.Vk[(size_t)col * J.ldv + row] : 0.0;
@@ -80,8 +86,8 @@ __global__ void __launch_bounds__(256) modes_f64_kernel(const ModesJob* __restri
       double a[4], v[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        a[q] = Xs[kk][tr + 16 * q];
-        v[q] = Vs[kk][tc + 16 * q];
+        a[q] = Xs[kk][tr + TR * q];
+        v[q] = Vs[kk][tc + TC * q];
       }
 #pragma unroll
       for (int p = 0; p < 4; ++p)
@@ -92,12 +98,12 @@ __global__ void __launch_bounds__(256) modes_f64_kernel(const ModesJob* __restri
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    const int col = c0 + tc + 16 * q;
+    const int col = c0 + tc + TC * q;
     if (col >= J.k) continue;
     const double sc = J.scale ? J.scale[col] : 1.0;
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
-      const int64_t r = r0 + tr + 16 * p;
+      const int64_t r = r0 + tr + TR * p;
       if (r < J.n) Y[(size_t)col * J.ldy + r] = acc[p][q] * sc;
     }
   }
@@ -105,8 +111,8 @@ __global__ void __launch_bounds__(256) modes_f64_kernel(const ModesJob* __restri
 
 }  // namespace
 
-int modes_tile_rows(bool fp64) { return fp64 ? kRows : 128; }
-int modes_tile_cols(bool fp64) { return fp64 ? kCols : 256; }
+int modes_f64_tile_cols(int k) { return k <= 16 ? 16 : (k <= 32 ? 32 : 64); }
+int modes_f64_tile_rows(int k) { return 4096 / modes_f64_tile_cols(k); }
 
 cudaError_t launch_gather(bool fp64_src, const GatherJob* jobs_dev, int njobs, cudaStream_t s) {
   if (njobs <= 0) return cudaSuccess;
@@ -118,11 +124,17 @@ cudaError_t launch_gather(bool fp64_src, const GatherJob* jobs_dev, int njobs, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_modes_f64(const ModesJob* jobs_dev, int njobs, int64_t total_blocks, cudaStream_t s) {
+cudaError_t launch_modes_f64(const ModesJob* jobs_dev, int njobs, int64_t total_blocks, int tile_cols, cudaStream_t s) {
   if (njobs <= 0 || total_blocks <= 0) return cudaSuccess;
   const int64_t gx = total_blocks < 65535 ? total_blocks : 65535;
   const int64_t gy = (total_blocks + gx - 1) / gx;
-  modes_f64_kernel<<<dim3((unsigned)gx, (unsigned)gy), 256, 0, s>>>(jobs_dev, njobs);
+  const dim3 grid((unsigned)gx, (unsigned)gy);
+  if (tile_cols == 16)
+    modes_f64_kernel<256, 16><<<grid, 256, 0, s>>>(jobs_dev, njobs);
+  else if (tile_cols == 32)
+    modes_f64_kernel<128, 32><<<grid, 256, 0, s>>>(jobs_dev, njobs);
+  else
+    modes_f64_kernel<64, 64><<<grid, 256, 0, s>>>(jobs_dev, njobs);
   return cudaGetLastError();
 }
 
