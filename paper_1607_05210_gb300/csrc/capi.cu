@@ -469,6 +469,81 @@ bool run_pod_back(Env& env, int precision, std::vector<Work*>& ws) {
   return ok;
 }
 
+// Y (n x m, FP32, ld ldx) -> Out = Y M (n x k), M FP64 m x k (ld m): one mixed modes launch.
+bool modes_pass_mixed(Env& env, const void* X, int64_t ldx, int64_t n, int m, const double* M, int k, void* Out,
+                      int64_t ldo) {
+  ModesJob J;
+  memset(&J, 0, sizeof(J));
+  J.X = X;
+  J.ldx = ldx;
+  J.Vk = M;
+  J.ldv = m;
+  J.Y = Out;
+  J.ldy = ldo;
+  J.n = n;
+  J.m = m;
+  J.k = k;
+  J.row_tiles = (int32_t)((n + modes_mixed_rows_per_block(k) - 1) / modes_mixed_rows_per_block(k));
+  J.col_tiles = (k + modes_mixed_tile_cols(k) - 1) / modes_mixed_tile_cols(k);
+  std::vector<ModesJob> mj{J};
+  ModesJob* md = env.upload(mj, "upload modes job");
+  if (!md) return false;
+  const bool vec = tma_compatible_f32(X, ldx) && tma_compatible_f32(Out, ldo);
+  cudaEvent_t t0 = env.tic();
+  bool ok = env.cuda(launch_modes_mixed(md, 1, (int64_t)J.row_tiles * J.col_tiles, modes_mixed_tile_cols(k), vec,
+                                        env.s),
+                     "modes launch");
+  env.toc(t0, 4, 1, 4.0 * n * (m + k), 2.0 * n * m * k);
+  env.release(md);
+  return ok;
+}
+
+// CholQR2 of the root's sigma-scaled modes Y (mixed form): U (orthonormal columns,
+// written to `out`) and refreshed sigma (host).  Sec. 2 footnote of the
+// method-of-snapshots remark: the Gram route loses orthogonality as cond(X)^2.
+bool root_cholqr2(Env& env, const void* Y, int64_t n, int64_t ldn, int k, void* out, std::vector<double>& sigma,
+                  bool* rank_deficient) {
+  const size_t kk = (size_t)k * k;
+  // layout (doubles): W | W2 | R1 | M1 | M | work (4 k^2) | sigma (k)
+  double* W = (double*)env.alloc(sizeof(double) * (9 * kk + k), "alloc CholQR2 work");
+  void* Q1 = env.alloc(sizeof(float) * ldn * k, "alloc CholQR2 Q1");
+  int* flag = (int*)env.alloc(sizeof(int) * 2, "alloc flag");
+  if (!W || !Q1 || !flag) return false;
+  double *W2 = W + kk, *R1 = W + 2 * kk, *M1 = W + 3 * kk, *M = W + 4 * kk, *work = W + 5 * kk;
+  double* sig_d = W + 9 * kk;
+  bool ok = env.cuda(cudaMemsetAsync(flag, 0, sizeof(int) * 2, env.s), "memset");
+  Work g;
+  g.X = Y;
+  g.ldx = ldn;
+  g.n = n;
+  g.m = k;
+  g.G = W;
+  std::vector<Work*> ws{&g};
+  env.err_dev = flag + 1;
+  ok = ok && step_gram(env, HAPOD_MIXED_BF16X3, ws);
+  ok = ok && env.cuda(launch_cholqr_first(W, R1, M1, k, flag, env.s), "cholqr launch");
+  ok = ok && modes_pass_mixed(env, Y, ldn, n, k, M1, k, Q1, ldn);
+  g.X = Q1;
+  g.G = W2;
+  ok = ok && step_gram(env, HAPOD_MIXED_BF16X3, ws);
+  ok = ok && env.cuda(launch_cholqr_second(W2, R1, work, M, sig_d, k, flag, env.s), "cholqr launch");
+  ok = ok && modes_pass_mixed(env, Q1, ldn, n, k, M, k, out, ldn);
+  int hflag[2] = {0, 0};
+  sigma.assign((size_t)k, 0.0);
+  if (ok)
+    ok = env.cuda(cudaMemcpyAsync(sigma.data(), sig_d, sizeof(double) * k, cudaMemcpyDeviceToHost, env.s), "read") &&
+         env.cuda(cudaMemcpyAsync(hflag, flag, sizeof(int) * 2, cudaMemcpyDeviceToHost, env.s), "read") &&
+         env.cuda(cudaStreamSynchronize(env.s), "synchronize");
+  env.err_dev = nullptr;
+  env.release(W);
+  env.release(Q1);
+  env.release(flag);
+  if (!ok) return false;
+  if (hflag[1]) return env.fail(HAPOD_ERR_TIMEOUT, "device-side wait timed out in the tensor-core Gram kernel");
+  *rank_deficient = hflag[0] != 0;
+  return true;
+}
+
 }  // namespace
 
 void hapod::set_thread_error(const char* msg) { g_thread_error = msg; }
@@ -623,6 +698,9 @@ bool run_batch(hapod_ctx* c, const std::vector<int>& batch) {
   // output placement and modes
   bool ok = true;
   std::vector<double*> scales;
+  void* root_tmp = nullptr;
+  Work* root_work = nullptr;
+  int root_node = -1;
   for (size_t i = 0; i < batch.size() && ok; ++i) {
     const int a = batch[i];
     NodeRT& A = c->nodes[a];
@@ -639,7 +717,17 @@ bool run_batch(hapod_ctx* c, const std::vector<int>& batch) {
     if (A.eps > 0.0 && A.m > 0) {
       w.Y = dst;
       w.ldy = c->ldn;
-      if (A.parent < 0) {
+      if (A.parent < 0 && c->precision != HAPOD_FP64 && A.k <= 256) {
+        // mixed form: unscaled Y to a temporary; CholQR2 writes U into the result below
+        root_tmp = env.alloc(pitch * A.k, "alloc root modes");
+        if (!root_tmp) {
+          ok = false;
+          break;
+        }
+        w.Y = root_tmp;
+        root_work = &w;
+        root_node = batch[i];
+      } else if (A.parent < 0) {
         std::vector<double> inv(A.k);
         for (int64_t j = 0; j < A.k; ++j) inv[j] = 1.0 / A.sigma[j];
         w.scale = env.upload(inv, "upload scale");
@@ -661,6 +749,16 @@ bool run_batch(hapod_ctx* c, const std::vector<int>& batch) {
     }
   }
   if (ok) ok = run_pod_back(env, c->precision, compute);
+  if (ok && root_work) {
+    NodeRT& R = c->nodes[root_node];
+    bool deficient = false;
+    ok = root_cholqr2(env, root_tmp, c->n, c->ldn, (int)R.k, c->result, R.sigma, &deficient);
+    if (ok && deficient) {
+      R.status = HAPOD_WARN_BELOW_FLOOR;
+      if (c->warning == HAPOD_OK) c->warning = HAPOD_WARN_BELOW_FLOOR;
+    }
+  }
+  env.release(root_tmp);
   free_work(env, compute);
   for (double* s : scales) env.release(s);
   if (!ok) return false;

@@ -143,4 +143,12 @@ cudaError_t launch_modes_mixed(const ModesJob* jobs_dev, int njobs, int64_t tota
 int modes_mixed_tile_cols(int k);
 int modes_mixed_rows_per_block(int k);
 
+// ---------------------------------------------------------------- CholQR2 (A6, mixed root)
+// R1 = chol(W) (upper, W = Y^T Y), M1 = R1^{-1}; k x k FP64, one CTA.
+cudaError_t launch_cholqr_first(const double* W, double* R1, double* M1, int k, int* flag, cudaStream_t s);
+// R2 = chol(W2), R = R2 R1 = P S Z^T; M = R2^{-1} P (columns by descending S), sigma = S.
+// work: 4 k^2 doubles.  k <= 256.
+cudaError_t launch_cholqr_second(const double* W2, const double* R1, double* work, double* M, double* sigma, int k,
+                                 int* flag, cudaStream_t s);
+
 }  // namespace hapod
