@@ -51,12 +51,14 @@ ORACLE_SAMPLE_ROWS = N_ROWS // 16
 
 
 def _peaks():
+    """(HBM GB/s, bf16 TFLOP/s sustained, source).  The tensor-core kernels run inside a
+    step of seconds, so the sustained bf16 figure is their denominator."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             p = json.load(f)
-        return float(p["hbm_gbs"]), float(p["bf16_tflops"]), "measured"
+        return float(p["hbm_gbs"]), float(p.get("bf16_tflops_sustained", p["bf16_tflops"])), "measured"
     except Exception:
-        return 6800.0, 1900.0, "fallback"
+        return 6800.0, 1700.0, "fallback"
 
 
 FP64_PEAK_TFLOPS = 1.25  # nominal FP64 rate of GB300 (CUDA cores and tensor cores alike)
@@ -183,7 +185,7 @@ def run_form(H, precision, bufs, fro2, steps, warmup, stream, dist_ctx, eps_rel=
     ms = ev0.elapsed_time(ev1) / steps
     ms = dist_ctx.max(ms)
     # algorithmic bytes of the whole HAPOD (b n (2 m + k) per node)
-    es = 8 if precision == H.HAPOD_FP64 else 4
+    es = 4 if precision == H.HAPOD_MIXED_BF16X3 else 8
     alg_bytes = sum(es * N_ROWS * (2 * st_["m"] + max(0, st_["k"])) for st_ in info["_nodes"] if st_["m"] > 0)
     per = {k: {f: v[f] / steps for f in v} for k, v in info.items() if not k.startswith("_")}
     return {"ms": ms, "alg_bytes": alg_bytes, "steps": per, "launches_per_step": launches[0] // steps,
@@ -227,12 +229,25 @@ def run_e2e(H, precision, host_bufs, dev_bufs, fro2, steps, stream):
             "ms_per_step": ms}
 
 
+def f64_alu(precision, H):
+    """Steps that run on the FP64 FMA pipe: every FP64-ALU step, the X V of the digit-slice form."""
+    return precision in (H.HAPOD_FP64, H.HAPOD_FP64_OZAKI)
+
+
 def roofline(res, precision, H, hbm, bf16, dom=None):
     steps = res["steps"]
     if dom is None:
         dom = max((k for k in steps if steps[k]["launches"] > 0), key=lambda k: steps[k]["ms"])
     d = steps[dom]
-    if precision == H.HAPOD_FP64 and dom in ("gram", "modes"):
+    if precision == H.HAPOD_FP64_OZAKI and dom == "gram":
+        # 28 bf16 digit-pair products per FP64 product of the n m (m + 1) / 2 unique Gram
+        # entries (the library reports 2 n m (m + 1) / 2 FP64 flops for the step)
+        ach = 28.0 * d["flops"] / (d["ms"] / 1e3) / 1e12
+        return dom, {"bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16,
+                     "traffic": None,
+                     "kernel": "gram (digit split + tcgen05 bf16 digit-pair MMAs + reduce; 28 pair products "
+                               "per FP64 product; peak = measured sustained bf16)"}
+    if f64_alu(precision, H) and dom in ("gram", "modes"):
         ach = d["flops"] / (d["ms"] / 1e3) / 1e12
         return dom, {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
@@ -320,7 +335,9 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--forms", default="mixed,fp64", help="include 'mixed' to add the mixed-form runs")
+    ap.add_argument("--forms", default="mixed,fp64,oz",
+                    help="comma list of forms: 'oz' (digit-slice FP64, the headline when present), "
+                         "'fp64' (FP64 ALU), 'mixed' (FP32 snapshots at eps = 1e-2)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -356,7 +373,7 @@ def main():
 
     def summarise(r, precision, eps_rel, dom=None):
         d, roof = roofline(r, precision, H, hbm, bf16, dom)
-        roof["peak_source"] = peak_src if roof["bound"] == "hbm" else "nominal"
+        roof["peak_source"] = peak_src if roof["bound"] in ("hbm", "tensor") else "nominal"
         return {"eps_rel": eps_rel, "value": total_cols / (r["ms"] / 1e3), "unit": UNIT, "ms_per_step": r["ms"],
                 "gb_per_s": r["alg_bytes"] / (r["ms"] / 1e3) / 1e9 * dist_ctx.world,
                 "k_root": r["k"], "max_leaf_k": r["leaf_k"], "max_inner_k": r["max_inner_k"],
@@ -375,12 +392,26 @@ def main():
             forms[f"mixed@{MIXED_EPS_REL:g}"] = {"unavailable": str(e)}
         del bufs
         torch.cuda.empty_cache()
-    # FP64 form: headline at the workload tolerance, then at the mixed tolerance
+    # FP64 snapshots: the digit-slice form (headline) and the FP64 ALU form at the
+    # workload tolerance, then the FP64 ALU form at the mixed tolerance
     bufs, fro2 = make_inputs(torch.float64, device)
-    sampler = ClockSampler(dist_ctx.local)
-    head = run_form(H, H.HAPOD_FP64, bufs, fro2, args.steps, args.warmup, stream, dist_ctx, EPS_REL)
-    clocks = sampler.stop()
-    forms[f"fp64@{EPS_REL:g}"] = summarise(head, H.HAPOD_FP64, EPS_REL)
+    head = head_prec = clocks = None
+    if "oz" in args.forms:
+        sampler = ClockSampler(dist_ctx.local)
+        head = run_form(H, H.HAPOD_FP64_OZAKI, bufs, fro2, args.steps, args.warmup, stream, dist_ctx, EPS_REL)
+        clocks = sampler.stop()
+        head_prec = H.HAPOD_FP64_OZAKI
+        forms[f"fp64_ozaki@{EPS_REL:g}"] = summarise(head, H.HAPOD_FP64_OZAKI, EPS_REL)
+    if "fp64" in args.forms or head is None:
+        sampler = ClockSampler(dist_ctx.local)
+        alu = run_form(H, H.HAPOD_FP64, bufs, fro2, args.steps, args.warmup, stream, dist_ctx, EPS_REL)
+        alu_clocks = sampler.stop()
+        forms[f"fp64@{EPS_REL:g}"] = summarise(alu, H.HAPOD_FP64, EPS_REL)
+        if head is None:
+            head, head_prec, clocks = alu, H.HAPOD_FP64, alu_clocks
+        else:
+            forms[f"fp64_ozaki@{EPS_REL:g}"]["speedup_vs_fp64_alu"] = alu["ms"] / head["ms"]
+    head_key = f"fp64_ozaki@{EPS_REL:g}" if head_prec == H.HAPOD_FP64_OZAKI else f"fp64@{EPS_REL:g}"
     if "mixed" in args.forms:
         r2 = run_form(H, H.HAPOD_FP64, bufs, fro2, max(1, min(args.steps, 2)), 1, stream, dist_ctx, MIXED_EPS_REL)
         forms[f"fp64@{MIXED_EPS_REL:g}"] = summarise(r2, H.HAPOD_FP64, MIXED_EPS_REL)
@@ -393,8 +424,8 @@ def main():
             host = [torch.empty(b.shape, dtype=b.dtype, pin_memory=True) for b in bufs]
             for h_, b in zip(host, bufs):
                 h_.copy_(b)
-            e2e = run_e2e(H, H.HAPOD_FP64, host, bufs, fro2, 1, stream)
-            e2e["form"] = f"fp64@{EPS_REL:g}"
+            e2e = run_e2e(H, head_prec, host, bufs, fro2, 1, stream)
+            e2e["form"] = head_key
             del host
         except (RuntimeError, MemoryError) as ex:
             e2e = {"value": None, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
@@ -403,12 +434,12 @@ def main():
     torch.cuda.empty_cache()
 
     value = total_cols / (head["ms"] / 1e3)
-    hs = forms[f"fp64@{EPS_REL:g}"]
+    hs = forms[head_key]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist_ctx.world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "form": "fp64", "parallelism": f"replicas x{dist_ctx.world}",
+        "config": {"workload": WORKLOAD, "form": head_key.split("@")[0], "parallelism": f"replicas x{dist_ctx.world}",
                    "l2": "inputs larger than L2 (no flush needed)"},
         "gb_per_s": hs["gb_per_s"],
         "roofline": hs["roofline"],

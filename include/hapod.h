@@ -22,11 +22,17 @@
  *     from a context call, the context accepts only hapod_node_stats,
  *     hapod_last_error and hapod_destroy.  HAPOD_WARN_* codes are not errors:
  *     the results are produced and the warning is recorded.
- *   - FP64 form: snapshots are IEEE double; all arithmetic is FP64.
- *     Mixed form: snapshots are IEEE float; Gram and X V run on the tensor cores
- *     as split-bf16 products (x = hi + lo, hi*hi + hi*lo + lo*hi) accumulated in
- *     FP32 over short row chunks and summed in FP64; eigensolve, tail sums and
- *     truncation in FP64 arithmetic on FP64 data except where stated.
+ *   - FP64 form (HAPOD_FP64): snapshots are IEEE double; all arithmetic is FP64.
+ *     Digit-slice FP64 form (HAPOD_FP64_OZAKI): snapshots and results as in the
+ *     FP64 form; the Gram is formed on the bf16 tensor cores from an exact
+ *     7-digit base-128 fixed-point representation of each column (relative to a
+ *     power-of-two bound of its largest entry, truncated below 2^-49 of it), with
+ *     integer-exact accumulation and one FP64 rounding per entry.
+ *     Mixed form (HAPOD_MIXED_BF16X3): snapshots are IEEE float; the Gram runs on
+ *     the tensor cores as TF32 hi/lo products (x = hi + lo, hi*hi + hi*lo + lo*hi)
+ *     accumulated in FP32 over short row chunks and summed in FP64, X V in FP32.
+ *     Eigensolve, tail sums and truncation use FP64 arithmetic on FP64 data except
+ *     where stated.
  */
 #ifndef HAPOD_H
 #define HAPOD_H
@@ -51,8 +57,12 @@ typedef enum {
 } hapod_status;
 
 typedef enum {
-  HAPOD_FP64 = 0,           /* double snapshots, FP64 everywhere */
-  HAPOD_MIXED_BF16X3 = 1    /* float snapshots, tensor-core split-bf16 Gram and X V */
+  HAPOD_FP64 = 0,           /* double snapshots, FP64 arithmetic everywhere */
+  HAPOD_MIXED_BF16X3 = 1,   /* float snapshots, tensor-core (TF32 hi/lo split) Gram, FP32 X V */
+  HAPOD_FP64_OZAKI = 2      /* double snapshots and results; the Gram from exact 7-bit digit
+                               products on the bf16 tensor cores (error-free splitting of
+                               Ozaki et al. 2012, integer-exact accumulation, one final FP64
+                               rounding per entry); eigensolver and X V in FP64 */
 } hapod_precision;
 
 /*
@@ -123,7 +133,7 @@ hapod_status hapod_create(const hapod_tree* tree, const hapod_tol* tol, int64_t 
 
 /*
  * hapod_push -- hand leaf `leaf` its snapshots: device matrix n x ncols, leading
- * dimension ld (elements), double for HAPOD_FP64, float for the mixed form.
+ * dimension ld (elements), double for the FP64 forms, float for the mixed form.
  * ncols must equal leaf_cols[leaf].  The caller keeps ownership; the library reads
  * the matrix asynchronously on the context's stream, so it must stay valid and
  * unchanged until that stream has passed the leaf's processing -- guaranteed once
@@ -181,14 +191,16 @@ void hapod_destroy(hapod_ctx* ctx);
  * Single-node steps.  Each runs the same kernels a context uses, on one node,
  * with caller-provided device buffers; workspace is taken from the library's
  * stream-ordered memory pool and returned before the call completes on the
- * stream.  `precision` selects the FP64 or the mixed form as above.
+ * stream.  `precision` selects the form as above.
  * ---------------------------------------------------------------------- */
 
 /*
  * hapod_gram -- Gramian G = X^T X of the method of snapshots (Sec. 2, Remark
  * def:method_of_snapshots: G = (s_i, s_j)_{i,j}).  X: device n x m (ld ldx),
- * double (FP64) or float (mixed).  G: device m x m FP64, ld = m, both triangles
- * written.  Errors: INVALID, CUDA, OOM.
+ * double (FP64 forms) or float (mixed).  G: device m x m FP64, ld = m, both
+ * triangles written; a column holding Inf or NaN makes its row and column of G NaN
+ * in the digit-slice form.  Errors: INVALID, CUDA, OOM, TIMEOUT (tensor-core forms:
+ * a bounded device-side wait ran out).
  */
 hapod_status hapod_gram(int32_t precision, int64_t n, int64_t m, const void* X, int64_t ldx, double* G,
                         void* stream);
@@ -198,7 +210,7 @@ hapod_status hapod_gram(int32_t precision, int64_t n, int64_t m, const void* X, 
  * semidefinite G (device m x m FP64, ld = m), as needed by the method of snapshots
  * (Sec. 2, Remark def:method_of_snapshots).  A diagonally pivoted Cholesky
  * G = L L^T + S (FP64) stops at the numerical rank r, once trace(S) <= m 2^-53
- * trace(G) (FP64 form) or 1e-7 trace(G) (mixed form); one-sided Jacobi with
+ * trace(G) (FP64 forms) or 1e-7 trace(G) (mixed form); one-sided Jacobi with
  * round-robin ordering on the r columns of L (FP64 or FP32 rotations) then gives
  * L L^T = W W^T with orthogonal columns w_j: eigenvector u_j = w_j / ||w_j||,
  * eigenvalue lambda_j = u_j^T G u_j in FP64.  lambda: device m doubles, descending,

@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -163,8 +164,10 @@ bool init_env(Env& env, void* stream) {
   return env.cuda(get_pool(env.dev, &env.pool), "memory pool");
 }
 
-bool valid_precision(int p) { return p == HAPOD_FP64 || p == HAPOD_MIXED_BF16X3; }
-size_t elem_size(int p) { return p == HAPOD_FP64 ? sizeof(double) : sizeof(float); }
+bool valid_precision(int p) { return p == HAPOD_FP64 || p == HAPOD_MIXED_BF16X3 || p == HAPOD_FP64_OZAKI; }
+// FP64 snapshots (the FP64 and digit-slice forms) versus FP32 snapshots (mixed form)
+bool f64_data(int p) { return p != HAPOD_MIXED_BF16X3; }
+size_t elem_size(int p) { return f64_data(p) ? sizeof(double) : sizeof(float); }
 
 // ------------------------------------------------------------- batched steps
 // One node of a batch: its input and the per-node device buffers of the steps.
@@ -230,9 +233,193 @@ void free_work(Env& env, std::vector<Work*>& ws) {
   }
 }
 
+// K1, digit-slice FP64 form: column exponents for every node, then rounds of digit
+// planes (at most oz_digit_cap() bytes at a time; a node taller than that is cut
+// into row chunks) and tensor-core Gram tiles, then one reduce of the split partials.
+// The digit-plane workspace defaults to 4 GiB; the environment variable
+// HAPOD_OZ_WORKSPACE_MB overrides it (read at every call).
+size_t oz_digit_cap() {
+  const char* e = getenv("HAPOD_OZ_WORKSPACE_MB");
+  if (e && *e) {
+    const long long mb = atoll(e);
+    if (mb > 0) return (size_t)mb << 20;
+  }
+  return (size_t)4 << 30;
+}
+
+bool step_gram_oz(Env& env, std::vector<Work*>& ws) {
+  if (ws.empty()) return true;
+  const size_t kOzDigitCap = oz_digit_cap();
+  const int nw = (int)ws.size();
+  std::vector<OzColJob> cj(nw);
+  int64_t total_cols = 0;
+  for (int i = 0; i < nw; ++i) {
+    memset(&cj[i], 0, sizeof(OzColJob));
+    cj[i].X = static_cast<const double*>(ws[i]->X);
+    cj[i].ldx = ws[i]->ldx;
+    cj[i].n = ws[i]->n;
+    cj[i].m = (int32_t)ws[i]->m;
+    cj[i].col_base = total_cols;
+    total_cols += ws[i]->m;
+  }
+  int32_t* exps = (int32_t*)env.alloc(sizeof(int32_t) * std::max<int64_t>(1, total_cols), "alloc exponents");
+  if (!exps) return false;
+  for (int i = 0; i < nw; ++i) cj[i].exps = exps + cj[i].col_base;
+  struct Chunk {
+    int node;
+    int64_t r0, rows;
+    int32_t CGp, RG, tiles, splits, sps;
+    size_t bytes;
+    int64_t slot0;
+  };
+  std::vector<Chunk> chunks;
+  std::vector<int64_t> node_slots(nw, 0);
+  for (int i = 0; i < nw; ++i) {
+    const int32_t CGp = oz_col_groups(ws[i]->m);
+    const size_t row_bytes = (size_t)CGp * 8 * kOzDigits * 2;
+    int64_t R = (int64_t)(kOzDigitCap / row_bytes) / kOzKBlock * kOzKBlock;
+    R = std::max<int64_t>(R, kOzKBlock);
+    for (int64_t r0 = 0; r0 < ws[i]->n; r0 += R) {
+      Chunk c;
+      c.node = i;
+      c.r0 = r0;
+      c.rows = std::min(R, ws[i]->n - r0);
+      c.CGp = CGp;
+      c.RG = (int32_t)oz_row_groups(c.rows);
+      c.tiles = oz_gram_tiles((int32_t)ws[i]->m, CGp);
+      c.bytes = (size_t)c.RG * 8 * row_bytes;
+      c.splits = c.sps = 0;
+      c.slot0 = 0;
+      chunks.push_back(c);
+    }
+  }
+  // rounds: consecutive chunks while the digit planes fit the cap
+  std::vector<std::pair<size_t, size_t>> rounds;
+  size_t max_round = 0;
+  for (size_t a = 0; a < chunks.size();) {
+    size_t b = a, bytes = 0;
+    while (b < chunks.size() && (b == a || bytes + chunks[b].bytes <= kOzDigitCap)) bytes += chunks[b++].bytes;
+    rounds.push_back({a, b});
+    max_round = std::max(max_round, bytes);
+    // splits: about two waves of one CTA per SM over the round's tiles, whole 256-row blocks
+    int64_t T = 0;
+    for (size_t c = a; c < b; ++c) T += chunks[c].tiles;
+    const int64_t want = std::max<int64_t>(1, (2 * kNumSMs) / std::max<int64_t>(1, T));
+    for (size_t c = a; c < b; ++c) {
+      Chunk& C = chunks[c];
+      const int64_t stages = C.RG / 2;
+      const int64_t blk = kOzKBlock / 16;
+      int64_t sps = (stages + want - 1) / want;
+      sps = std::max<int64_t>(blk, (sps + blk - 1) / blk * blk);
+      sps = std::min<int64_t>(sps, (int64_t)1 << 22);  // int64 flush sums stay exact (< 2^26 rows)
+      C.sps = (int32_t)sps;
+      C.splits = (int32_t)((stages + sps - 1) / sps);
+      C.slot0 = node_slots[C.node];
+      node_slots[C.node] += C.splits;
+    }
+    a = b;
+  }
+  std::vector<int64_t> node_base(nw, 0);
+  size_t total_partial = 0;
+  for (int i = 0; i < nw; ++i) {
+    const int64_t mp = (int64_t)oz_col_groups(ws[i]->m) * 8;
+    node_base[i] = (int64_t)total_partial;
+    total_partial += (size_t)node_slots[i] * mp * mp;
+  }
+  OzColJob* cj_d = env.upload(cj, "upload exponent jobs");
+  double* partial = (double*)env.alloc(sizeof(double) * std::max<size_t>(1, total_partial), "alloc gram partials");
+  uint16_t* digits = (uint16_t*)env.alloc(std::max<size_t>(16, max_round), "alloc digit planes");
+  bool ok = cj_d && partial && digits;
+  double bytes = 0, flops = 0;
+  for (Work* w : ws) {
+    bytes += 8.0 * w->n * w->m;
+    flops += (double)w->n * w->m * (w->m + 1);
+  }
+  cudaEvent_t t0 = env.tic();
+  int launches = 0;
+  if (ok) {
+    ok = env.cuda(launch_oz_colmax(cj_d, nw, total_cols, env.s), "exponent launch");
+    ++launches;
+  }
+  std::vector<void*> job_bufs;
+  for (size_t r = 0; r < rounds.size() && ok; ++r) {
+    std::vector<OzSplitJob> sj;
+    std::vector<OzGramJob> gj;
+    size_t off = 0;
+    int64_t threads = 0, items = 0;
+    for (size_t c = rounds[r].first; c < rounds[r].second; ++c) {
+      const Chunk& C = chunks[c];
+      Work* w = ws[C.node];
+      uint16_t* dblk = reinterpret_cast<uint16_t*>(reinterpret_cast<uint8_t*>(digits) + off);
+      off += C.bytes;
+      OzSplitJob S;
+      memset(&S, 0, sizeof(S));
+      S.X = static_cast<const double*>(w->X);
+      S.ldx = w->ldx;
+      S.r0 = C.r0;
+      S.rows = C.rows;
+      S.exps = cj[C.node].exps;
+      S.digits = dblk;
+      S.thread_base = threads;
+      S.m = (int32_t)w->m;
+      S.CGp = C.CGp;
+      threads += (int64_t)C.RG * C.CGp * 8;
+      sj.push_back(S);
+      OzGramJob G;
+      memset(&G, 0, sizeof(G));
+      const int64_t mp = (int64_t)C.CGp * 8;
+      G.digits = dblk;
+      G.exps = cj[C.node].exps;
+      G.partial = partial + node_base[C.node] + (size_t)C.slot0 * mp * mp;
+      G.item_base = items;
+      G.RG = C.RG;
+      G.CGp = C.CGp;
+      G.m = (int32_t)w->m;
+      G.splits = C.splits;
+      G.stages_per_split = C.sps;
+      G.tiles = C.tiles;
+      items += (int64_t)C.splits * C.tiles;
+      gj.push_back(G);
+    }
+    OzSplitJob* sj_d = env.upload(sj, "upload split jobs");
+    OzGramJob* gj_d = env.upload(gj, "upload gram jobs");
+    job_bufs.push_back(sj_d);
+    job_bufs.push_back(gj_d);
+    ok = sj_d && gj_d && env.cuda(launch_oz_split(sj_d, (int)sj.size(), threads, env.s), "digit split launch") &&
+         env.cuda(launch_gram_oz(gj_d, (int)gj.size(), items, env.err_dev, env.s), "gram launch");
+    launches += 2;
+  }
+  if (ok) {
+    std::vector<OzReduceJob> rj(nw);
+    int64_t cols = 0;
+    for (int i = 0; i < nw; ++i) {
+      memset(&rj[i], 0, sizeof(OzReduceJob));
+      rj[i].partial = partial + node_base[i];
+      rj[i].G = ws[i]->G;
+      rj[i].col_base = cols;
+      rj[i].slots = (int32_t)node_slots[i];
+      rj[i].m = (int32_t)ws[i]->m;
+      rj[i].mp = oz_col_groups(ws[i]->m) * 8;
+      cols += ws[i]->m;
+    }
+    OzReduceJob* rj_d = env.upload(rj, "upload reduce jobs");
+    job_bufs.push_back(rj_d);
+    ok = rj_d && env.cuda(launch_oz_reduce(rj_d, nw, cols, env.s), "gram reduce launch");
+    ++launches;
+  }
+  env.toc(t0, 0, launches, bytes, flops);
+  for (void* p : job_bufs) env.release(p);
+  env.release(cj_d);
+  env.release(partial);
+  env.release(digits);
+  env.release(exps);
+  return ok;
+}
+
 // K1 for every node of ws into w->G.
 bool step_gram(Env& env, int precision, std::vector<Work*>& ws) {
   if (ws.empty()) return true;
+  if (precision == HAPOD_FP64_OZAKI) return step_gram_oz(env, ws);
   const bool fp64 = precision == HAPOD_FP64;
   std::vector<GramJob> jobs(ws.size());
   for (size_t i = 0; i < ws.size(); ++i) {
@@ -343,7 +530,7 @@ bool step_truncate(Env& env, std::vector<Work*>& ws, NodeResult* res_d) {
 // Gram + eig + truncation for ws, then read back k, tail, sigma (synchronises).
 bool run_pod_front(Env& env, int precision, std::vector<Work*>& ws) {
   if (ws.empty()) return true;
-  const bool fp64 = precision == HAPOD_FP64;
+  const bool fp64 = f64_data(precision);
   if (!alloc_work(env, ws, fp64)) return false;
   if (!fp64) {
     // TMA reads need a 16-byte aligned base and pitch; copy the rare input that has neither
@@ -398,7 +585,7 @@ bool run_pod_front(Env& env, int precision, std::vector<Work*>& ws) {
 
 // Gather V_k and form Y = X V_k (diag(scale)) into w->Y for every w with k > 0.
 bool run_pod_back(Env& env, int precision, std::vector<Work*>& ws) {
-  const bool fp64 = precision == HAPOD_FP64;
+  const bool fp64 = f64_data(precision);
   std::vector<GatherJob> gj;
   std::vector<ModesJob> mj;
   std::vector<Work*> act;
@@ -717,7 +904,7 @@ bool run_batch(hapod_ctx* c, const std::vector<int>& batch) {
     if (A.eps > 0.0 && A.m > 0) {
       w.Y = dst;
       w.ldy = c->ldn;
-      if (A.parent < 0 && c->precision != HAPOD_FP64 && A.k <= 256) {
+      if (A.parent < 0 && c->precision == HAPOD_MIXED_BF16X3 && A.k <= 256) {
         // mixed form: unscaled Y to a temporary; CholQR2 writes U into the result below
         root_tmp = env.alloc(pitch * A.k, "alloc root modes");
         if (!root_tmp) {
@@ -734,7 +921,7 @@ bool run_batch(hapod_ctx* c, const std::vector<int>& batch) {
         if (!w.scale) ok = false;
         scales.push_back(w.scale);
         // resolution floor of the method of snapshots (Sec. 2 footnote: cond(G) = cond(X)^2)
-        const double u = c->precision == HAPOD_FP64 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
+        const double u = f64_data(c->precision) ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
         if (A.sigma[A.k - 1] < A.sigma[0] * std::sqrt((double)A.m * u)) {
           A.status = HAPOD_WARN_BELOW_FLOOR;
           if (c->warning == HAPOD_OK) c->warning = HAPOD_WARN_BELOW_FLOOR;
@@ -1078,9 +1265,9 @@ hapod_status hapod_gram(int32_t precision, int64_t n, int64_t m, const void* X, 
     if (!step_gram(env, precision, ws)) return step_error(env);
     return HAPOD_OK;
   }
-  // mixed form: aligned input for TMA, device error flag read back here
+  // tensor-core forms: aligned input for TMA (mixed form), device error flag read back here
   bool ok = true;
-  if (!tma_compatible_f32(X, ldx)) {
+  if (precision == HAPOD_MIXED_BF16X3 && !tma_compatible_f32(X, ldx)) {
     const int64_t ld = (n + 31) / 32 * 32;
     w.X_tmp = env.alloc(sizeof(float) * ld * m, "alloc aligned input");
     ok = w.X_tmp && env.cuda(cudaMemcpy2DAsync(w.X_tmp, ld * sizeof(float), X, ldx * sizeof(float),
@@ -1115,7 +1302,7 @@ hapod_status hapod_eig(int32_t precision, int64_t m, const double* G, double* la
   if (m == 0) return HAPOD_OK;
   Env env;
   if (!init_env(env, stream)) return step_error(env);
-  const bool fp64 = precision == HAPOD_FP64;
+  const bool fp64 = f64_data(precision);
   Work w;
   w.m = m;
   std::vector<Work*> ws{&w};
@@ -1194,7 +1381,7 @@ hapod_status hapod_modes(int32_t precision, int64_t n, int64_t m, const void* X,
   if (N == 0 || n == 0) return HAPOD_OK;
   Env env;
   if (!init_env(env, stream)) return step_error(env);
-  const bool fp64 = precision == HAPOD_FP64;
+  const bool fp64 = f64_data(precision);
   const int tr = fp64 ? modes_f64_tile_rows((int)N) : modes_mixed_rows_per_block((int)N);
   const int tc = fp64 ? modes_f64_tile_cols((int)N) : modes_mixed_tile_cols((int)N);
   ModesJob J;

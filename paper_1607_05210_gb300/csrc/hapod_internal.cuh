@@ -75,6 +75,75 @@ bool tma_compatible_f32(const void* base, int64_t ld);
 bool encode_colmajor_f32(CUtensorMap* out, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows,
                          int box_cols, bool swizzle128);
 
+// ---------------------------------------------------------------- Gram, digit-slice FP64 form
+// X (FP64) is represented exactly up to 2^-49 of each column's power-of-two bound
+// 2^E_j by 7 signed 7-bit digits per value (Ozaki et al. 2012 error-free splitting);
+// digit products are exact in bf16 x bf16 -> FP32 tensor-core arithmetic and their
+// level sums (t + u = s) stay exact integers over kOzKBlock rows.
+constexpr int kOzDigits = 7;
+constexpr int kOzKBlock = 256;                 // rows between exact flushes
+constexpr int kOzGroupBytes = kOzDigits * 128; // one 8 x 8 block of all digit planes
+constexpr int32_t kOzNonFinite = 0x7FFFFFFF;   // exponent marker of a column holding Inf / NaN
+
+// Column exponents: exps[j] = E_j with max_i |X_ij| < 2^E_j (kOzNonFinite for Inf/NaN).
+struct OzColJob {
+  const double* X;
+  int64_t ldx;
+  int64_t n;
+  int32_t* exps;
+  int64_t col_base;  // first global column index of this job
+  int32_t m;
+  int32_t pad;
+};
+cudaError_t launch_oz_colmax(const OzColJob* jobs_dev, int njobs, int64_t total_cols, cudaStream_t s);
+
+// Digit planes of rows [r0, r0 + rows) of X into `digits`, layout
+// [row group of 8][column group of 8 (CGp)][digit 7][column % 8][row % 8] (bf16),
+// RG = 2 ceil(rows / 16) row groups; rows >= `rows` and columns >= m are zero.
+struct OzSplitJob {
+  const double* X;
+  int64_t ldx;
+  int64_t r0;
+  int64_t rows;
+  const int32_t* exps;
+  uint16_t* digits;
+  int64_t thread_base;  // first thread of this job (RG * CGp * 8 threads per job)
+  int32_t m;
+  int32_t CGp;          // column groups, a multiple of 16
+};
+cudaError_t launch_oz_split(const OzSplitJob* jobs_dev, int njobs, int64_t total_threads, cudaStream_t s);
+__host__ __device__ inline int64_t oz_row_groups(int64_t rows) { return 2 * ((rows + 15) / 16); }
+__host__ __device__ inline int32_t oz_col_groups(int64_t m) { return (int32_t)(16 * ((m + 127) / 128)); }
+
+// Gram of one digit block: items (split, tile) in split-major order; tile (I, J) =
+// columns [128 I, 128 I + 128) x [64 J, 64 J + 64), J >= 2 I, 64 J < m.  The item
+// writes its FP64 128 x 64 block into partial slot `split` (mp x mp, ld mp, mp = 8 CGp).
+struct OzGramJob {
+  const uint16_t* digits;
+  const int32_t* exps;
+  double* partial;
+  int64_t item_base;
+  int32_t RG;
+  int32_t CGp;
+  int32_t m;
+  int32_t splits;
+  int32_t stages_per_split;  // 16-row stages per split, a multiple of kOzKBlock / 16
+  int32_t tiles;
+};
+int oz_gram_tiles(int32_t m, int32_t CGp);
+cudaError_t launch_gram_oz(const OzGramJob* jobs_dev, int njobs, int64_t total_items, int* err_flag, cudaStream_t s);
+// G (m x m, ld m) = sum of `slots` partials (upper triangle, mirrored).
+struct OzReduceJob {
+  const double* partial;
+  double* G;
+  int64_t col_base;  // first block of this job (one block per column)
+  int32_t slots;
+  int32_t m;
+  int32_t mp;
+  int32_t pad;
+};
+cudaError_t launch_oz_reduce(const OzReduceJob* jobs_dev, int njobs, int64_t total_cols, cudaStream_t s);
+
 // ---------------------------------------------------------------- eig (K2)
 struct EigJob {
   const double* G;     // m x m FP64 input (not modified)

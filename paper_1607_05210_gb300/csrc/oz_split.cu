@@ -1,0 +1,154 @@
+// Digit slices of FP64 snapshots for the tensor-core FP64 form (K1/K4 of the
+// digit-slice form): the error-free splitting of Ozaki, Ogita, Oishi and Rump
+// (2012), "Error-free transformations of matrix multiplication by using fast
+// routines of matrix multiplication and its applications", specialised to a
+// fixed-point representation per column.
+//
+// Column j gets the power-of-two bound 2^E_j > max_i |x_ij|.  Every value is
+// truncated to the fixed-point integer A = floor(|x| 2^(49 - E_j)) < 2^49 and
+// written in balanced base 128 with 7 digits,
+//   A = d_1 2^42 + d_2 2^35 + ... + d_7,   d_1 in [0, 128], d_2..d_7 in [-64, 63],
+// so x = sign(x) 2^E_j sum_t d_t 2^(-7 t) up to the dropped tail (< 2^(E_j - 49)).
+// Every digit is an integer of at most 8 significant bits, exact in bf16.
+//
+// Layout of a digit block (rows [r0, r0 + rows) of one node):
+//   [row group r/8][column group j/8][digit t][j % 8][r % 8]   (bf16)
+// i.e. 8 x 8 core matrices of 16-byte rows, all 7 digits of one 8 x 8 block
+// together (896 bytes).  Read as columns-by-rows it is the K-major no-swizzle UMMA
+// layout of the Gram (K = rows); read as rows-by-columns it is the MN-major layout
+// of X V (K = columns).
+#include "hapod_internal.cuh"
+
+namespace hapod {
+namespace {
+
+constexpr int kThreads = 256;
+// 64 in each of the six lower base-128 digit positions: adding it makes every lower
+// digit non-negative (balanced -> offset digits), the carry lands in d_1.
+constexpr uint64_t kBalance = 64ull * (1ull + (1ull << 7) + (1ull << 14) + (1ull << 21) + (1ull << 28) + (1ull << 35));
+
+__device__ __forceinline__ uint64_t warp_max_u64(uint64_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint64_t w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
+// One block per column: E_j from the largest |x| (compared as bit patterns, which
+// orders non-negative doubles; Inf and NaN patterns are above every finite one).
+__global__ void __launch_bounds__(kThreads) oz_colmax_kernel(const OzColJob* __restrict__ jobs, int njobs) {
+  const int64_t b = blockIdx.x + (int64_t)blockIdx.y * gridDim.x;
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].col_base <= b) lo = mid; else hi = mid - 1;
+  }
+  const OzColJob J = jobs[lo];
+  const int64_t j = b - J.col_base;
+  if (j >= J.m) return;
+  const unsigned long long* col = reinterpret_cast<const unsigned long long*>(J.X + j * J.ldx);
+  uint64_t mx = 0;
+  for (int64_t i = threadIdx.x; i < J.n; i += kThreads) {
+    const uint64_t a = col[i] & 0x7FFFFFFFFFFFFFFFull;
+    mx = a > mx ? a : mx;
+  }
+  mx = warp_max_u64(mx);
+  __shared__ uint64_t red[kThreads / 32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < kThreads / 32; ++w) mx = red[w] > mx ? red[w] : mx;
+    int32_t E;
+    if (mx >= 0x7FF0000000000000ull) {
+      E = kOzNonFinite;
+    } else {
+      // max in [2^(eb-1023), 2^(eb-1022)) for a normal max; below 2^-1022 otherwise
+      const int eb = (int)(mx >> 52);
+      E = eb == 0 ? -1022 : eb - 1022;
+    }
+    J.exps[j] = E;
+  }
+}
+
+// bf16 bit pattern of the digit v = code - bias (|v| <= 128): the float built from the
+// integer code by the 2^23 exponent trick is exact, and so is its upper half.
+__device__ __forceinline__ uint32_t digit_bf16(uint32_t code, float bias, uint32_t sign) {
+  const float f = __uint_as_float(0x4B000000u | code) - bias;
+  return (__float_as_uint(f) >> 16) ^ sign;
+}
+
+// The 7 digits of x (bf16 bit patterns in the low halves).
+__device__ __forceinline__ void oz_digits(double x, int E, uint32_t (&d)[kOzDigits]) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  const uint32_t sign = (uint32_t)(b >> 63) << 15;
+  const int eb = (int)((b >> 52) & 0x7FF);
+  uint64_t mant = b & 0x000FFFFFFFFFFFFFull;
+  if (eb) mant |= 1ull << 52;
+  // |x| = mant 2^(max(eb,1) - 1075); A = floor(|x| 2^(49 - E)) = mant >> sh
+  const int sh = E + 1026 - (eb ? eb : 1);
+  const uint64_t A = (sh < 64 ? (mant >> sh) : 0ull) + kBalance;
+  d[0] = digit_bf16((uint32_t)(A >> 42), 8388608.f, sign);
+#pragma unroll
+  for (int t = 1; t < kOzDigits; ++t)
+    d[t] = digit_bf16((uint32_t)(A >> (7 * (6 - t))) & 127u, 8388672.f, sign);  // 2^23 + 64
+}
+
+// Thread = (row group, column): 8 consecutive rows of one column -> one 16-byte
+// core-matrix row per digit.  Lanes 0..7 of a warp are the 8 columns of one column
+// group, so each digit's stores of those lanes form one 128-byte segment.
+__global__ void __launch_bounds__(kThreads) oz_split_kernel(const OzSplitJob* __restrict__ jobs, int njobs) {
+  const int64_t t = (blockIdx.x + (int64_t)blockIdx.y * gridDim.x) * kThreads + threadIdx.x;
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].thread_base <= t) lo = mid; else hi = mid - 1;
+  }
+  const OzSplitJob J = jobs[lo];
+  const int64_t local = t - J.thread_base;
+  const int64_t cols = (int64_t)J.CGp * 8;
+  const int64_t rg = local / cols;
+  if (rg >= oz_row_groups(J.rows)) return;
+  const int j = (int)(local - rg * cols);
+  uint32_t w[kOzDigits][4];
+#pragma unroll
+  for (int q = 0; q < kOzDigits; ++q) w[q][0] = w[q][1] = w[q][2] = w[q][3] = 0u;
+  const int E = j < J.m ? J.exps[j] : kOzNonFinite;
+  if (E != kOzNonFinite) {
+    const int64_t row0 = rg * 8;
+    const double* col = J.X + (int64_t)j * J.ldx + J.r0 + row0;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const double x = row0 + r < J.rows ? col[r] : 0.0;
+      uint32_t d[kOzDigits];
+      oz_digits(x, E, d);
+#pragma unroll
+      for (int q = 0; q < kOzDigits; ++q) w[q][r >> 1] |= d[q] << (16 * (r & 1));
+    }
+  }
+  uint4* out = reinterpret_cast<uint4*>(J.digits) + ((rg * J.CGp + (j >> 3)) * kOzDigits) * 8 + (j & 7);
+#pragma unroll
+  for (int q = 0; q < kOzDigits; ++q) out[q * 8] = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+}
+
+dim3 grid_for(int64_t blocks) {
+  const int64_t gx = blocks < 65535 ? blocks : 65535;
+  return dim3((unsigned)gx, (unsigned)((blocks + gx - 1) / gx));
+}
+
+}  // namespace
+
+cudaError_t launch_oz_colmax(const OzColJob* jobs_dev, int njobs, int64_t total_cols, cudaStream_t s) {
+  if (njobs <= 0 || total_cols <= 0) return cudaSuccess;
+  oz_colmax_kernel<<<grid_for(total_cols), kThreads, 0, s>>>(jobs_dev, njobs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_oz_split(const OzSplitJob* jobs_dev, int njobs, int64_t total_threads, cudaStream_t s) {
+  if (njobs <= 0 || total_threads <= 0) return cudaSuccess;
+  oz_split_kernel<<<grid_for((total_threads + kThreads - 1) / kThreads), kThreads, 0, s>>>(jobs_dev, njobs);
+  return cudaGetLastError();
+}
+
+}  // namespace hapod

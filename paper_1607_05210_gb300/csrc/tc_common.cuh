@@ -1,6 +1,6 @@
-// Shared device helpers for the tensor-core (tcgen05) kernels of the mixed form:
-// mbarrier waits with a bounded spin, TMA tiled loads, UMMA descriptors, TMEM
-// allocation and loads, and the split of FP32 values into bf16 hi + lo pieces.
+// Shared device helpers for the tensor-core (tcgen05) kernels: mbarrier waits with
+// a bounded spin, TMA tiled and bulk loads, UMMA descriptors, TMEM allocation and
+// loads, and the split of FP32 values into bf16 hi + lo pieces.
 // Inline PTX for sm_103a (tcgen05 / cp.async.bulk.tensor / mbarrier).
 #pragma once
 
@@ -93,6 +93,33 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   d |= (uint64_t)2 << 61;                   // 128-byte swizzle
   return d;
 }
+// Shared-memory matrix descriptor without swizzling: operand made of 8-row x 16-byte
+// core matrices (128 contiguous bytes each); `lbo` = byte distance between core
+// matrices adjacent along K, `sbo` = along M (or N).  The same two roles hold for
+// K-major and MN-major operands (checked on the device against integer products).
+__device__ __forceinline__ uint64_t ns_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version; layout type 0 = no swizzle
+  return d;
+}
+// Instruction descriptor: bf16 x bf16 -> FP32 with the A / B major-ness given
+// (0 = K-major, 1 = MN-major), M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32_major(uint32_t M, uint32_t N, uint32_t a_mn, uint32_t b_mn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (a_mn << 15) | (b_mn << 16) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+// Untiled bulk copy global -> shared (16-byte aligned addresses, size a multiple of
+// 16), completing `bytes` transaction bytes on bar.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
 // Instruction descriptor: bf16 x bf16 -> FP32, both operands K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(uint32_t M, uint32_t N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);

@@ -38,7 +38,8 @@ STATUS_NAMES = {0: "OK", 1: "ERR_INVALID", 2: "ERR_TREE", 3: "ERR_STATE", 4: "ER
 
 HAPOD_FP64 = 0
 HAPOD_MIXED_BF16X3 = 1
-DTYPE = {HAPOD_FP64: torch.float64, HAPOD_MIXED_BF16X3: torch.float32}
+HAPOD_FP64_OZAKI = 2
+DTYPE = {HAPOD_FP64: torch.float64, HAPOD_MIXED_BF16X3: torch.float32, HAPOD_FP64_OZAKI: torch.float64}
 
 
 class hapod_tree(ctypes.Structure):
