@@ -24,7 +24,7 @@
  *     the results are produced and the warning is recorded.
  *   - FP64 form (HAPOD_FP64): snapshots are IEEE double; all arithmetic is FP64.
  *     Digit-slice FP64 form (HAPOD_FP64_OZAKI): snapshots and results as in the
- *     FP64 form; the Gram is formed on the bf16 tensor cores from an exact
+ *     FP64 form; the Gram and X V are formed on the bf16 tensor cores from an exact
  *     7-digit base-128 fixed-point representation of each column (relative to a
  *     power-of-two bound of its largest entry, truncated below 2^-49 of it), with
  *     integer-exact accumulation and one FP64 rounding per entry.
@@ -59,10 +59,10 @@ typedef enum {
 typedef enum {
   HAPOD_FP64 = 0,           /* double snapshots, FP64 arithmetic everywhere */
   HAPOD_MIXED_BF16X3 = 1,   /* float snapshots, tensor-core (TF32 hi/lo split) Gram, FP32 X V */
-  HAPOD_FP64_OZAKI = 2      /* double snapshots and results; the Gram from exact 7-bit digit
-                               products on the bf16 tensor cores (error-free splitting of
-                               Ozaki et al. 2012, integer-exact accumulation, one final FP64
-                               rounding per entry); eigensolver and X V in FP64 */
+  HAPOD_FP64_OZAKI = 2      /* double snapshots and results; Gram and X V from exact 7-bit
+                               digit products on the bf16 tensor cores (error-free splitting
+                               of Ozaki et al. 2012, integer-exact accumulation, one final
+                               FP64 rounding per entry); eigensolver in FP64 */
 } hapod_precision;
 
 /*
@@ -239,7 +239,11 @@ hapod_status hapod_truncate(int64_t m, const double* lambda, double eps, int64_t
  * scale = NULL this is the sigma-scaled mode sigma_k phi_k that Def. HAPOD passes
  * to the parent, with scale_j = 1/sigma_j it is phi_j).  X: device n x m (ld ldx,
  * double or float by precision); V: device m x >= N FP64 (ld ldv); scale: device N
- * doubles or NULL; Y: device n x N (ld ldy), same type as X.
+ * doubles or NULL; Y: device n x N (ld ldy), same type as X.  The digit-slice form
+ * computes Y from exact digit products (X as for hapod_gram, V column c against a
+ * power-of-two bound of max_j 2^E_j |V_jc|), rounds once per entry, synchronises
+ * the stream, and returns NaN columns if X or V holds Inf or NaN; TIMEOUT if a
+ * bounded device-side wait ran out.
  */
 hapod_status hapod_modes(int32_t precision, int64_t n, int64_t m, const void* X, int64_t ldx, const double* V,
                          int64_t ldv, int64_t N, const double* scale, void* Y, int64_t ldy, void* stream);

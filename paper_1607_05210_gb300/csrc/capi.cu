@@ -194,6 +194,8 @@ struct Work {
   void* Y = nullptr;
   int64_t ldy = 0;
   double* scale = nullptr;  // device 1/sigma (root)
+  int32_t* exps = nullptr;  // digit-slice form: column exponents (owned)
+  int64_t ldvk = 0;         // leading dimension of Vk (0: m)
 };
 
 constexpr int kMaxSweeps = 40;
@@ -225,6 +227,8 @@ void free_work(Env& env, std::vector<Work*>& ws) {
     env.release(w->sigma);
     env.release(w->Vk);
     env.release(w->X_tmp);
+    env.release(w->exps);
+    w->exps = nullptr;
     w->X_tmp = nullptr;
     w->G = nullptr;
     w->A = w->V = nullptr;
@@ -233,11 +237,11 @@ void free_work(Env& env, std::vector<Work*>& ws) {
   }
 }
 
-// K1, digit-slice FP64 form: column exponents for every node, then rounds of digit
-// planes (at most oz_digit_cap() bytes at a time; a node taller than that is cut
-// into row chunks) and tensor-core Gram tiles, then one reduce of the split partials.
-// The digit-plane workspace defaults to 4 GiB; the environment variable
-// HAPOD_OZ_WORKSPACE_MB overrides it (read at every call).
+// ------------------------------------------------------------- digit-slice form
+// The digit planes of a node's X (14 bytes per element) are produced in rounds of at
+// most oz_digit_cap() bytes; a node taller than that is cut into row chunks.  The
+// cap defaults to 4 GiB; the environment variable HAPOD_OZ_WORKSPACE_MB overrides it
+// (read at every call).
 size_t oz_digit_cap() {
   const char* e = getenv("HAPOD_OZ_WORKSPACE_MB");
   if (e && *e) {
@@ -247,66 +251,112 @@ size_t oz_digit_cap() {
   return (size_t)4 << 30;
 }
 
-bool step_gram_oz(Env& env, std::vector<Work*>& ws) {
-  if (ws.empty()) return true;
-  const size_t kOzDigitCap = oz_digit_cap();
-  const int nw = (int)ws.size();
-  std::vector<OzColJob> cj(nw);
-  int64_t total_cols = 0;
-  for (int i = 0; i < nw; ++i) {
-    memset(&cj[i], 0, sizeof(OzColJob));
-    cj[i].X = static_cast<const double*>(ws[i]->X);
-    cj[i].ldx = ws[i]->ldx;
-    cj[i].n = ws[i]->n;
-    cj[i].m = (int32_t)ws[i]->m;
-    cj[i].col_base = total_cols;
-    total_cols += ws[i]->m;
-  }
-  int32_t* exps = (int32_t*)env.alloc(sizeof(int32_t) * std::max<int64_t>(1, total_cols), "alloc exponents");
-  if (!exps) return false;
-  for (int i = 0; i < nw; ++i) cj[i].exps = exps + cj[i].col_base;
-  struct Chunk {
-    int node;
-    int64_t r0, rows;
-    int32_t CGp, RG, tiles, splits, sps;
-    size_t bytes;
-    int64_t slot0;
-  };
-  std::vector<Chunk> chunks;
-  std::vector<int64_t> node_slots(nw, 0);
-  for (int i = 0; i < nw; ++i) {
+struct OzChunk {
+  int node;
+  int64_t r0, rows;
+  int32_t CGp, RG;
+  size_t bytes;
+  int32_t splits, sps;  // Gram: row splits and 16-row stages per split
+  int64_t slot0;        // Gram: first partial slot of the chunk within its node
+};
+
+// Row chunks of every node and rounds of consecutive chunks within the cap.
+void oz_plan(const std::vector<Work*>& ws, std::vector<OzChunk>& chunks, std::vector<std::pair<size_t, size_t>>& rounds,
+             size_t& max_round) {
+  const size_t cap = oz_digit_cap();
+  for (int i = 0; i < (int)ws.size(); ++i) {
     const int32_t CGp = oz_col_groups(ws[i]->m);
     const size_t row_bytes = (size_t)CGp * 8 * kOzDigits * 2;
-    int64_t R = (int64_t)(kOzDigitCap / row_bytes) / kOzKBlock * kOzKBlock;
+    int64_t R = (int64_t)(cap / row_bytes) / kOzKBlock * kOzKBlock;
     R = std::max<int64_t>(R, kOzKBlock);
     for (int64_t r0 = 0; r0 < ws[i]->n; r0 += R) {
-      Chunk c;
+      OzChunk c;
       c.node = i;
       c.r0 = r0;
       c.rows = std::min(R, ws[i]->n - r0);
       c.CGp = CGp;
       c.RG = (int32_t)oz_row_groups(c.rows);
-      c.tiles = oz_gram_tiles((int32_t)ws[i]->m, CGp);
       c.bytes = (size_t)c.RG * 8 * row_bytes;
       c.splits = c.sps = 0;
       c.slot0 = 0;
       chunks.push_back(c);
     }
   }
-  // rounds: consecutive chunks while the digit planes fit the cap
-  std::vector<std::pair<size_t, size_t>> rounds;
-  size_t max_round = 0;
+  max_round = 0;
   for (size_t a = 0; a < chunks.size();) {
     size_t b = a, bytes = 0;
-    while (b < chunks.size() && (b == a || bytes + chunks[b].bytes <= kOzDigitCap)) bytes += chunks[b++].bytes;
+    while (b < chunks.size() && (b == a || bytes + chunks[b].bytes <= cap)) bytes += chunks[b++].bytes;
     rounds.push_back({a, b});
     max_round = std::max(max_round, bytes);
+    a = b;
+  }
+}
+
+OzSplitJob oz_split_job(const Work* w, const OzChunk& C, uint16_t* dblk, int64_t thread_base) {
+  OzSplitJob S;
+  memset(&S, 0, sizeof(S));
+  S.X = static_cast<const double*>(w->X);
+  S.ldx = w->ldx;
+  S.r0 = C.r0;
+  S.rows = C.rows;
+  S.exps = w->exps;
+  S.digits = dblk;
+  S.thread_base = thread_base;
+  S.m = (int32_t)w->m;
+  S.CGp = C.CGp;
+  return S;
+}
+
+// Column exponents E_j of every node without them (w->exps, owned by the Work).
+bool oz_exponents(Env& env, std::vector<Work*>& ws) {
+  std::vector<OzColJob> cj;
+  int64_t total = 0;
+  for (Work* w : ws) {
+    if (w->exps) continue;
+    w->exps = (int32_t*)env.alloc(sizeof(int32_t) * std::max<int64_t>(1, w->m), "alloc exponents");
+    if (!w->exps) return false;
+    OzColJob J;
+    memset(&J, 0, sizeof(J));
+    J.X = static_cast<const double*>(w->X);
+    J.ldx = w->ldx;
+    J.n = w->n;
+    J.exps = w->exps;
+    J.col_base = total;
+    J.m = (int32_t)w->m;
+    total += w->m;
+    cj.push_back(J);
+  }
+  if (cj.empty()) return true;
+  OzColJob* d = env.upload(cj, "upload exponent jobs");
+  bool ok = d && env.cuda(launch_oz_colmax(d, (int)cj.size(), total, env.s), "exponent launch");
+  env.release(d);
+  return ok;
+}
+
+// K1, digit-slice FP64 form: exponents, then per round the digit planes and the
+// tensor-core Gram tiles of its chunks, then one reduce of the split partials.
+bool step_gram_oz(Env& env, std::vector<Work*>& ws) {
+  if (ws.empty()) return true;
+  const int nw = (int)ws.size();
+  double bytes = 0, flops = 0;
+  for (Work* w : ws) {
+    bytes += 8.0 * w->n * w->m;
+    flops += (double)w->n * w->m * (w->m + 1);
+  }
+  cudaEvent_t t0 = env.tic();
+  if (!oz_exponents(env, ws)) return false;
+  std::vector<OzChunk> chunks;
+  std::vector<std::pair<size_t, size_t>> rounds;
+  size_t max_round = 0;
+  oz_plan(ws, chunks, rounds, max_round);
+  std::vector<int64_t> node_slots(nw, 0);
+  for (const auto& rd : rounds) {
     // splits: about two waves of one CTA per SM over the round's tiles, whole 256-row blocks
     int64_t T = 0;
-    for (size_t c = a; c < b; ++c) T += chunks[c].tiles;
+    for (size_t c = rd.first; c < rd.second; ++c) T += oz_gram_tiles((int32_t)ws[chunks[c].node]->m, chunks[c].CGp);
     const int64_t want = std::max<int64_t>(1, (2 * kNumSMs) / std::max<int64_t>(1, T));
-    for (size_t c = a; c < b; ++c) {
-      Chunk& C = chunks[c];
+    for (size_t c = rd.first; c < rd.second; ++c) {
+      OzChunk& C = chunks[c];
       const int64_t stages = C.RG / 2;
       const int64_t blk = kOzKBlock / 16;
       int64_t sps = (stages + want - 1) / want;
@@ -317,7 +367,6 @@ bool step_gram_oz(Env& env, std::vector<Work*>& ws) {
       C.slot0 = node_slots[C.node];
       node_slots[C.node] += C.splits;
     }
-    a = b;
   }
   std::vector<int64_t> node_base(nw, 0);
   size_t total_partial = 0;
@@ -326,21 +375,10 @@ bool step_gram_oz(Env& env, std::vector<Work*>& ws) {
     node_base[i] = (int64_t)total_partial;
     total_partial += (size_t)node_slots[i] * mp * mp;
   }
-  OzColJob* cj_d = env.upload(cj, "upload exponent jobs");
   double* partial = (double*)env.alloc(sizeof(double) * std::max<size_t>(1, total_partial), "alloc gram partials");
   uint16_t* digits = (uint16_t*)env.alloc(std::max<size_t>(16, max_round), "alloc digit planes");
-  bool ok = cj_d && partial && digits;
-  double bytes = 0, flops = 0;
-  for (Work* w : ws) {
-    bytes += 8.0 * w->n * w->m;
-    flops += (double)w->n * w->m * (w->m + 1);
-  }
-  cudaEvent_t t0 = env.tic();
-  int launches = 0;
-  if (ok) {
-    ok = env.cuda(launch_oz_colmax(cj_d, nw, total_cols, env.s), "exponent launch");
-    ++launches;
-  }
+  bool ok = partial && digits;
+  int launches = 1;
   std::vector<void*> job_bufs;
   for (size_t r = 0; r < rounds.size() && ok; ++r) {
     std::vector<OzSplitJob> sj;
@@ -348,28 +386,17 @@ bool step_gram_oz(Env& env, std::vector<Work*>& ws) {
     size_t off = 0;
     int64_t threads = 0, items = 0;
     for (size_t c = rounds[r].first; c < rounds[r].second; ++c) {
-      const Chunk& C = chunks[c];
+      const OzChunk& C = chunks[c];
       Work* w = ws[C.node];
       uint16_t* dblk = reinterpret_cast<uint16_t*>(reinterpret_cast<uint8_t*>(digits) + off);
       off += C.bytes;
-      OzSplitJob S;
-      memset(&S, 0, sizeof(S));
-      S.X = static_cast<const double*>(w->X);
-      S.ldx = w->ldx;
-      S.r0 = C.r0;
-      S.rows = C.rows;
-      S.exps = cj[C.node].exps;
-      S.digits = dblk;
-      S.thread_base = threads;
-      S.m = (int32_t)w->m;
-      S.CGp = C.CGp;
+      sj.push_back(oz_split_job(w, C, dblk, threads));
       threads += (int64_t)C.RG * C.CGp * 8;
-      sj.push_back(S);
       OzGramJob G;
       memset(&G, 0, sizeof(G));
       const int64_t mp = (int64_t)C.CGp * 8;
       G.digits = dblk;
-      G.exps = cj[C.node].exps;
+      G.exps = w->exps;
       G.partial = partial + node_base[C.node] + (size_t)C.slot0 * mp * mp;
       G.item_base = items;
       G.RG = C.RG;
@@ -377,8 +404,8 @@ bool step_gram_oz(Env& env, std::vector<Work*>& ws) {
       G.m = (int32_t)w->m;
       G.splits = C.splits;
       G.stages_per_split = C.sps;
-      G.tiles = C.tiles;
-      items += (int64_t)C.splits * C.tiles;
+      G.tiles = oz_gram_tiles((int32_t)w->m, C.CGp);
+      items += (int64_t)C.splits * G.tiles;
       gj.push_back(G);
     }
     OzSplitJob* sj_d = env.upload(sj, "upload split jobs");
@@ -409,10 +436,112 @@ bool step_gram_oz(Env& env, std::vector<Work*>& ws) {
   }
   env.toc(t0, 0, launches, bytes, flops);
   for (void* p : job_bufs) env.release(p);
-  env.release(cj_d);
   env.release(partial);
   env.release(digits);
-  env.release(exps);
+  return ok;
+}
+
+// K4, digit-slice FP64 form: Y = X V_k (diag scale) for every w (k = w->res.k > 0,
+// V_k in w->Vk with ld m): digits of V_k, then per round the X digit planes and the
+// tensor-core modes tiles of its chunks.  Exponents are the Gram's (or computed here).
+bool step_modes_oz(Env& env, std::vector<Work*>& ws) {
+  if (ws.empty()) return true;
+  const int nw = (int)ws.size();
+  if (!oz_exponents(env, ws)) return false;
+  int max_k = 1;
+  for (Work* w : ws) max_k = std::max(max_k, (int)w->res.k);
+  const int NT = oz_modes_tile(max_k);
+  std::vector<OzVSplitJob> vj(nw);
+  std::vector<void*> bufs;
+  std::vector<uint16_t*> vdig(nw);
+  std::vector<int32_t*> fexp(nw);
+  int64_t vcols = 0;
+  bool ok = true;
+  for (int i = 0; i < nw && ok; ++i) {
+    Work* w = ws[i];
+    const int32_t CGp = oz_col_groups(w->m);
+    const int32_t n_tiles = (w->res.k + NT - 1) / NT;
+    const int32_t NG = n_tiles * NT / 8;
+    vdig[i] = (uint16_t*)env.alloc((size_t)CGp * NG * kOzGroupBytes, "alloc V digits");
+    fexp[i] = (int32_t*)env.alloc(sizeof(int32_t) * NG * 8, "alloc mode exponents");
+    bufs.push_back(vdig[i]);
+    bufs.push_back(fexp[i]);
+    ok = vdig[i] && fexp[i];
+    OzVSplitJob& J = vj[i];
+    memset(&J, 0, sizeof(J));
+    J.V = w->Vk;
+    J.ldv = w->ldvk ? w->ldvk : w->m;
+    J.exps = w->exps;
+    J.vdig = vdig[i];
+    J.fexp = fexp[i];
+    J.col_base = vcols;
+    J.m = (int32_t)w->m;
+    J.k = w->res.k;
+    J.NG = NG;
+    J.CGp = CGp;
+    vcols += (int64_t)NG * 8;
+  }
+  double bytes = 0, flops = 0;
+  for (Work* w : ws) {
+    bytes += 8.0 * w->n * (w->m + w->res.k);
+    flops += 2.0 * w->n * w->m * w->res.k;
+  }
+  cudaEvent_t t0 = env.tic();
+  int launches = 0;
+  if (ok) {
+    OzVSplitJob* vj_d = env.upload(vj, "upload V split jobs");
+    bufs.push_back(vj_d);
+    ok = vj_d && env.cuda(launch_oz_vsplit(vj_d, nw, vcols, env.s), "V split launch");
+    ++launches;
+  }
+  std::vector<OzChunk> chunks;
+  std::vector<std::pair<size_t, size_t>> rounds;
+  size_t max_round = 0;
+  oz_plan(ws, chunks, rounds, max_round);
+  uint16_t* digits = ok ? (uint16_t*)env.alloc(std::max<size_t>(16, max_round), "alloc digit planes") : nullptr;
+  ok = ok && digits;
+  for (size_t r = 0; r < rounds.size() && ok; ++r) {
+    std::vector<OzSplitJob> sj;
+    std::vector<OzModesJob> mj;
+    size_t off = 0;
+    int64_t threads = 0, items = 0;
+    for (size_t c = rounds[r].first; c < rounds[r].second; ++c) {
+      const OzChunk& C = chunks[c];
+      Work* w = ws[C.node];
+      uint16_t* dblk = reinterpret_cast<uint16_t*>(reinterpret_cast<uint8_t*>(digits) + off);
+      off += C.bytes;
+      sj.push_back(oz_split_job(w, C, dblk, threads));
+      threads += (int64_t)C.RG * C.CGp * 8;
+      OzModesJob M;
+      memset(&M, 0, sizeof(M));
+      M.xdig = dblk;
+      M.vdig = vdig[C.node];
+      M.fexp = fexp[C.node];
+      M.scale = w->scale;
+      M.Y = static_cast<double*>(w->Y) + C.r0;
+      M.ldy = w->ldy;
+      M.rows = C.rows;
+      M.item_base = items;
+      M.RG = C.RG;
+      M.CGp = C.CGp;
+      M.k = w->res.k;
+      M.n_tiles = (w->res.k + NT - 1) / NT;
+      M.NG = M.n_tiles * NT / 8;
+      M.row_tiles = (C.RG + 15) / 16;
+      items += (int64_t)M.row_tiles * M.n_tiles;
+      mj.push_back(M);
+    }
+    OzSplitJob* sj_d = env.upload(sj, "upload split jobs");
+    OzModesJob* mj_d = env.upload(mj, "upload modes jobs");
+    bufs.push_back(sj_d);
+    bufs.push_back(mj_d);
+    ok = sj_d && mj_d && env.cuda(launch_oz_split(sj_d, (int)sj.size(), threads, env.s), "digit split launch") &&
+         env.cuda(launch_modes_oz(mj_d, (int)mj.size(), items, NT, env.err_dev, env.s), "modes launch");
+    launches += 2;
+  }
+  env.toc(t0, 4, launches, bytes, flops);
+  env.release(digits);
+  for (void* p : bufs) env.release(p);
   return ok;
 }
 
@@ -609,6 +738,7 @@ bool run_pod_back(Env& env, int precision, std::vector<Work*>& ws) {
   env.toc(tg, 3, 1, 0.0, 0.0);
   env.release(gd);
   if (!ok) return false;
+  if (precision == HAPOD_FP64_OZAKI) return step_modes_oz(env, act);
   int max_k = 0;
   for (Work* w : act) max_k = std::max(max_k, w->res.k);
   const int tr = fp64 ? modes_f64_tile_rows(max_k) : modes_mixed_rows_per_block(max_k);
@@ -1283,6 +1413,7 @@ hapod_status hapod_gram(int32_t precision, int64_t n, int64_t m, const void* X, 
   if (ok) ok = env.cuda(cudaMemcpyAsync(&dev_err, env.err_dev, sizeof(int), cudaMemcpyDeviceToHost, env.s), "read flag");
   env.release(env.err_dev);
   env.release(w.X_tmp);
+  env.release(w.exps);
   ok = env.cuda(cudaStreamSynchronize(env.s), "synchronize") && ok;
   if (!ok) return step_error(env);
   if (dev_err) {
@@ -1381,6 +1512,36 @@ hapod_status hapod_modes(int32_t precision, int64_t n, int64_t m, const void* X,
   if (N == 0 || n == 0) return HAPOD_OK;
   Env env;
   if (!init_env(env, stream)) return step_error(env);
+  if (precision == HAPOD_FP64_OZAKI) {
+    // tensor-core kernel with bounded waits: its error flag is read back here
+    Work w;
+    w.X = X;
+    w.ldx = ldx;
+    w.n = n;
+    w.m = m;
+    w.Vk = const_cast<double*>(V);
+    w.ldvk = ldv;
+    w.scale = const_cast<double*>(scale);
+    w.Y = Y;
+    w.ldy = ldy;
+    w.res.k = (int32_t)N;
+    std::vector<Work*> ws{&w};
+    env.err_dev = (int*)env.alloc(sizeof(int), "alloc flag");
+    bool ok = env.err_dev && env.cuda(cudaMemsetAsync(env.err_dev, 0, sizeof(int), env.s), "memset") &&
+              step_modes_oz(env, ws);
+    int dev_err = 0;
+    if (ok)
+      ok = env.cuda(cudaMemcpyAsync(&dev_err, env.err_dev, sizeof(int), cudaMemcpyDeviceToHost, env.s), "read flag");
+    env.release(env.err_dev);
+    env.release(w.exps);
+    ok = env.cuda(cudaStreamSynchronize(env.s), "synchronize") && ok;
+    if (!ok) return step_error(env);
+    if (dev_err) {
+      g_thread_error = "hapod_modes: device-side wait timed out";
+      return HAPOD_ERR_TIMEOUT;
+    }
+    return HAPOD_OK;
+  }
   const bool fp64 = f64_data(precision);
   const int tr = fp64 ? modes_f64_tile_rows((int)N) : modes_mixed_rows_per_block((int)N);
   const int tc = fp64 ? modes_f64_tile_cols((int)N) : modes_mixed_tile_cols((int)N);

@@ -144,6 +144,43 @@ struct OzReduceJob {
 };
 cudaError_t launch_oz_reduce(const OzReduceJob* jobs_dev, int njobs, int64_t total_cols, cudaStream_t s);
 
+// X V of the digit-slice form: V_k (FP64 m x k, ld ldv) in digits against 2^(F_c - E_j)
+// (vdig: [CGp][NG][7][8][8], fexp: F_c per mode column, NG = kpad / 8).
+struct OzVSplitJob {
+  const double* V;
+  int64_t ldv;
+  const int32_t* exps;
+  uint16_t* vdig;
+  int32_t* fexp;
+  int64_t col_base;  // first block (one per padded mode column)
+  int32_t m;
+  int32_t k;
+  int32_t NG;
+  int32_t CGp;
+};
+cudaError_t launch_oz_vsplit(const OzVSplitJob* jobs_dev, int njobs, int64_t total_cols, cudaStream_t s);
+// Items (n tile, row tile) of 128 rows x NT modes over one X digit block (rows
+// [r0, r0 + rows) of the node; Y points at row r0).
+struct OzModesJob {
+  const uint16_t* xdig;
+  const uint16_t* vdig;
+  const int32_t* fexp;
+  const double* scale;  // k or null
+  double* Y;
+  int64_t ldy;
+  int64_t rows;
+  int64_t item_base;
+  int32_t RG;
+  int32_t CGp;
+  int32_t NG;
+  int32_t k;
+  int32_t row_tiles;
+  int32_t n_tiles;
+};
+int oz_modes_tile(int k);  // NT: 32 for k <= 32, else 64
+cudaError_t launch_modes_oz(const OzModesJob* jobs_dev, int njobs, int64_t total_items, int nt, int* err_flag,
+                            cudaStream_t s);
+
 // ---------------------------------------------------------------- eig (K2)
 struct EigJob {
   const double* G;     // m x m FP64 input (not modified)

@@ -132,6 +132,66 @@ def test_gram_oz_empty(H):
     assert st == H.HAPOD_OK and torch.all(G == 0)
 
 
+# ------------------------------------------------------------------ K4 X V
+def modes_bound(X, V, scale):
+    """Per entry: m 2^(F_c - 47) (digit truncation of X and of the rescaled V plus the
+    dropped levels, per term below 2^(F_c - 47)) + the FP64 rounding of the reference,
+    times |scale_c|; F_c = max_j (E_j + e(V_jc)) with |V_jc| < 2^e(V_jc)."""
+    m = X.shape[1]
+    E = col_exponents(X)
+    ev = np.where(V != 0, np.frexp(V)[1], -10 ** 6)
+    F = np.max(E[:, None] + ev, axis=0)
+    rn = np.sqrt(np.sum(X * X, axis=1))[:, None] * np.linalg.norm(V, axis=0)[None, :]
+    return (m * np.exp2(F - 47.0)[None, :] + 1e-13 * math.sqrt(m) * rn) * np.abs(scale)[None, :]
+
+
+@pytest.mark.parametrize("n,m,N", [(1, 3, 2), (1000, 100, 37), (4097, 130, 65), (300, 1, 1), (12345, 64, 64),
+                                   (5000, 500, 20), (70001, 256, 19), (129, 40, 33)])
+def test_modes_oz(H, n, m, N):
+    rng = np.random.default_rng(n + m + N)
+    X = rng.standard_normal((n, m)) * (1.0 + np.arange(m)) ** 0.5
+    V = np.asfortranarray(rng.standard_normal((m, N)) / math.sqrt(m))
+    scale = rng.uniform(0.5, 2.0, N)
+    Y = to_host(H.hapod_modes(to_dev(X), to_dev(V), N, torch.from_numpy(scale).cuda(), H.HAPOD_FP64_OZAKI))
+    ref = (X @ V) * scale
+    err = np.abs(Y - ref)
+    bound = modes_bound(X, V, scale)
+    assert np.all(err <= bound), float(np.max(err / bound))
+
+
+def test_modes_oz_exact_integers(H):
+    """Small-integer X and V: every digit and level sum is exact, so is X V."""
+    rng = np.random.default_rng(3)
+    X = rng.integers(-1000, 1001, size=(7000, 90)).astype(np.float64)
+    V = np.asfortranarray(rng.integers(-100, 101, size=(90, 23)).astype(np.float64))
+    Y = to_host(H.hapod_modes(to_dev(X), to_dev(V), 23, None, H.HAPOD_FP64_OZAKI))
+    ref = (X.astype(np.int64) @ V.astype(np.int64)).astype(np.float64)
+    assert np.array_equal(Y, ref)
+
+
+def test_modes_oz_nonfinite(H):
+    rng = np.random.default_rng(4)
+    X = rng.standard_normal((600, 12))
+    X[5, 3] = float("inf")
+    V = np.asfortranarray(rng.standard_normal((12, 4)))
+    Y = to_host(H.hapod_modes(to_dev(X), to_dev(V), 4, None, H.HAPOD_FP64_OZAKI))
+    assert np.all(np.isnan(Y))
+
+
+def test_modes_oz_row_chunks_and_ld(H, monkeypatch):
+    """1 MiB digit workspace (row chunks), padded leading dimensions of X, V and Y."""
+    rng = np.random.default_rng(6)
+    n, m, N = 30011, 130, 40
+    X = rng.standard_normal((n, m))
+    V = rng.standard_normal((m, N)) / math.sqrt(m)
+    Vd = to_dev(V, ld=m + 3)
+    monkeypatch.setenv("HAPOD_OZ_WORKSPACE_MB", "1")
+    Y = to_host(H.hapod_modes(to_dev(X, ld=n + 5), Vd, N, None, H.HAPOD_FP64_OZAKI))
+    monkeypatch.delenv("HAPOD_OZ_WORKSPACE_MB")
+    ref = X @ V
+    assert np.all(np.abs(Y - ref) <= modes_bound(X, V, np.ones(N)))
+
+
 # ------------------------------------------------------------------ one node
 @pytest.mark.parametrize("n,m,decay,rel", [(2000, 50, 0.2, 1e-4), (5000, 130, 0.08, 1e-6), (600, 300, 0.05, 1e-3),
                                            (128, 8, 1.0, 0.5)])
