@@ -442,44 +442,81 @@ bool step_gram_oz(Env& env, std::vector<Work*>& ws) {
 }
 
 // K4, digit-slice FP64 form: Y = X V_k (diag scale) for every w (k = w->res.k > 0,
-// V_k in w->Vk with ld m): digits of V_k, then per round the X digit planes and the
-// tensor-core modes tiles of its chunks.  Exponents are the Gram's (or computed here).
+// V_k in w->Vk): digits of V_k, then one persistent tensor-core launch that converts
+// X to digits on the fly.  Exponents are the Gram's (or computed here).
 bool step_modes_oz(Env& env, std::vector<Work*>& ws) {
   if (ws.empty()) return true;
   const int nw = (int)ws.size();
   if (!oz_exponents(env, ws)) return false;
-  int max_k = 1;
-  for (Work* w : ws) max_k = std::max(max_k, (int)w->res.k);
-  const int NT = oz_modes_tile(max_k);
+  const int NT = oz_modes_tile(0);
   std::vector<OzVSplitJob> vj(nw);
+  std::vector<OzModesJob> mj(nw);
   std::vector<void*> bufs;
-  std::vector<uint16_t*> vdig(nw);
-  std::vector<int32_t*> fexp(nw);
-  int64_t vcols = 0;
+  int64_t vcols = 0, items = 0;
   bool ok = true;
   for (int i = 0; i < nw && ok; ++i) {
     Work* w = ws[i];
     const int32_t CGp = oz_col_groups(w->m);
     const int32_t n_tiles = (w->res.k + NT - 1) / NT;
     const int32_t NG = n_tiles * NT / 8;
-    vdig[i] = (uint16_t*)env.alloc((size_t)CGp * NG * kOzGroupBytes, "alloc V digits");
-    fexp[i] = (int32_t*)env.alloc(sizeof(int32_t) * NG * 8, "alloc mode exponents");
-    bufs.push_back(vdig[i]);
-    bufs.push_back(fexp[i]);
-    ok = vdig[i] && fexp[i];
+    uint16_t* vdig = (uint16_t*)env.alloc((size_t)CGp * NG * kOzGroupBytes, "alloc V digits");
+    int32_t* fexp = (int32_t*)env.alloc(sizeof(int32_t) * NG * 8, "alloc mode exponents");
+    bufs.push_back(vdig);
+    bufs.push_back(fexp);
+    ok = vdig && fexp;
     OzVSplitJob& J = vj[i];
     memset(&J, 0, sizeof(J));
     J.V = w->Vk;
     J.ldv = w->ldvk ? w->ldvk : w->m;
     J.exps = w->exps;
-    J.vdig = vdig[i];
-    J.fexp = fexp[i];
+    J.vdig = vdig;
+    J.fexp = fexp;
     J.col_base = vcols;
     J.m = (int32_t)w->m;
     J.k = w->res.k;
     J.NG = NG;
     J.CGp = CGp;
     vcols += (int64_t)NG * 8;
+    OzModesJob& M = mj[i];
+    memset(&M, 0, sizeof(M));
+    M.X = static_cast<const double*>(w->X);
+    M.ldx = w->ldx;
+    M.exps = w->exps;
+    M.vdig = vdig;
+    M.fexp = fexp;
+    M.scale = w->scale;
+    M.Y = static_cast<double*>(w->Y);
+    M.ldy = w->ldy;
+    M.n = w->n;
+    M.item_base = items;
+    M.m = (int32_t)w->m;
+    M.CGp = CGp;
+    M.NG = NG;
+    M.k = w->res.k;
+    M.row_tiles = (int32_t)((w->n + 127) / 128);
+    M.n_tiles = n_tiles;
+    items += (int64_t)M.row_tiles * n_tiles;
+  }
+  // TMA maps of X (box 128 rows x 16 columns); an input TMA cannot read (base not
+  // 16-byte aligned or odd leading dimension) is first copied to an aligned buffer
+  std::vector<CUtensorMap> maps(nw);
+  for (int i = 0; i < nw && ok; ++i) {
+    Work* w = ws[i];
+    const double* X = static_cast<const double*>(w->X);
+    int64_t ldx = w->ldx;
+    if (!tma_compatible_f64(X, ldx)) {
+      ldx = (w->n + 1) / 2 * 2;
+      void* tmp = env.alloc(sizeof(double) * ldx * w->m, "alloc aligned input");
+      bufs.push_back(tmp);
+      ok = tmp && env.cuda(cudaMemcpy2DAsync(tmp, ldx * sizeof(double), X, w->ldx * sizeof(double),
+                                             w->n * sizeof(double), w->m, cudaMemcpyDeviceToDevice, env.s),
+                           "copy input for TMA");
+      X = static_cast<const double*>(tmp);
+      mj[i].X = X;
+      mj[i].ldx = ldx;
+    }
+    if (ok && !encode_colmajor_f64(&maps[i], X, w->n, w->m, ldx, 128, 16))
+      ok = env.fail(HAPOD_ERR_CUDA, "cuTensorMapEncodeTiled failed for an X V input");
   }
   double bytes = 0, flops = 0;
   for (Work* w : ws) {
@@ -487,60 +524,17 @@ bool step_modes_oz(Env& env, std::vector<Work*>& ws) {
     flops += 2.0 * w->n * w->m * w->res.k;
   }
   cudaEvent_t t0 = env.tic();
-  int launches = 0;
   if (ok) {
     OzVSplitJob* vj_d = env.upload(vj, "upload V split jobs");
-    bufs.push_back(vj_d);
-    ok = vj_d && env.cuda(launch_oz_vsplit(vj_d, nw, vcols, env.s), "V split launch");
-    ++launches;
-  }
-  std::vector<OzChunk> chunks;
-  std::vector<std::pair<size_t, size_t>> rounds;
-  size_t max_round = 0;
-  oz_plan(ws, chunks, rounds, max_round);
-  uint16_t* digits = ok ? (uint16_t*)env.alloc(std::max<size_t>(16, max_round), "alloc digit planes") : nullptr;
-  ok = ok && digits;
-  for (size_t r = 0; r < rounds.size() && ok; ++r) {
-    std::vector<OzSplitJob> sj;
-    std::vector<OzModesJob> mj;
-    size_t off = 0;
-    int64_t threads = 0, items = 0;
-    for (size_t c = rounds[r].first; c < rounds[r].second; ++c) {
-      const OzChunk& C = chunks[c];
-      Work* w = ws[C.node];
-      uint16_t* dblk = reinterpret_cast<uint16_t*>(reinterpret_cast<uint8_t*>(digits) + off);
-      off += C.bytes;
-      sj.push_back(oz_split_job(w, C, dblk, threads));
-      threads += (int64_t)C.RG * C.CGp * 8;
-      OzModesJob M;
-      memset(&M, 0, sizeof(M));
-      M.xdig = dblk;
-      M.vdig = vdig[C.node];
-      M.fexp = fexp[C.node];
-      M.scale = w->scale;
-      M.Y = static_cast<double*>(w->Y) + C.r0;
-      M.ldy = w->ldy;
-      M.rows = C.rows;
-      M.item_base = items;
-      M.RG = C.RG;
-      M.CGp = C.CGp;
-      M.k = w->res.k;
-      M.n_tiles = (w->res.k + NT - 1) / NT;
-      M.NG = M.n_tiles * NT / 8;
-      M.row_tiles = (C.RG + 15) / 16;
-      items += (int64_t)M.row_tiles * M.n_tiles;
-      mj.push_back(M);
-    }
-    OzSplitJob* sj_d = env.upload(sj, "upload split jobs");
     OzModesJob* mj_d = env.upload(mj, "upload modes jobs");
-    bufs.push_back(sj_d);
+    CUtensorMap* maps_d = env.upload(maps, "upload tensor maps");
+    bufs.push_back(vj_d);
     bufs.push_back(mj_d);
-    ok = sj_d && mj_d && env.cuda(launch_oz_split(sj_d, (int)sj.size(), threads, env.s), "digit split launch") &&
-         env.cuda(launch_modes_oz(mj_d, (int)mj.size(), items, NT, env.err_dev, env.s), "modes launch");
-    launches += 2;
+    bufs.push_back(maps_d);
+    ok = vj_d && mj_d && maps_d && env.cuda(launch_oz_vsplit(vj_d, nw, vcols, env.s), "V split launch") &&
+         env.cuda(launch_modes_oz(mj_d, maps_d, nw, items, env.err_dev, env.s), "modes launch");
   }
-  env.toc(t0, 4, launches, bytes, flops);
-  env.release(digits);
+  env.toc(t0, 4, 2, bytes, flops);
   for (void* p : bufs) env.release(p);
   return ok;
 }

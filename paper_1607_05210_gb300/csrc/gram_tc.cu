@@ -323,6 +323,23 @@ bool encode_colmajor_f32(CUtensorMap* out, const void* base, int64_t rows, int64
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+bool tma_compatible_f64(const void* base, int64_t ld) {
+  return base && (reinterpret_cast<uintptr_t>(base) % 16 == 0) && (ld % 2 == 0);
+}
+
+bool encode_colmajor_f64(CUtensorMap* out, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows,
+                         int box_cols) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || !tma_compatible_f64(base, ld) || rows < 1 || cols < 1) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)rows, (cuuint64_t)cols};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 8};
+  cuuint32_t box[2] = {(cuuint32_t)box_rows, (cuuint32_t)box_cols};
+  cuuint32_t es[2] = {1, 1};
+  return fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<void*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int gram_tc_rows_per_stage() { return kRowsPerStage; }
 
 cudaError_t launch_gram_tc(const GramJob* jobs_dev, const CUtensorMap* maps_dev, const int4* items_dev, int num_items,

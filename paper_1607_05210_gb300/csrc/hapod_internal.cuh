@@ -72,6 +72,10 @@ cudaError_t launch_gram_tc(const GramJob* jobs_dev, const CUtensorMap* maps_dev,
 int gram_tc_rows_per_stage();
 // TMA needs a 16-byte aligned base and a row pitch that is a multiple of 16 bytes.
 bool tma_compatible_f32(const void* base, int64_t ld);
+bool tma_compatible_f64(const void* base, int64_t ld);
+// FP64 column-major map, box box_rows x box_cols, no swizzle, zero fill outside.
+bool encode_colmajor_f64(CUtensorMap* out, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows,
+                         int box_cols);
 bool encode_colmajor_f32(CUtensorMap* out, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows,
                          int box_cols, bool swizzle128);
 
@@ -159,27 +163,31 @@ struct OzVSplitJob {
   int32_t CGp;
 };
 cudaError_t launch_oz_vsplit(const OzVSplitJob* jobs_dev, int njobs, int64_t total_cols, cudaStream_t s);
-// Items (n tile, row tile) of 128 rows x NT modes over one X digit block (rows
-// [r0, r0 + rows) of the node; Y points at row r0).
+// Items (n tile, row tile) of 128 rows x 32 modes of one node; the kernel converts
+// X (FP64, ld ldx) to digits itself with the node's column exponents.
 struct OzModesJob {
-  const uint16_t* xdig;
+  const double* X;
+  int64_t ldx;
+  const int32_t* exps;
   const uint16_t* vdig;
   const int32_t* fexp;
   const double* scale;  // k or null
   double* Y;
   int64_t ldy;
-  int64_t rows;
+  int64_t n;
   int64_t item_base;
-  int32_t RG;
+  int32_t m;
   int32_t CGp;
   int32_t NG;
   int32_t k;
   int32_t row_tiles;
   int32_t n_tiles;
 };
-int oz_modes_tile(int k);  // NT: 32 for k <= 32, else 64
-cudaError_t launch_modes_oz(const OzModesJob* jobs_dev, int njobs, int64_t total_items, int nt, int* err_flag,
-                            cudaStream_t s);
+int oz_modes_tile(int k);  // modes per item (32)
+// Persistent: min(items, SMs) CTAs walk the items.  maps_dev[j]: TMA map of job j's X
+// (encode_colmajor_f64, box 128 rows x 16 columns); X needs tma_compatible_f64.
+cudaError_t launch_modes_oz(const OzModesJob* jobs_dev, const CUtensorMap* maps_dev, int njobs, int64_t total_items,
+                            int* err_flag, cudaStream_t s);
 
 // ---------------------------------------------------------------- eig (K2)
 struct EigJob {

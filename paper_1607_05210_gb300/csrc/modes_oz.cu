@@ -2,24 +2,28 @@
 // def:method_of_snapshots: sigma_k phi_k = X psi_k, or phi_k with scale = 1/sigma)
 // from exact digits on the tensor cores (tcgen05 kind::f16, bf16 x bf16 -> FP32).
 //
-// X is split per column as for the Gram, x_rj = 2^E_j xt_rj (oz_split.cu).  Moving
-// the column scale into V, Y_rc = sum_j xt_rj (2^E_j V_jc) = 2^F_c sum_j xt_rj vt_jc
-// with 2^F_c > max_j 2^E_j |V_jc| and vt_jc = 2^(E_j - F_c) V_jc < 1, split into 7
-// base-128 digits the same way (oz_vsplit_kernel below: the digits of V_jc against
-// the bound 2^(F_c - E_j), so nothing overflows).  Level sums over the columns are
-// exact integers below 2^24 for up to kKBlock = 448 columns; longer rows are cut
-// into 448-column blocks whose level sums are flushed exactly into int64 sums as
-// in the Gram kernel, and Y_rc = 2^(F_c - 56) (hi 2^28 + lo) scale_c is rounded
-// once to FP64.
+// X is split per column as for the Gram, x_rj = 2^E_j xt_rj (oz_common.cuh).
+// Moving the column scale into V, Y_rc = sum_j xt_rj (2^E_j V_jc) = 2^F_c sum_j
+// xt_rj vt_jc with 2^F_c > max_j 2^E_j |V_jc| and vt_jc = 2^(E_j - F_c) V_jc, split
+// into 7 base-128 digits the same way (oz_vsplit_kernel: the digits of V_jc
+// against the bound 2^(F_c - E_j), so nothing overflows).  Level sums over the
+// columns are exact integers below 2^24 for up to 448 columns; longer rows are cut
+// into 448-column blocks whose level sums are flushed exactly into int64 sums, and
+// Y_rc = 2^(F_c - 56) (hi 2^28 + lo) scale_c is rounded once to FP64.
 //
-// Work item = 128 rows x NT modes.  The X digit block is read as the MN-major A
-// operand (M = rows: 16 row groups x 2 column groups per 16-column stage), the V
-// digits as the K-major B operand.  One CTA per item:
-//   warp 0       bulk-copy producer (3-deep ring: 16 x 1792 B of X digits and
-//                2 x NT/8 x 896 B of V digits per 16-column stage)
-//   warp 1       TMEM owner and single-thread UMMA issuer (28 MMAs 128 x NT x 16
-//                per stage into 7 level accumulators of NT TMEM columns)
-//   warps 2..    NT/4 flusher warps (16 modes x 32 rows each)
+// Persistent kernel, one CTA per SM, looping over items (node, 128-row tile,
+// 32-mode tile).  Per 16-column stage the loader brings the FP64 X tile (128 rows x
+// 16 columns, one TMA box, zero-filled outside X) into a 5-deep staging ring and the
+// V digits (K-major B operand) into the 4-deep operand ring; the converter warps
+// write the tile's 7 digit planes into the operand ring as the MN-major A operand
+// (M = rows; row groups padded to 1808 bytes so the digit stores are conflict-free).
+// Warps:
+//   warp 0       loader (TMA X tiles, bulk copies of V digits)
+//   warp 1       TMEM owner and single-thread UMMA issuer: 28 MMAs 128 x 32 x 16
+//                per stage into 7 level accumulators; two accumulator sets, so a
+//                tile's output overlaps the next tile's products
+//   warps 2..9   converters (FP64 -> digits)
+//   warps 10..17 output (16 modes x 32 rows each)
 #include <climits>
 
 #include "hapod_internal.cuh"
@@ -29,101 +33,135 @@
 namespace hapod {
 namespace {
 
-constexpr int kStages = 3;
-constexpr int kStageA = 16 * 2 * kOzGroupBytes;  // 28672 B: 128 rows x 16 columns, all digits
-constexpr int kKBlockStages = 28;                // 448 columns between exact flushes
+constexpr int NT = 32;                              // modes per item
+constexpr int kStages = 4;
+constexpr int kRowGroupBytes = 2 * kOzGroupBytes + 16;  // padded: conflict-free digit stores
+constexpr int kStageA = 16 * kRowGroupBytes;        // 128 rows x 16 columns, all digits
+constexpr int kStageB = 2 * (NT / 8) * kOzGroupBytes;
+constexpr int kStageBytes = kStageA + kStageB;
+constexpr int kXSlots = 5;                         // FP64 staging ring (TMA boxes of 128 rows x 16 columns)
+constexpr int kXSlotBytes = 128 * 16 * 8;
+constexpr int kSmemBytes = kStages * kStageBytes + kXSlots * kXSlotBytes + 128;
+constexpr int kKBlockStages = 28;                   // 448 columns between exact flushes
 constexpr int kLevels = 7;
-
-template <int NT>
-struct Cfg {
-  static constexpr int kStageB = 2 * (NT / 8) * kOzGroupBytes;
-  static constexpr int kStageBytes = kStageA + kStageB;
-  static constexpr int kSmemBytes = kStages * kStageBytes + 128;
-  static constexpr int kFlushWarps = NT / 4;
-  static constexpr int kThreads = (2 + kFlushWarps) * 32;
-  static constexpr uint32_t kTmemCols = NT == 64 ? 512 : 256;
-};
+constexpr int kConvWarps = 8;
+constexpr int kFirstConvWarp = 2;
+constexpr int kFirstOutWarp = kFirstConvWarp + kConvWarps;
+constexpr int kOutWarps = 8;
+constexpr int kThreads = (kFirstOutWarp + kOutWarps) * 32;
+constexpr uint32_t kAccCols = kLevels * NT;         // one accumulator set
+constexpr uint32_t kTmemCols = 512;
 
 struct Bars {
-  uint64_t full[kStages];
-  uint64_t empty[kStages];
-  uint64_t acc_full;
-  uint64_t acc_empty;
+  uint64_t xfull[kXSlots];   // TMA (transaction bytes)
+  uint64_t xempty[kXSlots];  // converters (8 arrivals)
+  uint64_t vfull[kStages];   // loader (transaction bytes of the V digits)
+  uint64_t full[kStages];    // converters (8 arrivals)
+  uint64_t empty[kStages];   // MMA completion
+  uint64_t acc_full[2];
+  uint64_t acc_empty[2];    // output warps (8 arrivals)
   uint64_t mma_done;
 };
 
-template <int NT>
-__global__ void __launch_bounds__(Cfg<NT>::kThreads, 1)
-    modes_oz_kernel(const OzModesJob* __restrict__ jobs, int njobs, int* err) {
-  using C = Cfg<NT>;
+__device__ __forceinline__ int find_job(const OzModesJob* jobs, int njobs, int64_t item) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].item_base <= item) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    modes_oz_kernel(const OzModesJob* __restrict__ jobs, const CUtensorMap* __restrict__ maps, int njobs,
+                    int64_t total_items, int* err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   __shared__ Bars bars;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
-
-  const int64_t b = blockIdx.x + (int64_t)blockIdx.y * gridDim.x;
-  int jlo = 0, jhi = njobs - 1;
-  while (jlo < jhi) {
-    const int mid = (jlo + jhi + 1) >> 1;
-    if (jobs[mid].item_base <= b) jlo = mid; else jhi = mid - 1;
-  }
-  const OzModesJob J = jobs[jlo];
-  const int64_t local = b - J.item_base;
-  if (local >= (int64_t)J.row_tiles * J.n_tiles) return;
-  const int64_t rt = local % J.row_tiles;
-  const int nt = (int)(local / J.row_tiles);
-  const int rg0 = (int)(rt * 16);
-  const int nrg = min(16, J.RG - rg0);  // row groups present in this tile
-  const int nst = J.CGp / 2;            // 16-column stages
-  const int nkb = (nst + kKBlockStages - 1) / kKBlockStages;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  auto stage_a = [&](int s) -> uint8_t* { return smem + (size_t)s * C::kStageBytes; };
-  auto stage_b = [&](int s) -> uint8_t* { return smem + (size_t)s * C::kStageBytes + kStageA; };
+  auto stage_a = [&](int s) -> uint8_t* { return smem + (size_t)s * kStageBytes; };
+  auto stage_b = [&](int s) -> uint8_t* { return smem + (size_t)s * kStageBytes + kStageA; };
 
   if (tid == 0) {
+    for (int s = 0; s < kXSlots; ++s) {
+      tc::mbar_init(&bars.xfull[s], 1);
+      tc::mbar_init(&bars.xempty[s], kConvWarps);
+    }
     for (int s = 0; s < kStages; ++s) {
-      tc::mbar_init(&bars.full[s], 1);
+      tc::mbar_init(&bars.vfull[s], 1);
+      tc::mbar_init(&bars.full[s], kConvWarps);
       tc::mbar_init(&bars.empty[s], 1);
     }
-    tc::mbar_init(&bars.acc_full, 1);
-    tc::mbar_init(&bars.acc_empty, C::kFlushWarps);
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&bars.acc_full[b], 1);
+      tc::mbar_init(&bars.acc_empty[b], kOutWarps);
+    }
     tc::mbar_init(&bars.mma_done, 1);
     abort_flag = 0;
     tc::mbar_fence_init();
   }
-  if (warp == 1) tc::tmem_alloc(&tmem_base, C::kTmemCols);
+  if (warp == 1) tc::tmem_alloc(&tmem_base, kTmemCols);
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t tbase = tmem_base;
 
+  // Every role walks the same item sequence; `gk` counts 16-column stages over it.
+  double* xs = reinterpret_cast<double*>(smem + (size_t)kStages * kStageBytes);
   if (warp == 0) {
-    // ------------------------------------------------------------ producer
+    // ------------------------------------------------------------ loader: X tiles (TMA), V digits
     if (lane == 0) {
-      const uint8_t* xd = reinterpret_cast<const uint8_t*>(J.xdig);
-      const uint8_t* vd = reinterpret_cast<const uint8_t*>(J.vdig);
-      const uint32_t bytes = (uint32_t)nrg * (2 * kOzGroupBytes) + C::kStageB;
-      int issued = 0;
-      for (int k = 0; k < nst; ++k) {
-        const int s = k % kStages;
-        if (k >= kStages && !tc::mbar_wait(&bars.empty[s], ((k / kStages) - 1) & 1, &abort_flag, err)) break;
-        tc::mbar_expect_tx(&bars.full[s], bytes);
-        for (int q = 0; q < nrg; ++q)
-          tc::bulk_load(stage_a(s) + q * (2 * kOzGroupBytes),
-                        xd + ((int64_t)(rg0 + q) * J.CGp + 2 * k) * kOzGroupBytes, 2 * kOzGroupBytes, &bars.full[s]);
-#pragma unroll
-        for (int q = 0; q < 2; ++q)
-          tc::bulk_load(stage_b(s) + q * (C::kStageB / 2),
-                        vd + ((int64_t)(2 * k + q) * J.NG + nt * (NT / 8)) * kOzGroupBytes, C::kStageB / 2,
-                        &bars.full[s]);
-        issued = k + 1;
-      }
-      if (abort_flag) {
-        for (int k = max(0, issued - kStages); k < issued; ++k) {
-          const long long t0 = clock64();
-          while (!tc::mbar_try(&bars.full[k % kStages], (k / kStages) & 1) && clock64() - t0 < tc::kWaitBudget) {
+      int64_t gx = 0, gv = 0;  // X tiles and V stages issued
+      int last_job = -1;
+      for (int64_t it = blockIdx.x; it < total_items && !abort_flag; it += gridDim.x) {
+        const int jb = find_job(jobs, njobs, it);
+        const OzModesJob& J = jobs[jb];
+        if (jb != last_job) {
+          tc::tensormap_acquire(maps + jb);
+          last_job = jb;
+        }
+        const int64_t local = it - J.item_base;
+        const int row0 = (int)((local % J.row_tiles) * 128);
+        const int nt = (int)(local / J.row_tiles);
+        const uint8_t* vd = reinterpret_cast<const uint8_t*>(J.vdig);
+        const int nst = (J.m + 15) / 16;
+        bool ok = true;
+        for (int k = 0; k < nst; ++k) {
+          const int x = (int)(gx % kXSlots);
+          if (gx >= kXSlots && !tc::mbar_wait(&bars.xempty[x], ((gx / kXSlots) - 1) & 1, &abort_flag, err)) {
+            ok = false;
+            break;
           }
+          tc::mbar_expect_tx(&bars.xfull[x], kXSlotBytes);
+          tc::tma_load_2d(xs + (size_t)x * (kXSlotBytes / 8), maps + jb, row0, 16 * k, &bars.xfull[x]);
+          ++gx;
+          const int s = (int)(gv % kStages);
+          if (gv >= kStages && !tc::mbar_wait(&bars.empty[s], ((gv / kStages) - 1) & 1, &abort_flag, err)) {
+            ok = false;
+            break;
+          }
+          tc::mbar_expect_tx(&bars.vfull[s], kStageB);
+#pragma unroll
+          for (int q = 0; q < 2; ++q)
+            tc::bulk_load(stage_b(s) + q * (kStageB / 2),
+                          vd + ((int64_t)(2 * k + q) * J.NG + nt * (NT / 8)) * kOzGroupBytes, kStageB / 2,
+                          &bars.vfull[s]);
+          ++gv;
+        }
+        if (!ok) break;
+      }
+      // copies in flight must land before shared memory is released
+      for (int64_t k = max((int64_t)0, gv - kStages); k < gv; ++k) {
+        const long long t0 = clock64();
+        while (!tc::mbar_try(&bars.vfull[k % kStages], (k / kStages) & 1) && clock64() - t0 < tc::kWaitBudget) {
+        }
+      }
+      const int64_t gk = gx;
+      for (int64_t k = max((int64_t)0, gk - kXSlots); k < gk; ++k) {
+        const long long t0 = clock64();
+        while (!tc::mbar_try(&bars.xfull[k % kXSlots], (k / kXSlots) & 1) && clock64() - t0 < tc::kWaitBudget) {
         }
       }
     }
@@ -131,71 +169,177 @@ __global__ void __launch_bounds__(Cfg<NT>::kThreads, 1)
     // ------------------------------------------------------------ UMMA issuer
     if (lane == 0) {
       constexpr uint32_t idesc = tc::idesc_bf16_f32_major(128, NT, 1, 0);
-      for (int k = 0; k < nst; ++k) {
-        const int s = k % kStages;
-        const int pos = k % kKBlockStages;
-        if (pos == 0 && k > 0 && !tc::mbar_wait(&bars.acc_empty, ((k / kKBlockStages) - 1) & 1, &abort_flag, err))
-          break;
-        if (!tc::mbar_wait(&bars.full[s], (k / kStages) & 1, &abort_flag, err)) break;
-        tc::tc_fence_after();
-        const uint32_t a0 = tc::smem_u32(stage_a(s)), b0 = tc::smem_u32(stage_b(s));
+      int64_t gk = 0;
+      int uses[2] = {0, 0};  // K-blocks accumulated per accumulator set
+      int tile = 0;
+      bool ok = true;
+      for (int64_t it = blockIdx.x; it < total_items && ok; it += gridDim.x, ++tile) {
+        const OzModesJob& J = jobs[find_job(jobs, njobs, it)];
+        const int nst = (J.m + 15) / 16;
+        const int b = tile & 1;
+        const uint32_t acc = tbase + (uint32_t)b * kAccCols;
+        for (int k = 0; k < nst && ok; ++k, ++gk) {
+          const int s = (int)(gk % kStages);
+          const int pos = k % kKBlockStages;
+          if (pos == 0 && uses[b] > 0 &&
+              !tc::mbar_wait(&bars.acc_empty[b], (uses[b] - 1) & 1, &abort_flag, err)) {
+            ok = false;
+            break;
+          }
+          if (!tc::mbar_wait(&bars.vfull[s], (gk / kStages) & 1, &abort_flag, err) ||
+              !tc::mbar_wait(&bars.full[s], (gk / kStages) & 1, &abort_flag, err)) {
+            ok = false;
+            break;
+          }
+          tc::tc_fence_after();
+          const uint32_t a0 = tc::smem_u32(stage_a(s)), b0 = tc::smem_u32(stage_b(s));
 #pragma unroll
-        for (int lv = 2; lv <= 8; ++lv) {
-          const int t_lo = lv - 7 > 1 ? lv - 7 : 1;
-          const int t_hi = lv - 1 < 7 ? lv - 1 : 7;
+          for (int lv = 2; lv <= 8; ++lv) {
+            const int t_lo = lv - 7 > 1 ? lv - 7 : 1;
+            const int t_hi = lv - 1 < 7 ? lv - 1 : 7;
 #pragma unroll
-          for (int t = t_lo; t <= t_hi; ++t) {
-            const int u = lv - t;
-            // A (MN-major): LBO = column-group stride (K), SBO = row-group stride (M);
-            // B (K-major): LBO = column-group stride (K), SBO = mode-group stride (N)
-            tc::umma_bf16(tbase + (uint32_t)((lv - 2) * NT),
-                          tc::ns_desc(a0 + (uint32_t)(t - 1) * 128u, kOzGroupBytes, 2 * kOzGroupBytes),
-                          tc::ns_desc(b0 + (uint32_t)(u - 1) * 128u, C::kStageB / 2, kOzGroupBytes), idesc,
-                          (pos == 0 && t == t_lo) ? 0u : 1u);
+            for (int t = t_lo; t <= t_hi; ++t) {
+              const int u = lv - t;
+              // A (MN-major): LBO = column-group stride (K), SBO = padded row-group stride (M);
+              // B (K-major): LBO = column-group stride (K), SBO = mode-group stride (N)
+              tc::umma_bf16(acc + (uint32_t)((lv - 2) * NT),
+                            tc::ns_desc(a0 + (uint32_t)(t - 1) * 128u, kOzGroupBytes, kRowGroupBytes),
+                            tc::ns_desc(b0 + (uint32_t)(u - 1) * 128u, kStageB / 2, kOzGroupBytes), idesc,
+                            (pos == 0 && t == t_lo) ? 0u : 1u);
+            }
+          }
+          tc::umma_commit(&bars.empty[s]);
+          if (pos == kKBlockStages - 1 || k == nst - 1) {
+            tc::umma_commit(&bars.acc_full[b]);
+            ++uses[b];
           }
         }
-        tc::umma_commit(&bars.empty[s]);
-        if (pos == kKBlockStages - 1 || k == nst - 1) tc::umma_commit(&bars.acc_full);
       }
       tc::umma_commit(&bars.mma_done);
       const long long t0 = clock64();
       while (!tc::mbar_try(&bars.mma_done, 0) && clock64() - t0 < tc::kWaitBudget) {
       }
     }
-  } else {
-    // ------------------------------------------------------------ flushers + output
-    const int q = warp & 3;
-    const int cw = (warp - 2) >> 2;  // 16-mode slice of the NT-mode tile
-    const uint32_t lanes = (uint32_t)(32 * q) << 16;
-    long long hi[16], lo[16];
-#pragma unroll
-    for (int c = 0; c < 16; ++c) hi[c] = lo[c] = 0;
-    bool ok = true;
-    for (int kb = 0; kb < nkb; ++kb) {
-      if (!tc::mbar_wait_warp(&bars.acc_full, kb & 1, &abort_flag, err)) {
-        ok = false;
-        break;
-      }
-      tc::tc_fence_after();
-#pragma unroll
-      for (int lv = 0; lv < kLevels; ++lv) {
-        float v[16];
-        tc::tmem_ld16(tbase + lanes + (uint32_t)(lv * NT + 16 * cw), v);
-        tc::tmem_wait_ld();
-        const long long w = lv < 3 ? (1ll << (7 * (2 - lv))) : (1ll << (7 * (6 - lv)));
-#pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const long long x = (long long)__float2int_rn(v[c]) * w;
-          if (lv < 3) hi[c] += x; else lo[c] += x;
+  } else if (warp < kFirstOutWarp) {
+    // ------------------------------------------------------------ converters
+    // warp cw: columns 2 cw, 2 cw + 1 of each stage; lane: rows 4 lane .. 4 lane + 3
+    // (one 8-byte half of a 16-byte core-matrix row per digit plane and column).
+    const int cw = warp - kFirstConvWarp;
+    int64_t gk = 0;
+    for (int64_t it = blockIdx.x; it < total_items && !abort_flag; it += gridDim.x) {
+      const OzModesJob& J = jobs[find_job(jobs, njobs, it)];
+      const int nst = (J.m + 15) / 16;
+      bool ok = true;
+      for (int k = 0; k < nst; ++k, ++gk) {
+        const int x = (int)(gk % kXSlots);
+        const int s = (int)(gk % kStages);
+        if (!tc::mbar_wait_warp(&bars.xfull[x], (gk / kXSlots) & 1, &abort_flag, err)) {
+          ok = false;
+          break;
         }
+        const double* xsl = xs + (size_t)x * (kXSlotBytes / 8);
+        double v[2][4];
+        int E[2];
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) {
+          const int jl = 2 * cw + jj;
+          const int j = 16 * k + jl;
+          E[jj] = j < J.m ? J.exps[j] : kOzNonFinite;
+          const double2* src = reinterpret_cast<const double2*>(xsl + jl * 128 + 4 * lane);
+          const double2 a = src[0], b2 = src[1];
+          v[jj][0] = a.x;
+          v[jj][1] = a.y;
+          v[jj][2] = b2.x;
+          v[jj][3] = b2.y;
+        }
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&bars.xempty[x]);
+        // digits of 4 consecutive rows, packed two bf16 per word
+        uint32_t w[2][kOzDigits][2];
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            uint32_t d[kOzDigits];
+            if (E[jj] != kOzNonFinite) {
+              oz_digits(v[jj][i], E[jj], d);
+            } else {
+#pragma unroll
+              for (int q = 0; q < kOzDigits; ++q) d[q] = 0u;
+            }
+#pragma unroll
+            for (int q = 0; q < kOzDigits; ++q) {
+              if (i & 1)
+                w[jj][q][i >> 1] |= d[q] << 16;
+              else
+                w[jj][q][i >> 1] = d[q];
+            }
+          }
+        }
+        if (gk >= kStages && !tc::mbar_wait_warp(&bars.empty[s], ((gk / kStages) - 1) & 1, &abort_flag, err)) {
+          ok = false;
+          break;
+        }
+        uint8_t* A = stage_a(s) + (lane >> 1) * kRowGroupBytes + (lane & 1) * 8;
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) {
+          const int jl = 2 * cw + jj;
+          uint8_t* p = A + (jl >> 3) * kOzGroupBytes + (jl & 7) * 16;
+#pragma unroll
+          for (int q = 0; q < kOzDigits; ++q)
+            *reinterpret_cast<uint2*>(p + q * 128) = make_uint2(w[jj][q][0], w[jj][q][1]);
+        }
+        tc::fence_async_smem();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&bars.full[s]);
       }
-      tc::tc_fence_before();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&bars.acc_empty);
+      if (!ok) break;
     }
-    if (__all_sync(0xffffffffu, ok && !abort_flag)) {
-      const int64_t r = (int64_t)rg0 * 8 + 32 * q + lane;
-      if (r < J.rows) {
+  } else {
+    // ------------------------------------------------------------ output
+    const int q = warp & 3;
+    const int cw = (warp - kFirstOutWarp) >> 2;  // 16-mode half of the 32-mode tile
+    const uint32_t lanes = (uint32_t)(32 * q) << 16;
+    int uses[2] = {0, 0};
+    int tile = 0;
+    for (int64_t it = blockIdx.x; it < total_items; it += gridDim.x, ++tile) {
+      const OzModesJob& J = jobs[find_job(jobs, njobs, it)];
+      const int64_t local = it - J.item_base;
+      const int64_t rt = local % J.row_tiles;
+      const int nt = (int)(local / J.row_tiles);
+      const int nkb = ((J.m + 15) / 16 + kKBlockStages - 1) / kKBlockStages;
+      const int b = tile & 1;
+      const uint32_t acc = tbase + lanes + (uint32_t)b * kAccCols + (uint32_t)(16 * cw);
+      long long hi[16], lo[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) hi[c] = lo[c] = 0;
+      bool ok = true;
+      for (int kb = 0; kb < nkb; ++kb) {
+        if (!tc::mbar_wait_warp(&bars.acc_full[b], uses[b] & 1, &abort_flag, err)) {
+          ok = false;
+          break;
+        }
+        tc::tc_fence_after();
+#pragma unroll
+        for (int lv = 0; lv < kLevels; ++lv) {
+          float v[16];
+          tc::tmem_ld16(acc + (uint32_t)(lv * NT), v);
+          tc::tmem_wait_ld();
+          const long long w = lv < 3 ? (1ll << (7 * (2 - lv))) : (1ll << (7 * (6 - lv)));
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            const long long xv = (long long)__float2int_rn(v[c]) * w;
+            if (lv < 3) hi[c] += xv; else lo[c] += xv;
+          }
+        }
+        tc::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&bars.acc_empty[b]);
+        ++uses[b];
+      }
+      if (!__all_sync(0xffffffffu, ok && !abort_flag)) break;
+      const int64_t r = rt * 128 + 32 * q + lane;
+      if (r < J.n) {
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
           const int col = nt * NT + 16 * cw + c;
@@ -216,7 +360,7 @@ __global__ void __launch_bounds__(Cfg<NT>::kThreads, 1)
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
-  if (warp == 1) tc::tmem_dealloc(tbase, C::kTmemCols);
+  if (warp == 1) tc::tmem_dealloc(tbase, kTmemCols);
 }
 
 // One block per mode column c (of kpad = 8 NG): F_c = max_j (E_j + e(V_jc)) with
@@ -282,34 +426,22 @@ __global__ void __launch_bounds__(256) oz_vsplit_kernel(const OzVSplitJob* __res
   }
 }
 
-dim3 grid_for(int64_t blocks) {
-  const int64_t gx = blocks < 65535 ? blocks : 65535;
-  return dim3((unsigned)gx, (unsigned)((blocks + gx - 1) / gx));
-}
+}  // namespace
 
-template <int NT>
-cudaError_t launch_nt(const OzModesJob* jobs_dev, int njobs, int64_t total_items, int* err_flag, cudaStream_t s) {
+int oz_modes_tile(int) { return NT; }
+
+cudaError_t launch_modes_oz(const OzModesJob* jobs_dev, const CUtensorMap* maps_dev, int njobs, int64_t total_items,
+                            int* err_flag, cudaStream_t s) {
+  if (njobs <= 0 || total_items <= 0) return cudaSuccess;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e =
-        cudaFuncSetAttribute(modes_oz_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<NT>::kSmemBytes);
+    cudaError_t e = cudaFuncSetAttribute(modes_oz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  modes_oz_kernel<NT><<<grid_for(total_items), Cfg<NT>::kThreads, Cfg<NT>::kSmemBytes, s>>>(jobs_dev, njobs, err_flag);
+  const int grid = (int)(total_items < kNumSMs ? total_items : kNumSMs);
+  modes_oz_kernel<<<grid, kThreads, kSmemBytes, s>>>(jobs_dev, maps_dev, njobs, total_items, err_flag);
   return cudaGetLastError();
-}
-
-}  // namespace
-
-int oz_modes_tile(int k) { return k <= 32 ? 32 : 64; }
-
-cudaError_t launch_modes_oz(const OzModesJob* jobs_dev, int njobs, int64_t total_items, int nt, int* err_flag,
-                            cudaStream_t s) {
-  if (njobs <= 0 || total_items <= 0) return cudaSuccess;
-  if (nt == 32) return launch_nt<32>(jobs_dev, njobs, total_items, err_flag, s);
-  if (nt == 64) return launch_nt<64>(jobs_dev, njobs, total_items, err_flag, s);
-  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_oz_vsplit(const OzVSplitJob* jobs_dev, int njobs, int64_t total_cols, cudaStream_t s) {
