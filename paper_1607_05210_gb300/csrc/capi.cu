@@ -361,7 +361,7 @@ bool step_gram_oz(Env& env, std::vector<Work*>& ws) {
       const int64_t blk = kOzKBlock / 16;
       int64_t sps = (stages + want - 1) / want;
       sps = std::max<int64_t>(blk, (sps + blk - 1) / blk * blk);
-      sps = std::min<int64_t>(sps, (int64_t)1 << 22);  // int64 flush sums stay exact (< 2^26 rows)
+      sps = std::min<int64_t>(sps, (int64_t)1 << 18);  // int64 flush sums stay exact (<= 2^22 rows)
       C.sps = (int32_t)sps;
       C.splits = (int32_t)((stages + sps - 1) / sps);
       C.slot0 = node_slots[C.node];

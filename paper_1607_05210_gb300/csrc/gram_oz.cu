@@ -2,18 +2,18 @@
 // from the exact digit planes of X (oz_split.cu) on the 5th-generation tensor cores
 // (tcgen05 kind::f16, bf16 x bf16 -> FP32).
 //
-// With x_ri = 2^E_i sum_t d_t(r,i) 2^(-7t),
-//   G_ij = 2^(E_i + E_j) sum_{s=2}^{8} 2^(-7 s) L_s(i, j),
+// With x_ri = 2^(E_i+1) sum_t d_t(r,i) 2^(-8t) (7 balanced base-256 digits),
+//   G_ij = 2^(E_i + E_j + 2) sum_{s=2}^{8} 2^(-8 s) L_s(i, j),
 //   L_s(i, j) = sum_r sum_{t+u=s} d_t(r,i) d_u(r,j),
-// keeping the 28 digit pairs with t + u <= 8 (the dropped pairs weigh < 2^-49 of
-// 2^(E_i + E_j) per row, the same order as the truncation of the digits).  Over a
-// block of 256 rows every level sum is an integer below 9 * 2^20 < 2^24, so the FP32
-// tensor-core accumulation of digit products is exact; after each block the seven
-// level accumulators are converted to integers and added exactly into two int64
-// fixed-point sums per entry:  hi = sum (L_2 2^14 + L_3 2^7 + L_4),
-// lo = sum (L_5 2^21 + L_6 2^14 + L_7 2^7 + L_8), G_ij = 2^(E_i+E_j-56) (hi 2^28 + lo),
-// rounded once to FP64.  The only rounding of the whole Gram is that final one and
-// the FP64 sum over row splits.
+// keeping the 28 digit pairs with t + u <= 8 (the dropped pairs weigh < 2^-57 of
+// 2^(E_i + E_j) per row, below the truncation of the digits).  Over a block of 128
+// rows every level sum is an integer below 7 * 2^21 < 2^24, so the FP32 tensor-core
+// accumulation of digit products is exact; after each block the seven level
+// accumulators are converted to integers and added exactly into two int64
+// fixed-point sums per entry: hi = sum (L_2 2^16 + L_3 2^8 + L_4),
+// lo = sum (L_5 2^24 + L_6 2^16 + L_7 2^8 + L_8), G_ij = 2^(E_i+E_j-62) (hi 2^32 + lo),
+// rounded once to FP64.  The only rounding of the whole Gram is that final one and the FP64
+// sum over row splits.
 //
 // Work item = one 128 x 64 tile (columns 128 I.. x 64 J..) over one row split.  One
 // CTA per item, 18 warps:
@@ -21,10 +21,11 @@
 //                planes of the 128 A columns and the 64 B columns, 42 KB)
 //   warp 1       TMEM owner and single-thread UMMA issuer (28 MMAs of 128 x 64 x 16
 //                per stage into 7 level accumulators of 64 TMEM columns)
-//   warps 2..17  flushers: after every 256-row block, 16 columns x 32 lanes each
+//   warps 2..17  flushers: after every 128-row block, 16 columns x 32 lanes each
 // Every mbarrier wait is bounded: a timeout raises the error flag, the CTA drains
 // its copies and MMAs and frees TMEM.
 #include "hapod_internal.cuh"
+#include "oz_common.cuh"
 #include "tc_common.cuh"
 
 namespace hapod {
@@ -41,7 +42,7 @@ constexpr int kBlockStages = kOzKBlock / 16;                  // stages per exac
 constexpr int kThreads = 576;
 constexpr int kFirstFlushWarp = 2;
 constexpr int kFlushWarps = 16;
-constexpr int kLevels = 7;
+constexpr int kLevels = kOzLevels;
 constexpr uint32_t kLevelCols = 64;
 constexpr uint32_t kTmemCols = 512;
 
@@ -151,9 +152,9 @@ __global__ void __launch_bounds__(kThreads, 1) gram_oz_kernel(const OzGramJob* _
         tc::tc_fence_after();
         const uint32_t a0 = tc::smem_u32(stage_a(s)), b0 = tc::smem_u32(stage_b(s));
 #pragma unroll
-        for (int lv = 2; lv <= 8; ++lv) {
-          const int t_lo = lv - 7 > 1 ? lv - 7 : 1;
-          const int t_hi = lv - 1 < 7 ? lv - 1 : 7;
+        for (int lv = 2; lv <= kLevels + 1; ++lv) {
+          const int t_lo = 1;
+          const int t_hi = lv - 1;
 #pragma unroll
           for (int t = t_lo; t <= t_hi; ++t) {
             const int u = lv - t;
@@ -192,8 +193,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_oz_kernel(const OzGramJob* _
         float v[16];
         tc::tmem_ld16(tbase + lanes + (uint32_t)lv * kLevelCols + (uint32_t)(16 * cw), v);
         tc::tmem_wait_ld();
-        // level lv + 2: weight 2^(7 (4 - level)) in hi (levels 2..4), 2^(7 (8 - level)) in lo
-        const long long w = lv < 3 ? (1ll << (7 * (2 - lv))) : (1ll << (7 * (6 - lv)));
+        const long long w = oz_level_weight(lv);
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
           const long long x = (long long)__float2int_rn(v[c]) * w;
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_oz_kernel(const OzGramJob* _
           if (Ei == kOzNonFinite || Ej == kOzNonFinite)
             v = __longlong_as_double(0x7FF8000000000000ll);
           else
-            v = scalbn((double)hi[c] * 268435456.0 + (double)lo[c], Ei + Ej - 56);
+            v = oz_combine(hi[c], lo[c], Ei + Ej - 62);
         }
         out[(size_t)j * mp + i] = v;
       }

@@ -80,12 +80,13 @@ bool encode_colmajor_f32(CUtensorMap* out, const void* base, int64_t rows, int64
                          int box_cols, bool swizzle128);
 
 // ---------------------------------------------------------------- Gram, digit-slice FP64 form
-// X (FP64) is represented exactly up to 2^-49 of each column's power-of-two bound
-// 2^E_j by 7 signed 7-bit digits per value (Ozaki et al. 2012 error-free splitting);
-// digit products are exact in bf16 x bf16 -> FP32 tensor-core arithmetic and their
-// level sums (t + u = s) stay exact integers over kOzKBlock rows.
+// X (FP64) is represented exactly up to 2^-55 of each column's power-of-two bound
+// 2^E_j by 7 balanced base-256 digits per value (Ozaki et al. 2012 error-free
+// splitting); digit products are exact in bf16 x bf16 -> FP32 tensor-core arithmetic
+// and their level sums (t + u = s <= 8) stay exact integers over kOzKBlock rows.
 constexpr int kOzDigits = 7;
-constexpr int kOzKBlock = 256;                 // rows between exact flushes
+constexpr int kOzLevels = 7;                   // s = 2..8
+constexpr int kOzKBlock = 128;                 // rows (columns for X V) between exact flushes
 constexpr int kOzGroupBytes = kOzDigits * 128; // one 8 x 8 block of all digit planes
 constexpr int32_t kOzNonFinite = 0x7FFFFFFF;   // exponent marker of a column holding Inf / NaN
 
@@ -102,7 +103,7 @@ struct OzColJob {
 cudaError_t launch_oz_colmax(const OzColJob* jobs_dev, int njobs, int64_t total_cols, cudaStream_t s);
 
 // Digit planes of rows [r0, r0 + rows) of X into `digits`, layout
-// [row group of 8][column group of 8 (CGp)][digit 7][column % 8][row % 8] (bf16),
+// [row group of 8][column group of 8 (CGp)][digit][column % 8][row % 8] (bf16),
 // RG = 2 ceil(rows / 16) row groups; rows >= `rows` and columns >= m are zero.
 struct OzSplitJob {
   const double* X;
@@ -149,7 +150,7 @@ struct OzReduceJob {
 cudaError_t launch_oz_reduce(const OzReduceJob* jobs_dev, int njobs, int64_t total_cols, cudaStream_t s);
 
 // X V of the digit-slice form: V_k (FP64 m x k, ld ldv) in digits against 2^(F_c - E_j)
-// (vdig: [CGp][NG][7][8][8], fexp: F_c per mode column, NG = kpad / 8).
+// (vdig: [CGp][NG][digit][8][8], fexp: F_c per mode column, NG = kpad / 8).
 struct OzVSplitJob {
   const double* V;
   int64_t ldv;

@@ -5,18 +5,17 @@
 // X is split per column as for the Gram, x_rj = 2^E_j xt_rj (oz_common.cuh).
 // Moving the column scale into V, Y_rc = sum_j xt_rj (2^E_j V_jc) = 2^F_c sum_j
 // xt_rj vt_jc with 2^F_c > max_j 2^E_j |V_jc| and vt_jc = 2^(E_j - F_c) V_jc, split
-// into 7 base-128 digits the same way (oz_vsplit_kernel: the digits of V_jc
-// against the bound 2^(F_c - E_j), so nothing overflows).  Level sums over the
-// columns are exact integers below 2^24 for up to 448 columns; longer rows are cut
-// into 448-column blocks whose level sums are flushed exactly into int64 sums, and
-// Y_rc = 2^(F_c - 56) (hi 2^28 + lo) scale_c is rounded once to FP64.
+// into 7 base-256 digits the same way (oz_vsplit_kernel: the digits of V_jc against
+// the bound 2^(F_c - E_j), so nothing overflows).  The 28 digit pairs of level
+// t + u <= 8 are summed exactly over blocks of 128 columns, flushed exactly into
+// int64 sums, and Y_rc = 2^(F_c - 62) (hi 2^32 + lo) scale_c is rounded once to FP64.
 //
 // Persistent kernel, one CTA per SM, looping over items (node, 128-row tile,
 // 32-mode tile).  Per 16-column stage the loader brings the FP64 X tile (128 rows x
 // 16 columns, one TMA box, zero-filled outside X) into a 5-deep staging ring and the
 // V digits (K-major B operand) into the 4-deep operand ring; the converter warps
 // write the tile's 7 digit planes into the operand ring as the MN-major A operand
-// (M = rows; row groups padded to 1808 bytes so the digit stores are conflict-free).
+// (M = rows; row groups padded by 16 bytes so the digit stores are conflict-free).
 // Warps:
 //   warp 0       loader (TMA X tiles, bulk copies of V digits)
 //   warp 1       TMEM owner and single-thread UMMA issuer: 28 MMAs 128 x 32 x 16
@@ -42,8 +41,8 @@ constexpr int kStageBytes = kStageA + kStageB;
 constexpr int kXSlots = 5;                         // FP64 staging ring (TMA boxes of 128 rows x 16 columns)
 constexpr int kXSlotBytes = 128 * 16 * 8;
 constexpr int kSmemBytes = kStages * kStageBytes + kXSlots * kXSlotBytes + 128;
-constexpr int kKBlockStages = 28;                   // 448 columns between exact flushes
-constexpr int kLevels = 7;
+constexpr int kKBlockStages = kOzKBlock / 16;       // 128 columns between exact flushes
+constexpr int kLevels = kOzLevels;
 constexpr int kConvWarps = 8;
 constexpr int kFirstConvWarp = 2;
 constexpr int kFirstOutWarp = kFirstConvWarp + kConvWarps;
@@ -194,9 +193,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc::tc_fence_after();
           const uint32_t a0 = tc::smem_u32(stage_a(s)), b0 = tc::smem_u32(stage_b(s));
 #pragma unroll
-          for (int lv = 2; lv <= 8; ++lv) {
-            const int t_lo = lv - 7 > 1 ? lv - 7 : 1;
-            const int t_hi = lv - 1 < 7 ? lv - 1 : 7;
+          for (int lv = 2; lv <= kLevels + 1; ++lv) {
+            const int t_lo = 1;
+            const int t_hi = lv - 1;
 #pragma unroll
             for (int t = t_lo; t <= t_hi; ++t) {
               const int u = lv - t;
@@ -255,24 +254,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&bars.xempty[x]);
         // digits of 4 consecutive rows, packed two bf16 per word
-        uint32_t w[2][kOzDigits][2];
+        uint32_t w[2][2][kOzDigits];
 #pragma unroll
         for (int jj = 0; jj < 2; ++jj) {
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            uint32_t d[kOzDigits];
+          for (int h = 0; h < 2; ++h) {
             if (E[jj] != kOzNonFinite) {
-              oz_digits(v[jj][i], E[jj], d);
+              oz_digits2(v[jj][2 * h], v[jj][2 * h + 1], E[jj], w[jj][h]);
             } else {
 #pragma unroll
-              for (int q = 0; q < kOzDigits; ++q) d[q] = 0u;
-            }
-#pragma unroll
-            for (int q = 0; q < kOzDigits; ++q) {
-              if (i & 1)
-                w[jj][q][i >> 1] |= d[q] << 16;
-              else
-                w[jj][q][i >> 1] = d[q];
+              for (int q = 0; q < kOzDigits; ++q) w[jj][h][q] = 0u;
             }
           }
         }
@@ -287,7 +278,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           uint8_t* p = A + (jl >> 3) * kOzGroupBytes + (jl & 7) * 16;
 #pragma unroll
           for (int q = 0; q < kOzDigits; ++q)
-            *reinterpret_cast<uint2*>(p + q * 128) = make_uint2(w[jj][q][0], w[jj][q][1]);
+            *reinterpret_cast<uint2*>(p + q * 128) = make_uint2(w[jj][0][q], w[jj][1][q]);
         }
         tc::fence_async_smem();
         __syncwarp();
@@ -325,7 +316,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           float v[16];
           tc::tmem_ld16(acc + (uint32_t)(lv * NT), v);
           tc::tmem_wait_ld();
-          const long long w = lv < 3 ? (1ll << (7 * (2 - lv))) : (1ll << (7 * (6 - lv)));
+          const long long w = oz_level_weight(lv);
 #pragma unroll
           for (int c = 0; c < 16; ++c) {
             const long long xv = (long long)__float2int_rn(v[c]) * w;
@@ -349,7 +340,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (F == kOzNonFinite) {
             v = __longlong_as_double(0x7FF8000000000000ll);
           } else {
-            v = scalbn((double)hi[c] * 268435456.0 + (double)lo[c], F - 56);
+            v = oz_combine(hi[c], lo[c], F - 62);
             if (J.scale) v *= J.scale[col];
           }
           J.Y[(size_t)col * J.ldy + r] = v;

@@ -1,22 +1,19 @@
-// Digit slices of FP64 snapshots for the tensor-core FP64 form (K1/K4 of the
-// digit-slice form): the error-free splitting of Ozaki, Ogita, Oishi and Rump
-// (2012), "Error-free transformations of matrix multiplication by using fast
-// routines of matrix multiplication and its applications", specialised to a
-// fixed-point representation per column.
+// Digit slices of FP64 snapshots for the digit-slice FP64 form: the error-free
+// splitting of Ozaki, Ogita, Oishi and Rump (2012), "Error-free transformations of
+// matrix multiplication by using fast routines of matrix multiplication and its
+// applications", specialised to a fixed-point representation per column.
 //
 // Column j gets the power-of-two bound 2^E_j > max_i |x_ij|.  Every value is
-// truncated to the fixed-point integer A = floor(|x| 2^(49 - E_j)) < 2^49 and
-// written in balanced base 128 with 7 digits,
-//   A = d_1 2^42 + d_2 2^35 + ... + d_7,   d_1 in [0, 128], d_2..d_7 in [-64, 63],
-// so x = sign(x) 2^E_j sum_t d_t 2^(-7 t) up to the dropped tail (< 2^(E_j - 49)).
-// Every digit is an integer of at most 8 significant bits, exact in bf16.
+// truncated to the fixed-point integer A = floor(|x| 2^(55 - E_j)) < 2^55 and
+// written in balanced base 256 with 7 digits (oz_common.cuh),
+//   A = d_1 2^48 + d_2 2^40 + ... + d_7,   d_1 in [0, 128], d_2..d_7 in [-128, 127],
+// so x = sign(x) 2^(E_j+1) sum_t d_t 2^(-8 t) up to the dropped tail (< 2^(E_j - 55)).
 //
 // Layout of a digit block (rows [r0, r0 + rows) of one node):
 //   [row group r/8][column group j/8][digit t][j % 8][r % 8]   (bf16)
 // i.e. 8 x 8 core matrices of 16-byte rows, all 7 digits of one 8 x 8 block
 // together (896 bytes).  Read as columns-by-rows it is the K-major no-swizzle UMMA
-// layout of the Gram (K = rows); read as rows-by-columns it is the MN-major layout
-// of X V (K = columns).
+// layout of the Gram (K = rows).
 #include "hapod_internal.cuh"
 #include "oz_common.cuh"
 

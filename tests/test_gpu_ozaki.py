@@ -1,12 +1,12 @@
 """Digit-slice FP64 form (HAPOD_FP64_OZAKI) on the GPU versus the CPU oracle.
 
 The Gram is formed from an exact fixed-point representation of every column:
-x = 2^E_j * (7 signed base-128 digits), truncated below 2^(E_j - 49), with
+x = 2^E_j * (7 balanced base-256 digits), truncated below 2^(E_j - 55), with
 2^E_j > max_i |x_ij|; digit pairs of level t + u <= 8 are summed exactly.  Per
-row the product x_ri x_rj is then represented to within 2^(E_i + E_j - 47)
-(digit truncation 2 * 2^-49 plus the dropped levels < 1.01 * 2^-48.4), so
+row the product x_ri x_rj is then represented to within 2^(E_i + E_j - 53)
+(digit truncation 2 * 2^-55 plus the dropped levels < 1.01 * 6 * 2^-58), so
 
-  |G_ij - G_ref_ij| <= n 2^(E_i + E_j - 47) + 1e-13 sqrt(n) sqrt(G_ii G_jj)
+  |G_ij - G_ref_ij| <= n 2^(E_i + E_j - 53) + 1e-13 sqrt(n) sqrt(G_ii G_jj)
 
 the second term covering the rounding of the oracle's own FP64 sums and the
 final FP64 rounding of the split sums.  Inputs whose digits are exact (small
@@ -45,7 +45,7 @@ def gram_bound(X, ref):
     n = X.shape[0]
     E = col_exponents(X)
     d = np.sqrt(np.abs(np.diag(ref)))
-    return n * np.exp2(E[:, None] + E[None, :] - 47.0) + 1e-13 * math.sqrt(max(n, 1)) * np.outer(d, d)
+    return n * np.exp2(E[:, None] + E[None, :] - 53.0) + 1e-13 * math.sqrt(max(n, 1)) * np.outer(d, d)
 
 
 @pytest.mark.parametrize("n,m,ld", [(1, 1, 1), (1000, 1, 1000), (10000, 100, 10000), (3000, 130, 3001),
@@ -106,7 +106,7 @@ def test_gram_oz_nonfinite_column(H, bad):
 
 
 def test_gram_oz_row_chunks(H, monkeypatch):
-    """A 1 MiB digit workspace cuts the node into 256-row chunks (one per round)."""
+    """A 1 MiB digit workspace cuts the node into row chunks (a few per round)."""
     rng = np.random.default_rng(5)
     n, m = 20011, 130
     X = rng.standard_normal((n, m))
@@ -134,15 +134,15 @@ def test_gram_oz_empty(H):
 
 # ------------------------------------------------------------------ K4 X V
 def modes_bound(X, V, scale):
-    """Per entry: m 2^(F_c - 47) (digit truncation of X and of the rescaled V plus the
-    dropped levels, per term below 2^(F_c - 47)) + the FP64 rounding of the reference,
+    """Per entry: m 2^(F_c - 53) (digit truncation of X and of the rescaled V plus the
+    dropped levels, per term below 2^(F_c - 53)) + the FP64 rounding of the reference,
     times |scale_c|; F_c = max_j (E_j + e(V_jc)) with |V_jc| < 2^e(V_jc)."""
     m = X.shape[1]
     E = col_exponents(X)
     ev = np.where(V != 0, np.frexp(V)[1], -10 ** 6)
     F = np.max(E[:, None] + ev, axis=0)
     rn = np.sqrt(np.sum(X * X, axis=1))[:, None] * np.linalg.norm(V, axis=0)[None, :]
-    return (m * np.exp2(F - 47.0)[None, :] + 1e-13 * math.sqrt(m) * rn) * np.abs(scale)[None, :]
+    return (m * np.exp2(F - 53.0)[None, :] + 1e-13 * math.sqrt(m) * rn) * np.abs(scale)[None, :]
 
 
 @pytest.mark.parametrize("n,m,N", [(1, 3, 2), (1000, 100, 37), (4097, 130, 65), (300, 1, 1), (12345, 64, 64),
