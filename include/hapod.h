@@ -24,7 +24,7 @@
  *     the results are produced and the warning is recorded.
  *   - FP64 form (HAPOD_FP64): snapshots are IEEE double; all arithmetic is FP64.
  *     Digit-slice FP64 form (HAPOD_FP64_OZAKI): snapshots and results as in the
- *     FP64 form; the Gram and X V are formed on the bf16 tensor cores from an exact
+ *     FP64 form; the Gram and X V are formed on the fp16 tensor cores from an exact
  *     7-digit balanced base-256 fixed-point representation of each column (relative
  *     to a power-of-two bound of its largest entry, truncated below 2^-55 of it),
  *     with integer-exact accumulation and one FP64 rounding per entry.
@@ -60,7 +60,7 @@ typedef enum {
   HAPOD_FP64 = 0,           /* double snapshots, FP64 arithmetic everywhere */
   HAPOD_MIXED_BF16X3 = 1,   /* float snapshots, tensor-core (TF32 hi/lo split) Gram, FP32 X V */
   HAPOD_FP64_OZAKI = 2      /* double snapshots and results; Gram and X V from exact 8-bit
-                               digit products on the bf16 tensor cores (error-free splitting
+                               digit products on the fp16 tensor cores (error-free splitting
                                of Ozaki et al. 2012, integer-exact accumulation, one final
                                FP64 rounding per entry); eigensolver in FP64 */
 } hapod_precision;

@@ -254,7 +254,7 @@ size_t oz_digit_cap() {
 struct OzChunk {
   int node;
   int64_t r0, rows;
-  int32_t CGp, RG;
+  int32_t CGs, RG;
   size_t bytes;
   int32_t splits, sps;  // Gram: row splits and 16-row stages per split
   int64_t slot0;        // Gram: first partial slot of the chunk within its node
@@ -265,8 +265,8 @@ void oz_plan(const std::vector<Work*>& ws, std::vector<OzChunk>& chunks, std::ve
              size_t& max_round) {
   const size_t cap = oz_digit_cap();
   for (int i = 0; i < (int)ws.size(); ++i) {
-    const int32_t CGp = oz_col_groups(ws[i]->m);
-    const size_t row_bytes = (size_t)CGp * 8 * kOzDigits * 2;
+    const int32_t CGs = oz_stored_groups(ws[i]->m);
+    const size_t row_bytes = (size_t)CGs * 8 * kOzDigits * 2;
     int64_t R = (int64_t)(cap / row_bytes) / kOzKBlock * kOzKBlock;
     R = std::max<int64_t>(R, kOzKBlock);
     for (int64_t r0 = 0; r0 < ws[i]->n; r0 += R) {
@@ -274,7 +274,7 @@ void oz_plan(const std::vector<Work*>& ws, std::vector<OzChunk>& chunks, std::ve
       c.node = i;
       c.r0 = r0;
       c.rows = std::min(R, ws[i]->n - r0);
-      c.CGp = CGp;
+      c.CGs = CGs;
       c.RG = (int32_t)oz_row_groups(c.rows);
       c.bytes = (size_t)c.RG * 8 * row_bytes;
       c.splits = c.sps = 0;
@@ -287,7 +287,7 @@ void oz_plan(const std::vector<Work*>& ws, std::vector<OzChunk>& chunks, std::ve
     size_t b = a, bytes = 0;
     while (b < chunks.size() && (b == a || bytes + chunks[b].bytes <= cap)) bytes += chunks[b++].bytes;
     rounds.push_back({a, b});
-    max_round = std::max(max_round, bytes);
+    max_round = std::max(max_round, bytes + kOzDigitSlack);
     a = b;
   }
 }
@@ -303,7 +303,7 @@ OzSplitJob oz_split_job(const Work* w, const OzChunk& C, uint16_t* dblk, int64_t
   S.digits = dblk;
   S.thread_base = thread_base;
   S.m = (int32_t)w->m;
-  S.CGp = C.CGp;
+  S.CGs = C.CGs;
   return S;
 }
 
@@ -353,7 +353,7 @@ bool step_gram_oz(Env& env, std::vector<Work*>& ws) {
   for (const auto& rd : rounds) {
     // splits: about two waves of one CTA per SM over the round's tiles, whole 256-row blocks
     int64_t T = 0;
-    for (size_t c = rd.first; c < rd.second; ++c) T += oz_gram_tiles((int32_t)ws[chunks[c].node]->m, chunks[c].CGp);
+    for (size_t c = rd.first; c < rd.second; ++c) T += oz_gram_tiles((int32_t)ws[chunks[c].node]->m);
     const int64_t want = std::max<int64_t>(1, (2 * kNumSMs) / std::max<int64_t>(1, T));
     for (size_t c = rd.first; c < rd.second; ++c) {
       OzChunk& C = chunks[c];
@@ -371,7 +371,7 @@ bool step_gram_oz(Env& env, std::vector<Work*>& ws) {
   std::vector<int64_t> node_base(nw, 0);
   size_t total_partial = 0;
   for (int i = 0; i < nw; ++i) {
-    const int64_t mp = (int64_t)oz_col_groups(ws[i]->m) * 8;
+    const int64_t mp = ws[i]->m;
     node_base[i] = (int64_t)total_partial;
     total_partial += (size_t)node_slots[i] * mp * mp;
   }
@@ -391,20 +391,21 @@ bool step_gram_oz(Env& env, std::vector<Work*>& ws) {
       uint16_t* dblk = reinterpret_cast<uint16_t*>(reinterpret_cast<uint8_t*>(digits) + off);
       off += C.bytes;
       sj.push_back(oz_split_job(w, C, dblk, threads));
-      threads += (int64_t)C.RG * C.CGp * 8;
+      threads += (int64_t)C.RG * C.CGs * 8;
       OzGramJob G;
       memset(&G, 0, sizeof(G));
-      const int64_t mp = (int64_t)C.CGp * 8;
+      const int64_t mp = w->m;
       G.digits = dblk;
       G.exps = w->exps;
       G.partial = partial + node_base[C.node] + (size_t)C.slot0 * mp * mp;
       G.item_base = items;
       G.RG = C.RG;
-      G.CGp = C.CGp;
+      G.CGs = C.CGs;
       G.m = (int32_t)w->m;
+      G.mp = (int32_t)mp;
       G.splits = C.splits;
       G.stages_per_split = C.sps;
-      G.tiles = oz_gram_tiles((int32_t)w->m, C.CGp);
+      G.tiles = oz_gram_tiles((int32_t)w->m);
       items += (int64_t)C.splits * G.tiles;
       gj.push_back(G);
     }
@@ -426,7 +427,7 @@ bool step_gram_oz(Env& env, std::vector<Work*>& ws) {
       rj[i].col_base = cols;
       rj[i].slots = (int32_t)node_slots[i];
       rj[i].m = (int32_t)ws[i]->m;
-      rj[i].mp = oz_col_groups(ws[i]->m) * 8;
+      rj[i].mp = (int32_t)ws[i]->m;
       cols += ws[i]->m;
     }
     OzReduceJob* rj_d = env.upload(rj, "upload reduce jobs");

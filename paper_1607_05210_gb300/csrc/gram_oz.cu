@@ -1,6 +1,6 @@
 // K1, digit-slice FP64 form: G = X^T X (Sec. 2, Remark def:method_of_snapshots)
 // from the exact digit planes of X (oz_split.cu) on the 5th-generation tensor cores
-// (tcgen05 kind::f16, bf16 x bf16 -> FP32).
+// (tcgen05 kind::f16, fp16 x fp16 -> FP32).
 //
 // With x_ri = 2^(E_i+1) sum_t d_t(r,i) 2^(-8t) (7 balanced base-256 digits),
 //   G_ij = 2^(E_i + E_j + 2) sum_{s=2}^{8} 2^(-8 s) L_s(i, j),
@@ -15,8 +15,10 @@
 // rounded once to FP64.  The only rounding of the whole Gram is that final one and the FP64
 // sum over row splits.
 //
-// Work item = one 128 x 64 tile (columns 128 I.. x 64 J..) over one row split.  One
-// CTA per item, 18 warps:
+// Work item = one 128 x 64 tile (columns 128 I.. x 64 J..) over one row split.  The
+// digit rows hold ceil(m / 8) column groups; a block that runs past them reads the
+// next digits or the buffer's slack, which only reach tile rows / columns >= m, never
+// written back.  One CTA per item, 18 warps:
 //   warp 0       bulk-copy producer: 4-deep ring of 16-row stages (all 7 digit
 //                planes of the 128 A columns and the 64 B columns, 42 KB)
 //   warp 1       TMEM owner and single-thread UMMA issuer (28 MMAs of 128 x 64 x 16
@@ -54,13 +56,13 @@ struct Bars {
   uint64_t mma_done;
 };
 
-__device__ __forceinline__ void tile_of(int tile, int m, int CGp, int* I, int* J) {
+// tile index -> (I, J), J from 2 I up to ceil(m / 64) - 1
+__device__ __forceinline__ void tile_of(int tile, int m, int* I, int* J) {
   const int jmax = (m + 63) / 64;
   int i = 0;
-  for (; i < CGp / 16; ++i) {
+  for (;; ++i) {
     const int cnt = jmax - 2 * i;
-    if (cnt <= 0) break;
-    if (tile < cnt) break;
+    if (cnt <= 0 || tile < cnt) break;
     tile -= cnt;
   }
   *I = i;
@@ -85,7 +87,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_oz_kernel(const OzGramJob* _
   if (local >= (int64_t)J.splits * J.tiles) return;  // whole CTA leaves before any barrier
   const int sp = (int)(local / J.tiles);
   int TI, TJ;
-  tile_of((int)(local % J.tiles), J.m, J.CGp, &TI, &TJ);
+  tile_of((int)(local % J.tiles), J.m, &TI, &TJ);
   const int total_stages = J.RG / 2;
   const int st0 = sp * J.stages_per_split;
   const int nst = max(0, min(total_stages - st0, J.stages_per_split));
@@ -123,7 +125,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_oz_kernel(const OzGramJob* _
         const int64_t rg0 = 2 * (int64_t)(st0 + k);
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-          const int64_t row = (rg0 + q) * J.CGp;
+          const int64_t row = (rg0 + q) * J.CGs;  // the A / B blocks may run past the stored groups
           tc::bulk_load(stage_a(s) + q * (kStageA / 2), base + (row + kAGroups * TI) * kOzGroupBytes, kStageA / 2,
                         &bars.full[s]);
           tc::bulk_load(stage_b(s) + q * (kStageB / 2), base + (row + kBGroups * TJ) * kOzGroupBytes, kStageB / 2,
@@ -142,7 +144,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_oz_kernel(const OzGramJob* _
   } else if (warp == 1) {
     // ------------------------------------------------------------ UMMA issuer
     if (lane == 0) {
-      constexpr uint32_t idesc = tc::idesc_bf16_f32_major(128, 64, 0, 0);
+      constexpr uint32_t idesc = tc::idesc_f16_f32_major(128, 64, 0, 0);
       for (int k = 0; k < nst; ++k) {
         const int s = k % kStages;
         const int pos = k % kBlockStages;
@@ -159,7 +161,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_oz_kernel(const OzGramJob* _
           for (int t = t_lo; t <= t_hi; ++t) {
             const int u = lv - t;
             // A: LBO = row-group stride (K), SBO = column-group stride (M); same for B
-            tc::umma_bf16(tbase + (uint32_t)(lv - 2) * kLevelCols,
+            tc::umma_f16(tbase + (uint32_t)(lv - 2) * kLevelCols,
                           tc::ns_desc(a0 + (uint32_t)(t - 1) * 128u, kStageA / 2, kOzGroupBytes),
                           tc::ns_desc(b0 + (uint32_t)(u - 1) * 128u, kStageB / 2, kOzGroupBytes), idesc,
                           (pos == 0 && t == t_lo) ? 0u : 1u);
@@ -205,22 +207,22 @@ __global__ void __launch_bounds__(kThreads, 1) gram_oz_kernel(const OzGramJob* _
       if (lane == 0) tc::mbar_arrive(&bars.acc_empty);
     }
     if (__all_sync(0xffffffffu, ok && !abort_flag)) {
-      const int mp = J.CGp * 8;
+      const int mp = J.mp;
       const int i = 128 * TI + 32 * q + lane;
       const int Ei = i < J.m ? J.exps[i] : 0;
       double* out = J.partial + (size_t)sp * mp * mp;
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
         const int j = 64 * TJ + 16 * cw + c;
-        double v = 0.0;
-        if (i < J.m && j < J.m) {
+        if (i < J.m && j < J.m) {  // rows / columns past m come from slack digits
           const int Ej = J.exps[j];
+          double v;
           if (Ei == kOzNonFinite || Ej == kOzNonFinite)
             v = __longlong_as_double(0x7FF8000000000000ll);
           else
             v = oz_combine(hi[c], lo[c], Ei + Ej - 62);
+          out[(size_t)j * mp + i] = v;
         }
-        out[(size_t)j * mp + i] = v;
       }
     }
   }
@@ -259,10 +261,10 @@ dim3 grid_for(int64_t blocks) {
 
 }  // namespace
 
-int oz_gram_tiles(int32_t m, int32_t CGp) {
+int oz_gram_tiles(int32_t m) {
   const int jmax = (m + 63) / 64;
   int n = 0;
-  for (int i = 0; i < CGp / 16; ++i) n += jmax - 2 * i > 0 ? jmax - 2 * i : 0;
+  for (int i = 0; 2 * i < jmax; ++i) n += jmax - 2 * i;
   return n;
 }
 

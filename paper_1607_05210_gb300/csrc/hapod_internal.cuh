@@ -82,7 +82,7 @@ bool encode_colmajor_f32(CUtensorMap* out, const void* base, int64_t rows, int64
 // ---------------------------------------------------------------- Gram, digit-slice FP64 form
 // X (FP64) is represented exactly up to 2^-55 of each column's power-of-two bound
 // 2^E_j by 7 balanced base-256 digits per value (Ozaki et al. 2012 error-free
-// splitting); digit products are exact in bf16 x bf16 -> FP32 tensor-core arithmetic
+// splitting); digit products are exact in fp16 x fp16 -> FP32 tensor-core arithmetic
 // and their level sums (t + u = s <= 8) stay exact integers over kOzKBlock rows.
 constexpr int kOzDigits = 7;
 constexpr int kOzLevels = 7;                   // s = 2..8
@@ -103,8 +103,9 @@ struct OzColJob {
 cudaError_t launch_oz_colmax(const OzColJob* jobs_dev, int njobs, int64_t total_cols, cudaStream_t s);
 
 // Digit planes of rows [r0, r0 + rows) of X into `digits`, layout
-// [row group of 8][column group of 8 (CGp)][digit][column % 8][row % 8] (bf16),
-// RG = 2 ceil(rows / 16) row groups; rows >= `rows` and columns >= m are zero.
+// [row group of 8][column group of 8 (CGs)][digit][column % 8][row % 8] (fp16),
+// RG = 2 ceil(rows / 16) row groups, CGs = ceil(m / 8) column groups; rows >= `rows`
+// and columns >= m are zero.
 struct OzSplitJob {
   const double* X;
   int64_t ldx;
@@ -112,30 +113,37 @@ struct OzSplitJob {
   int64_t rows;
   const int32_t* exps;
   uint16_t* digits;
-  int64_t thread_base;  // first thread of this job (RG * CGp * 8 threads per job)
+  int64_t thread_base;  // first thread of this job (RG * CGs * 8 threads per job)
   int32_t m;
-  int32_t CGp;          // column groups, a multiple of 16
+  int32_t CGs;
 };
 cudaError_t launch_oz_split(const OzSplitJob* jobs_dev, int njobs, int64_t total_threads, cudaStream_t s);
 __host__ __device__ inline int64_t oz_row_groups(int64_t rows) { return 2 * ((rows + 15) / 16); }
 __host__ __device__ inline int32_t oz_col_groups(int64_t m) { return (int32_t)(16 * ((m + 127) / 128)); }
+__host__ __device__ inline int32_t oz_stored_groups(int64_t m) { return (int32_t)((m + 7) / 8); }
+// A Gram tile reads up to 15 column groups past the stored ones (rows of the tile that
+// are never written back): every digit buffer carries this much readable slack.
+constexpr size_t kOzDigitSlack = 16 * kOzGroupBytes;
 
 // Gram of one digit block: items (split, tile) in split-major order; tile (I, J) =
 // columns [128 I, 128 I + 128) x [64 J, 64 J + 64), J >= 2 I, 64 J < m.  The item
-// writes its FP64 128 x 64 block into partial slot `split` (mp x mp, ld mp, mp = 8 CGp).
+// writes the entries i, j < m of its FP64 128 x 64 block into partial slot `split`
+// (mp x mp, ld mp).
 struct OzGramJob {
   const uint16_t* digits;
   const int32_t* exps;
   double* partial;
   int64_t item_base;
   int32_t RG;
-  int32_t CGp;
+  int32_t CGs;
   int32_t m;
+  int32_t mp;
   int32_t splits;
   int32_t stages_per_split;  // 16-row stages per split, a multiple of kOzKBlock / 16
   int32_t tiles;
+  int32_t pad;
 };
-int oz_gram_tiles(int32_t m, int32_t CGp);
+int oz_gram_tiles(int32_t m);
 cudaError_t launch_gram_oz(const OzGramJob* jobs_dev, int njobs, int64_t total_items, int* err_flag, cudaStream_t s);
 // G (m x m, ld m) = sum of `slots` partials (upper triangle, mirrored).
 struct OzReduceJob {

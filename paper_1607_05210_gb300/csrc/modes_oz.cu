@@ -1,6 +1,6 @@
 // K4, digit-slice FP64 form: Y = X V_k diag(scale) (Sec. 2, Remark
 // def:method_of_snapshots: sigma_k phi_k = X psi_k, or phi_k with scale = 1/sigma)
-// from exact digits on the tensor cores (tcgen05 kind::f16, bf16 x bf16 -> FP32).
+// from exact digits on the tensor cores (tcgen05 kind::f16, fp16 x fp16 -> FP32).
 //
 // X is split per column as for the Gram, x_rj = 2^E_j xt_rj (oz_common.cuh).
 // Moving the column scale into V, Y_rc = sum_j xt_rj (2^E_j V_jc) = 2^F_c sum_j
@@ -18,8 +18,9 @@
 // (M = rows; row groups padded by 16 bytes so the digit stores are conflict-free).
 // Warps:
 //   warp 0       loader (TMA X tiles, bulk copies of V digits)
-//   warp 1       TMEM owner and single-thread UMMA issuer: 28 MMAs 128 x 32 x 16
-//                per stage into 7 level accumulators; two accumulator sets, so a
+//   warp 1       TMEM owner and single-thread UMMA issuer: per stage 10 MMAs
+//                128 x (32..128) x 16 (one X digit against up to 4 V digits) into
+//                7 level accumulators; two accumulator sets, so a
 //                tile's output overlaps the next tile's products
 //   warps 2..9   converters (FP64 -> digits)
 //   warps 10..17 output (16 modes x 32 rows each)
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int q = 0; q < 2; ++q)
             tc::bulk_load(stage_b(s) + q * (kStageB / 2),
-                          vd + ((int64_t)(2 * k + q) * J.NG + nt * (NT / 8)) * kOzGroupBytes, kStageB / 2,
+                          vd + ((int64_t)(2 * k + q) * J.n_tiles + nt) * (kStageB / 2), kStageB / 2,
                           &bars.vfull[s]);
           ++gv;
         }
@@ -167,7 +168,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     // ------------------------------------------------------------ UMMA issuer
     if (lane == 0) {
-      constexpr uint32_t idesc = tc::idesc_bf16_f32_major(128, NT, 1, 0);
       int64_t gk = 0;
       int uses[2] = {0, 0};  // K-blocks accumulated per accumulator set
       int tile = 0;
@@ -192,19 +192,20 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc::tc_fence_after();
           const uint32_t a0 = tc::smem_u32(stage_a(s)), b0 = tc::smem_u32(stage_b(s));
+          // digit t of X against digits u0 .. u0 + len - 1 of V in one MMA: the B planes
+          // are consecutive (N = 32 len) and so are the level accumulators t + u.
+          // A (MN-major): LBO = column-group stride (K), SBO = padded row-group stride (M);
+          // B (K-major): LBO = column-group stride (K), SBO = 128 (mode groups, then planes)
 #pragma unroll
-          for (int lv = 2; lv <= kLevels + 1; ++lv) {
-            const int t_lo = 1;
-            const int t_hi = lv - 1;
+          for (int t = 1; t <= kOzDigits; ++t) {
 #pragma unroll
-            for (int t = t_lo; t <= t_hi; ++t) {
-              const int u = lv - t;
-              // A (MN-major): LBO = column-group stride (K), SBO = padded row-group stride (M);
-              // B (K-major): LBO = column-group stride (K), SBO = mode-group stride (N)
-              tc::umma_bf16(acc + (uint32_t)((lv - 2) * NT),
+            for (int u0 = 1; u0 <= kLevels + 1 - t; u0 += 4) {
+              const int len = min(4, kLevels + 2 - t - u0);
+              const uint32_t idesc = tc::idesc_f16_f32_major(128, NT * len, 1, 0);
+              tc::umma_f16(acc + (uint32_t)((t + u0 - 2) * NT),
                             tc::ns_desc(a0 + (uint32_t)(t - 1) * 128u, kOzGroupBytes, kRowGroupBytes),
-                            tc::ns_desc(b0 + (uint32_t)(u - 1) * 128u, kStageB / 2, kOzGroupBytes), idesc,
-                            (pos == 0 && t == t_lo) ? 0u : 1u);
+                            tc::ns_desc(b0 + (uint32_t)(u0 - 1) * (NT / 8) * 128u, kStageB / 2, 128u), idesc,
+                            (pos == 0 && t == 1) ? 0u : 1u);
             }
           }
           tc::umma_commit(&bars.empty[s]);
@@ -253,7 +254,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&bars.xempty[x]);
-        // digits of 4 consecutive rows, packed two bf16 per word
+        // digits of 4 consecutive rows, packed two fp16 per word
         uint32_t w[2][2][kOzDigits];
 #pragma unroll
         for (int jj = 0; jj < 2; ++jj) {
@@ -356,8 +357,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // One block per mode column c (of kpad = 8 NG): F_c = max_j (E_j + e(V_jc)) with
 // |V_jc| < 2^e(V_jc), then the digits of V_jc against 2^(F_c - E_j) into
-// [column group j/8][mode group c/8][digit][c % 8][j % 8].  Columns c >= k and rows
-// j >= m are zero.  A non-finite X column (E_j marker) or V entry marks F_c.
+// [column group j/8][32-mode tile c/32][digit][mode group (c%32)/8][c % 8][j % 8], so
+// that consecutive digit planes of one tile form one K-major operand of up to 128
+// modes.  Columns c >= k and rows j >= m are zero.  A non-finite X column (E_j
+// marker) or V entry marks F_c.
 __global__ void __launch_bounds__(256) oz_vsplit_kernel(const OzVSplitJob* __restrict__ jobs, int njobs) {
   const int64_t b = blockIdx.x;
   int lo = 0, hi = njobs - 1;
@@ -411,9 +414,11 @@ __global__ void __launch_bounds__(256) oz_vsplit_kernel(const OzVSplitJob* __res
         for (int q = 0; q < kOzDigits; ++q) w[q][r >> 1] |= d[q] << (16 * (r & 1));
       }
     }
-    uint4* out = reinterpret_cast<uint4*>(J.vdig) + (((size_t)g * J.NG + (c >> 3)) * kOzDigits) * 8 + (c & 7);
+    const int tiles = J.NG / (NT / 8);
+    uint4* out = reinterpret_cast<uint4*>(J.vdig) + (((size_t)g * tiles + (c / NT)) * kOzDigits) * (NT / 8) * 8 +
+                 ((c % NT) >> 3) * 8 + (c & 7);
 #pragma unroll
-    for (int q = 0; q < kOzDigits; ++q) out[q * 8] = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+    for (int q = 0; q < kOzDigits; ++q) out[q * (NT / 8) * 8] = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
   }
 }
 

@@ -4,7 +4,7 @@
 //   d_1 in [0, 128], d_2..d_7 in [-128, 127],
 // so x = sign(x) 2^(E+1) sum_{t=1..7} d_t 2^(-8t) up to the truncated tail (< 2^(E-55)):
 // the error-free splitting of Ozaki, Ogita, Oishi and Rump (2012) in fixed-point form.
-// Every digit is an integer of magnitude <= 128, exact in bf16, and every product of
+// Every digit is an integer of magnitude <= 128, exact in fp16, and every product of
 // two digits is at most 2^14 in magnitude.
 #pragma once
 
@@ -43,41 +43,45 @@ __device__ __forceinline__ void oz_fixed(double x, int E, uint32_t& ahi, uint32_
   ahi = hi + kOzBalanceHi + (alo < lo ? 1u : 0u);
 }
 
-// Float bit patterns of the 7 digits of x (bf16 pattern = upper half), sign applied
-// by the caller.  The float built from a digit code c by the 2^23 exponent trick,
-// minus the bias, is exact.
-__device__ __forceinline__ void oz_digit_floats(uint32_t ahi, uint32_t alo, uint32_t (&f)[kOzDigits]) {
-  f[0] = __float_as_uint(__uint_as_float(0x4B000000u | (ahi >> 16)) - 8388608.f);
-  f[1] = __float_as_uint(__uint_as_float(__byte_perm(ahi, 0x4B000000u, 0x7441)) - 8388736.f);  // 2^23 + 128
-  f[2] = __float_as_uint(__uint_as_float(__byte_perm(ahi, 0x4B000000u, 0x7440)) - 8388736.f);
-  f[3] = __float_as_uint(__uint_as_float(__byte_perm(alo, 0x4B000000u, 0x7443)) - 8388736.f);
-  f[4] = __float_as_uint(__uint_as_float(__byte_perm(alo, 0x4B000000u, 0x7442)) - 8388736.f);
-  f[5] = __float_as_uint(__uint_as_float(__byte_perm(alo, 0x4B000000u, 0x7441)) - 8388736.f);
-  f[6] = __float_as_uint(__uint_as_float(__byte_perm(alo, 0x4B000000u, 0x7440)) - 8388736.f);
+// Digit codes (bytes of A + balance): code t of plane t sits in byte kOzByte[t] of
+// (t == 0 ? ahi : t < 3 ? ahi : alo); the value is code - 128 (code for the top digit).
+// fp16 patterns of two digits of one plane, two elements at once: the bytes are placed
+// under the exponent pattern 0x64 (1024 + code, exact in fp16) and one signed fused
+// multiply-add gives sign * (code - bias), exact.
+__device__ __forceinline__ uint32_t oz_pair(uint32_t a, uint32_t b, uint32_t sel, uint32_t sgn2, uint32_t nb2) {
+  const uint32_t t = (__byte_perm(a, b, sel) & 0x00FF00FFu) | 0x64006400u;
+  uint32_t r;
+  asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(r) : "r"(t), "r"(sgn2), "r"(nb2));
+  return r;
 }
 
-// The 7 digits of x as bf16 bit patterns in the low halves.
-__device__ __forceinline__ void oz_digits(double x, int E, uint32_t (&d)[kOzDigits]) {
-  uint32_t ahi, alo, f[kOzDigits];
-  oz_fixed(x, E, ahi, alo);
-  oz_digit_floats(ahi, alo, f);
-  const uint32_t sign = (uint32_t)((uint64_t)__double_as_longlong(x) >> 63) << 15;
-#pragma unroll
-  for (int t = 0; t < kOzDigits; ++t) d[t] = (f[t] >> 16) ^ sign;
-}
-
-// The 7 digits of two values of one column (same E), packed bf16x2 per digit plane:
+// The 7 digit planes of two values of one column (same E), packed f16x2 per plane:
 // x0 in the low half, x1 in the high half.
 __device__ __forceinline__ void oz_digits2(double x0, double x1, int E, uint32_t (&w)[kOzDigits]) {
-  uint32_t h0, l0, h1, l1, f0[kOzDigits], f1[kOzDigits];
+  uint32_t h0, l0, h1, l1;
   oz_fixed(x0, E, h0, l0);
   oz_fixed(x1, E, h1, l1);
-  oz_digit_floats(h0, l0, f0);
-  oz_digit_floats(h1, l1, f1);
-  const uint32_t smask = (((uint32_t)((uint64_t)__double_as_longlong(x0) >> 63)) << 15) |
-                         (((uint32_t)((uint64_t)__double_as_longlong(x1) >> 63)) << 31);
+  // +-1 per half, and -bias * sign for the top digit (1024) and the others (1152)
+  const uint32_t sgn2 = 0x3C003C00u | ((uint32_t)((uint64_t)__double_as_longlong(x0) >> 63) << 15) |
+                        ((uint32_t)((uint64_t)__double_as_longlong(x1) >> 63) << 31);
+  uint32_t nb_top, nb_low;
+  asm("mul.rn.f16x2 %0, %1, %2;" : "=r"(nb_top) : "r"(sgn2), "r"(0xE400E400u));  // -1024
+  asm("mul.rn.f16x2 %0, %1, %2;" : "=r"(nb_low) : "r"(sgn2), "r"(0xE480E480u));  // -1152
+  w[0] = oz_pair(h0, h1, 0x6622u, sgn2, nb_top);
+  w[1] = oz_pair(h0, h1, 0x5511u, sgn2, nb_low);
+  w[2] = oz_pair(h0, h1, 0x4400u, sgn2, nb_low);
+  w[3] = oz_pair(l0, l1, 0x7733u, sgn2, nb_low);
+  w[4] = oz_pair(l0, l1, 0x6622u, sgn2, nb_low);
+  w[5] = oz_pair(l0, l1, 0x5511u, sgn2, nb_low);
+  w[6] = oz_pair(l0, l1, 0x4400u, sgn2, nb_low);
+}
+
+// The 7 digits of x as fp16 bit patterns in the low halves.
+__device__ __forceinline__ void oz_digits(double x, int E, uint32_t (&d)[kOzDigits]) {
+  uint32_t w[kOzDigits];
+  oz_digits2(x, 0.0, E, w);
 #pragma unroll
-  for (int t = 0; t < kOzDigits; ++t) w[t] = __byte_perm(f0[t], f1[t], 0x7632) ^ smask;
+  for (int t = 0; t < kOzDigits; ++t) d[t] = w[t] & 0xFFFFu;
 }
 
 // Exact level sums of one flush, combined into the two int64 fixed-point sums
@@ -87,9 +91,34 @@ __device__ __forceinline__ long long oz_level_weight(int lv) {
   return lv < 3 ? (1ll << (8 * (2 - lv))) : (1ll << (8 * (6 - lv)));
 }
 
-// value = 2^(shift) (hi 2^32 + lo), rounded once to FP64
+// value = 2^(shift) (hi 2^32 + lo), rounded once to FP64 (to nearest, ties to even),
+// with integer arithmetic: the FP64 pipe of this part is a small fraction of its
+// integer rate.  Results outside the normal range take the FP64 route.
 __device__ __forceinline__ double oz_combine(long long hi, long long lo, int shift) {
-  return scalbn((double)hi * 4294967296.0 + (double)lo, shift);
+  // T = hi 2^32 + lo as a signed 128-bit integer
+  const __int128 T = ((__int128)hi << 32) + (__int128)lo;
+  if (T == 0) return 0.0;
+  const bool neg = T < 0;
+  const unsigned __int128 M = neg ? (unsigned __int128)(-T) : (unsigned __int128)T;
+  const uint64_t mh = (uint64_t)(M >> 64), ml = (uint64_t)M;
+  const int z = mh ? __clzll((long long)mh) : 64 + __clzll((long long)ml);  // leading zeros of M
+  const unsigned __int128 N = M << z;                                       // top bit at 127
+  const uint64_t w = (uint64_t)(N >> 64), rest = (uint64_t)N;
+  uint64_t mant = w >> 11;  // 53 bits, leading one at bit 52
+  const uint64_t half = (w >> 10) & 1u;
+  const bool sticky = (w & 0x3FFu) != 0 || rest != 0;
+  int be = (127 - z) + shift + 1023;  // biased exponent of the leading bit
+  mant += half & ((sticky ? 1u : 0u) | (mant & 1u));
+  if (mant >> 53) {
+    mant >>= 1;
+    ++be;
+  }
+  if (be < 1 || be > 2046) {
+    const double v = (double)hi * 4294967296.0 + (double)lo;
+    return scalbn(v, shift);
+  }
+  const uint64_t bits = ((uint64_t)neg << 63) | ((uint64_t)be << 52) | (mant & 0x000FFFFFFFFFFFFFull);
+  return __longlong_as_double((long long)bits);
 }
 
 }  // namespace hapod

@@ -10,7 +10,7 @@
 // so x = sign(x) 2^(E_j+1) sum_t d_t 2^(-8 t) up to the dropped tail (< 2^(E_j - 55)).
 //
 // Layout of a digit block (rows [r0, r0 + rows) of one node):
-//   [row group r/8][column group j/8][digit t][j % 8][r % 8]   (bf16)
+//   [row group r/8][column group j/8][digit t][j % 8][r % 8]   (fp16)
 // i.e. 8 x 8 core matrices of 16-byte rows, all 7 digits of one 8 x 8 block
 // together (896 bytes).  Read as columns-by-rows it is the K-major no-swizzle UMMA
 // layout of the Gram (K = rows).
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(kThreads) oz_split_kernel(const OzSplitJob* __
   }
   const OzSplitJob J = jobs[lo];
   const int64_t local = t - J.thread_base;
-  const int64_t cols = (int64_t)J.CGp * 8;
+  const int64_t cols = (int64_t)J.CGs * 8;
   const int64_t rg = local / cols;
   if (rg >= oz_row_groups(J.rows)) return;
   const int j = (int)(local - rg * cols);
@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(kThreads) oz_split_kernel(const OzSplitJob* __
       for (int q = 0; q < kOzDigits; ++q) w[q][r >> 1] |= d[q] << (16 * (r & 1));
     }
   }
-  uint4* out = reinterpret_cast<uint4*>(J.digits) + ((rg * J.CGp + (j >> 3)) * kOzDigits) * 8 + (j & 7);
+  uint4* out = reinterpret_cast<uint4*>(J.digits) + ((rg * J.CGs + (j >> 3)) * kOzDigits) * 8 + (j & 7);
 #pragma unroll
   for (int q = 0; q < kOzDigits; ++q) out[q * 8] = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
 }

@@ -105,6 +105,11 @@ __device__ __forceinline__ uint64_t ns_desc(uint32_t saddr, uint32_t lbo, uint32
   d |= (uint64_t)1 << 46;  // descriptor version; layout type 0 = no swizzle
   return d;
 }
+// Instruction descriptor: fp16 x fp16 -> FP32 (kind::f16) with the A / B major-ness
+// given (0 = K-major, 1 = MN-major), M x N.
+__host__ __device__ constexpr uint32_t idesc_f16_f32_major(uint32_t M, uint32_t N, uint32_t a_mn, uint32_t b_mn) {
+  return (1u << 4) | (a_mn << 15) | (b_mn << 16) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
 // Instruction descriptor: bf16 x bf16 -> FP32 with the A / B major-ness given
 // (0 = K-major, 1 = MN-major), M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32_major(uint32_t M, uint32_t N, uint32_t a_mn, uint32_t b_mn) {
@@ -139,7 +144,8 @@ __device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t a_desc, uint
       : "memory");
 }
 
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+// D (+)= A B^T, kind::f16: fp16 or bf16 operands (both the same) per the instruction descriptor
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
                                           uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
