@@ -292,7 +292,7 @@ void oz_plan(const std::vector<Work*>& ws, std::vector<OzChunk>& chunks, std::ve
   }
 }
 
-OzSplitJob oz_split_job(const Work* w, const OzChunk& C, uint16_t* dblk, int64_t thread_base) {
+OzSplitJob oz_split_job(const Work* w, const OzChunk& C, uint16_t* dblk, int64_t block_base) {
   OzSplitJob S;
   memset(&S, 0, sizeof(S));
   S.X = static_cast<const double*>(w->X);
@@ -301,7 +301,7 @@ OzSplitJob oz_split_job(const Work* w, const OzChunk& C, uint16_t* dblk, int64_t
   S.rows = C.rows;
   S.exps = w->exps;
   S.digits = dblk;
-  S.thread_base = thread_base;
+  S.block_base = block_base;
   S.m = (int32_t)w->m;
   S.CGs = C.CGs;
   return S;
@@ -384,14 +384,14 @@ bool step_gram_oz(Env& env, std::vector<Work*>& ws) {
     std::vector<OzSplitJob> sj;
     std::vector<OzGramJob> gj;
     size_t off = 0;
-    int64_t threads = 0, items = 0;
+    int64_t blocks = 0, items = 0;
     for (size_t c = rounds[r].first; c < rounds[r].second; ++c) {
       const OzChunk& C = chunks[c];
       Work* w = ws[C.node];
       uint16_t* dblk = reinterpret_cast<uint16_t*>(reinterpret_cast<uint8_t*>(digits) + off);
       off += C.bytes;
-      sj.push_back(oz_split_job(w, C, dblk, threads));
-      threads += (int64_t)C.RG * C.CGs * 8;
+      sj.push_back(oz_split_job(w, C, dblk, blocks));
+      blocks += oz_split_blocks(C.rows, C.CGs);
       OzGramJob G;
       memset(&G, 0, sizeof(G));
       const int64_t mp = w->m;
@@ -413,7 +413,7 @@ bool step_gram_oz(Env& env, std::vector<Work*>& ws) {
     OzGramJob* gj_d = env.upload(gj, "upload gram jobs");
     job_bufs.push_back(sj_d);
     job_bufs.push_back(gj_d);
-    ok = sj_d && gj_d && env.cuda(launch_oz_split(sj_d, (int)sj.size(), threads, env.s), "digit split launch") &&
+    ok = sj_d && gj_d && env.cuda(launch_oz_split(sj_d, (int)sj.size(), blocks, env.s), "digit split launch") &&
          env.cuda(launch_gram_oz(gj_d, (int)gj.size(), items, env.err_dev, env.s), "gram launch");
     launches += 2;
   }

@@ -113,11 +113,12 @@ struct OzSplitJob {
   int64_t rows;
   const int32_t* exps;
   uint16_t* digits;
-  int64_t thread_base;  // first thread of this job (RG * CGs * 8 threads per job)
+  int64_t block_base;   // first block of this job (oz_split_blocks(rows, CGs) blocks)
   int32_t m;
   int32_t CGs;
 };
-cudaError_t launch_oz_split(const OzSplitJob* jobs_dev, int njobs, int64_t total_threads, cudaStream_t s);
+int64_t oz_split_blocks(int64_t rows, int32_t CGs);
+cudaError_t launch_oz_split(const OzSplitJob* jobs_dev, int njobs, int64_t total_blocks, cudaStream_t s);
 __host__ __device__ inline int64_t oz_row_groups(int64_t rows) { return 2 * ((rows + 15) / 16); }
 __host__ __device__ inline int32_t oz_col_groups(int64_t m) { return (int32_t)(16 * ((m + 127) / 128)); }
 __host__ __device__ inline int32_t oz_stored_groups(int64_t m) { return (int32_t)((m + 7) / 8); }

@@ -67,36 +67,56 @@ __global__ void __launch_bounds__(kThreads) oz_colmax_kernel(const OzColJob* __r
   }
 }
 
-// Thread = (row group, column): 8 consecutive rows of one column -> one 16-byte
-// core-matrix row per digit.  Lanes 0..7 of a warp are the 8 columns of one column
-// group, so each digit's stores of those lanes form one 128-byte segment.
+// Block = 64 rows x 32 columns (8 row groups x 4 column groups) of one digit block.
+// The FP64 tile is read column by column (each warp 256-byte runs of one column)
+// into shared memory, then thread (row group, column) converts 8 consecutive rows
+// of one column into one 16-byte core-matrix row per digit; the 8 lanes of one
+// column group write one 128-byte segment per digit.
+constexpr int kTileRows = 64, kTileCols = 32;
+
 __global__ void __launch_bounds__(kThreads) oz_split_kernel(const OzSplitJob* __restrict__ jobs, int njobs) {
-  const int64_t t = (blockIdx.x + (int64_t)blockIdx.y * gridDim.x) * kThreads + threadIdx.x;
+  __shared__ double tile[kTileCols][kTileRows + 1];
+  const int64_t b = blockIdx.x + (int64_t)blockIdx.y * gridDim.x;
   int lo = 0, hi = njobs - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (jobs[mid].thread_base <= t) lo = mid; else hi = mid - 1;
+    if (jobs[mid].block_base <= b) lo = mid; else hi = mid - 1;
   }
   const OzSplitJob J = jobs[lo];
-  const int64_t local = t - J.thread_base;
-  const int64_t cols = (int64_t)J.CGs * 8;
-  const int64_t rg = local / cols;
-  if (rg >= oz_row_groups(J.rows)) return;
-  const int j = (int)(local - rg * cols);
+  const int64_t local = b - J.block_base;
+  const int ct = (J.CGs + 3) / 4;  // column tiles
+  const int64_t rt = local / ct;
+  if (rt >= (oz_row_groups(J.rows) + 7) / 8) return;
+  const int c0 = (int)(local - rt * ct) * kTileCols;
+  const int64_t r0 = rt * kTileRows;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int cc = warp; cc < kTileCols; cc += kThreads / 32) {
+    const int j = c0 + cc;
+    const bool col = j < J.m && J.exps[j] != kOzNonFinite;
+    const double* src = J.X + (int64_t)j * J.ldx + J.r0;
+#pragma unroll
+    for (int h = 0; h < kTileRows / 32; ++h) {
+      const int64_t r = r0 + lane + 32 * h;
+      tile[cc][lane + 32 * h] = (col && r < J.rows) ? src[r] : 0.0;
+    }
+  }
+  __syncthreads();
+  const int cc = threadIdx.x & 31;   // column in the tile
+  const int rgl = threadIdx.x >> 5;  // row group in the tile
+  const int j = c0 + cc;
+  const int64_t rg = rt * 8 + rgl;
+  if (rg >= oz_row_groups(J.rows) || (j >> 3) >= J.CGs) return;
+  const int E = j < J.m ? J.exps[j] : kOzNonFinite;
   uint32_t w[kOzDigits][4];
 #pragma unroll
   for (int q = 0; q < kOzDigits; ++q) w[q][0] = w[q][1] = w[q][2] = w[q][3] = 0u;
-  const int E = j < J.m ? J.exps[j] : kOzNonFinite;
   if (E != kOzNonFinite) {
-    const int64_t row0 = rg * 8;
-    const double* col = J.X + (int64_t)j * J.ldx + J.r0 + row0;
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const double x = row0 + r < J.rows ? col[r] : 0.0;
+    for (int p = 0; p < 4; ++p) {
       uint32_t d[kOzDigits];
-      oz_digits(x, E, d);
+      oz_digits2(tile[cc][rgl * 8 + 2 * p], tile[cc][rgl * 8 + 2 * p + 1], E, d);
 #pragma unroll
-      for (int q = 0; q < kOzDigits; ++q) w[q][r >> 1] |= d[q] << (16 * (r & 1));
+      for (int q = 0; q < kOzDigits; ++q) w[q][p] = d[q];
     }
   }
   uint4* out = reinterpret_cast<uint4*>(J.digits) + ((rg * J.CGs + (j >> 3)) * kOzDigits) * 8 + (j & 7);
@@ -117,9 +137,13 @@ cudaError_t launch_oz_colmax(const OzColJob* jobs_dev, int njobs, int64_t total_
   return cudaGetLastError();
 }
 
-cudaError_t launch_oz_split(const OzSplitJob* jobs_dev, int njobs, int64_t total_threads, cudaStream_t s) {
-  if (njobs <= 0 || total_threads <= 0) return cudaSuccess;
-  oz_split_kernel<<<grid_for((total_threads + kThreads - 1) / kThreads), kThreads, 0, s>>>(jobs_dev, njobs);
+int64_t oz_split_blocks(int64_t rows, int32_t CGs) {
+  return (oz_row_groups(rows) + 7) / 8 * ((CGs + 3) / 4);
+}
+
+cudaError_t launch_oz_split(const OzSplitJob* jobs_dev, int njobs, int64_t total_blocks, cudaStream_t s) {
+  if (njobs <= 0 || total_blocks <= 0) return cudaSuccess;
+  oz_split_kernel<<<grid_for(total_blocks), kThreads, 0, s>>>(jobs_dev, njobs);
   return cudaGetLastError();
 }
 
