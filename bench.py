@@ -10,11 +10,14 @@ generated on the device before timing and are larger than L2, so no flush is
 needed between steps.
 
 A step is one full HAPOD through the C ABI: create, push every leaf, result,
-destroy.  The headline is the FP64 form at the workload's tolerance eps = 1e-5
-rel.  The mixed form (FP32 snapshots, tensor-core split-bf16 Gram) resolves
+destroy.  The headline is the digit-slice FP64 form (FP64 data and results; Gram
+and X V from exact integer digit products on the tensor cores) at the workload's
+tolerance eps = 1e-5 rel; the FP64 ALU form runs at the same tolerance for
+comparison.  The mixed form (FP32 snapshots, TF32 tensor-core Gram) resolves
 singular values only down to its measured Gram error (noise eigenvalues summing
-to ~2.5e-6 of the trace), so it is run at eps = 1e-2 rel, and the FP64 form is run
-at that tolerance too for a same-accuracy comparison; both appear under "forms".
+to ~6e-8 of the trace), so it is run at eps = 1e-2 rel, and the FP64 ALU form is
+run at that tolerance too for a same-accuracy comparison; all appear under
+"forms".
 
 --impl reference times the CPU FP64 oracle on the host cores on a bounded sample
 of the same workload (there is no other reference implementation of the method).
@@ -245,8 +248,9 @@ def roofline(res, precision, H, hbm, bf16, dom=None):
         ach = 28.0 * d["flops"] / (d["ms"] / 1e3) / 1e12
         return dom, {"bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16,
                      "traffic": None,
-                     "kernel": "gram (digit split + tcgen05 bf16 digit-pair MMAs + reduce; 28 pair products "
-                               "per FP64 product; peak = measured sustained bf16)"}
+                     "kernel": "gram step (column maxima + digit split + tcgen05 fp16 digit-pair MMAs + "
+                               "reduce; 28 pair products per FP64 product; peak = measured sustained "
+                               "bf16, the fp16 dense rate is the same)"}
     if f64_alu(precision, H) and dom in ("gram", "modes"):
         ach = d["flops"] / (d["ms"] / 1e3) / 1e12
         return dom, {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
