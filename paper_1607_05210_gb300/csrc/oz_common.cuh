@@ -26,21 +26,14 @@ __device__ __forceinline__ void oz_fixed(double x, int E, uint32_t& ahi, uint32_
   const int eb = (int)((h >> 20) & 0x7FF);
   const uint32_t mh = (h & 0xFFFFFu) | (eb ? 0x100000u : 0u);  // mantissa = mh:l (53 bits)
   // |x| = mantissa 2^(max(eb,1) - 1075); A = mantissa >> sh (a left shift for sh < 0; sh >= -2)
+  // (branch-free: the elements of one warp take different shifts)
   const int sh = E + 1020 - (eb ? eb : 1);
-  uint32_t hi, lo;
-  if (sh < 0) {
-    hi = __funnelshift_l(l, mh, -sh);
-    lo = l << -sh;
-  } else if (sh < 32) {
-    lo = __funnelshift_r(l, mh, sh);
-    hi = mh >> sh;
-  } else {
-    lo = sh < 64 ? (mh >> (sh - 32)) : 0u;
-    hi = 0u;
-  }
-  // + balance (64-bit add)
-  alo = lo + kOzBalanceLo;
-  ahi = hi + kOzBalanceHi + (alo < lo ? 1u : 0u);
+  const uint64_t mant = ((uint64_t)mh << 32) | l;
+  const uint64_t left = mant << (sh < 0 ? -sh : 0);
+  const uint64_t A = sh < 0 ? left : (sh < 64 ? (mant >> (sh & 63)) : 0ull);
+  const uint64_t Ab = A + (((uint64_t)kOzBalanceHi << 32) | kOzBalanceLo);
+  ahi = (uint32_t)(Ab >> 32);
+  alo = (uint32_t)Ab;
 }
 
 // Digit codes (bytes of A + balance): code t of plane t sits in byte kOzByte[t] of
