@@ -8,7 +8,8 @@
 // into 7 base-256 digits the same way (oz_vsplit_kernel: the digits of V_jc against
 // the bound 2^(F_c - E_j), so nothing overflows).  The 28 digit pairs of level
 // t + u <= 8 are summed exactly over blocks of 128 columns, flushed exactly into
-// int64 sums, and Y_rc = 2^(F_c - 62) (hi 2^32 + lo) scale_c is rounded once to FP64.
+// int64 sums, rounded to FP64 per block (Y_rc = 2^(F_c - 62) (hi 2^32 + lo)) and
+// summed over the blocks in FP64 (one rounding for m <= 128), times scale_c.
 //
 // Persistent kernel, one CTA per SM, looping over items (node, 128-row tile,
 // 32-mode tile).  Per 16-column stage the loader brings the FP64 X tile (128 rows x
@@ -20,10 +21,11 @@
 //   warp 0       loader (TMA X tiles, bulk copies of V digits)
 //   warp 1       TMEM owner and single-thread UMMA issuer: per stage 10 MMAs
 //                128 x (32..128) x 16 (one X digit against up to 4 V digits) into
-//                7 level accumulators; two accumulator sets, so a
-//                tile's output overlaps the next tile's products
+//                7 level accumulators; two accumulator sets alternating per
+//                128-column block, so a block's output overlaps the next
+//                block's products
 //   warps 2..9   converters (FP64 -> digits)
-//   warps 10..17 output (16 modes x 32 rows each)
+//   warps 10..13 output (32 modes x 32 rows each; 14 warps leave 128 registers a thread)
 #include <climits>
 
 #include "hapod_internal.cuh"
@@ -47,7 +49,7 @@ constexpr int kLevels = kOzLevels;
 constexpr int kConvWarps = 8;
 constexpr int kFirstConvWarp = 2;
 constexpr int kFirstOutWarp = kFirstConvWarp + kConvWarps;
-constexpr int kOutWarps = 8;
+constexpr int kOutWarps = 4;
 constexpr int kThreads = (kFirstOutWarp + kOutWarps) * 32;
 constexpr uint32_t kAccCols = kLevels * NT;         // one accumulator set
 constexpr uint32_t kTmemCols = 512;
@@ -170,16 +172,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       int64_t gk = 0;
       int uses[2] = {0, 0};  // K-blocks accumulated per accumulator set
-      int tile = 0;
+      int kbg = 0;           // K-blocks so far: the sets alternate per 128-column block
       bool ok = true;
-      for (int64_t it = blockIdx.x; it < total_items && ok; it += gridDim.x, ++tile) {
+      for (int64_t it = blockIdx.x; it < total_items && ok; it += gridDim.x) {
         const OzModesJob& J = jobs[find_job(jobs, njobs, it)];
         const int nst = (J.m + 15) / 16;
-        const int b = tile & 1;
-        const uint32_t acc = tbase + (uint32_t)b * kAccCols;
+        int b = 0;
+        uint32_t acc = tbase;
         for (int k = 0; k < nst && ok; ++k, ++gk) {
           const int s = (int)(gk % kStages);
           const int pos = k % kKBlockStages;
+          if (pos == 0) {
+            b = kbg & 1;
+            acc = tbase + (uint32_t)b * kAccCols;
+          }
           if (pos == 0 && uses[b] > 0 &&
               !tc::mbar_wait(&bars.acc_empty[b], (uses[b] - 1) & 1, &abort_flag, err)) {
             ok = false;
@@ -212,6 +218,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (pos == kKBlockStages - 1 || k == nst - 1) {
             tc::umma_commit(&bars.acc_full[b]);
             ++uses[b];
+            ++kbg;
           }
         }
       }
@@ -223,28 +230,37 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp < kFirstOutWarp) {
     // ------------------------------------------------------------ converters
     // warp cw: columns 2 cw, 2 cw + 1 of each stage; lane: rows 4 lane .. 4 lane + 3
-    // (one 8-byte half of a 16-byte core-matrix row per digit plane and column).
+    // (one 8-byte half of a 16-byte core-matrix row per digit plane and column).  The
+    // job is copied to registers per item and the next stage's column exponents are
+    // loaded before the current stage's wait, off the conversion's critical path.
     const int cw = warp - kFirstConvWarp;
     int64_t gk = 0;
     for (int64_t it = blockIdx.x; it < total_items && !abort_flag; it += gridDim.x) {
-      const OzModesJob& J = jobs[find_job(jobs, njobs, it)];
+      const OzModesJob J = jobs[find_job(jobs, njobs, it)];
       const int nst = (J.m + 15) / 16;
+      auto exps_of = [&](int k, int jj) -> int {
+        const int j = 16 * k + 2 * cw + jj;
+        return j < J.m ? __ldg(J.exps + j) : kOzNonFinite;
+      };
+      int En[2] = {exps_of(0, 0), exps_of(0, 1)};
       bool ok = true;
       for (int k = 0; k < nst; ++k, ++gk) {
         const int x = (int)(gk % kXSlots);
         const int s = (int)(gk % kStages);
+        const int E[2] = {En[0], En[1]};
+        if (k + 1 < nst) {
+          En[0] = exps_of(k + 1, 0);
+          En[1] = exps_of(k + 1, 1);
+        }
         if (!tc::mbar_wait_warp(&bars.xfull[x], (gk / kXSlots) & 1, &abort_flag, err)) {
           ok = false;
           break;
         }
         const double* xsl = xs + (size_t)x * (kXSlotBytes / 8);
         double v[2][4];
-        int E[2];
 #pragma unroll
         for (int jj = 0; jj < 2; ++jj) {
           const int jl = 2 * cw + jj;
-          const int j = 16 * k + jl;
-          E[jj] = j < J.m ? J.exps[j] : kOzNonFinite;
           const double2* src = reinterpret_cast<const double2*>(xsl + jl * 128 + 4 * lane);
           const double2 a = src[0], b2 = src[1];
           v[jj][0] = a.x;
@@ -289,39 +305,61 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // ------------------------------------------------------------ output
+    // Per 128-column block: 8 modes at a time, the exact level sums -> FP64 (one
+    // rounding); blocks after the first are added to the partial result in Y.
     const int q = warp & 3;
-    const int cw = (warp - kFirstOutWarp) >> 2;  // 16-mode half of the 32-mode tile
     const uint32_t lanes = (uint32_t)(32 * q) << 16;
     int uses[2] = {0, 0};
-    int tile = 0;
-    for (int64_t it = blockIdx.x; it < total_items; it += gridDim.x, ++tile) {
+    int kbg = 0;
+    for (int64_t it = blockIdx.x; it < total_items; it += gridDim.x) {
       const OzModesJob& J = jobs[find_job(jobs, njobs, it)];
       const int64_t local = it - J.item_base;
       const int64_t rt = local % J.row_tiles;
       const int nt = (int)(local / J.row_tiles);
       const int nkb = ((J.m + 15) / 16 + kKBlockStages - 1) / kKBlockStages;
-      const int b = tile & 1;
-      const uint32_t acc = tbase + lanes + (uint32_t)b * kAccCols + (uint32_t)(16 * cw);
-      long long hi[16], lo[16];
-#pragma unroll
-      for (int c = 0; c < 16; ++c) hi[c] = lo[c] = 0;
+      const int64_t r = rt * 128 + 32 * q + lane;
       bool ok = true;
-      for (int kb = 0; kb < nkb; ++kb) {
+      for (int kb = 0; kb < nkb; ++kb, ++kbg) {
+        const int b = kbg & 1;
+        const uint32_t acc = tbase + lanes + (uint32_t)b * kAccCols;
         if (!tc::mbar_wait_warp(&bars.acc_full[b], uses[b] & 1, &abort_flag, err)) {
           ok = false;
           break;
         }
         tc::tc_fence_after();
+        const bool last = kb == nkb - 1;
+#pragma unroll 1
+        for (int c8 = 0; c8 < NT / 8; ++c8) {
+          long long hi[8], lo[8];
 #pragma unroll
-        for (int lv = 0; lv < kLevels; ++lv) {
-          float v[16];
-          tc::tmem_ld16(acc + (uint32_t)(lv * NT), v);
-          tc::tmem_wait_ld();
-          const long long w = oz_level_weight(lv);
+          for (int c = 0; c < 8; ++c) hi[c] = lo[c] = 0;
 #pragma unroll
-          for (int c = 0; c < 16; ++c) {
-            const long long xv = (long long)__float2int_rn(v[c]) * w;
-            if (lv < 3) hi[c] += xv; else lo[c] += xv;
+          for (int lv = 0; lv < kLevels; ++lv) {
+            float v[8];
+            tc::tmem_ld8(acc + (uint32_t)(lv * NT + 8 * c8), v);
+            tc::tmem_wait_ld();
+            const long long w = oz_level_weight(lv);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+              const long long xv = (long long)__float2int_rn(v[c]) * w;
+              if (lv < 3) hi[c] += xv; else lo[c] += xv;
+            }
+          }
+          if (r < J.n) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+              const int col = nt * NT + 8 * c8 + c;
+              if (col >= J.k) break;
+              const int F = J.fexp[col];
+              double* y = J.Y + (size_t)col * J.ldy + r;
+              double v = F == kOzNonFinite ? 0.0 : oz_combine(hi[c], lo[c], F - 62);
+              if (kb > 0) v += *y;
+              if (last) {
+                if (F == kOzNonFinite) v = __longlong_as_double(0x7FF8000000000000ll);
+                else if (J.scale) v *= J.scale[col];
+              }
+              *y = v;
+            }
           }
         }
         tc::tc_fence_before();
@@ -330,23 +368,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         ++uses[b];
       }
       if (!__all_sync(0xffffffffu, ok && !abort_flag)) break;
-      const int64_t r = rt * 128 + 32 * q + lane;
-      if (r < J.n) {
-#pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const int col = nt * NT + 16 * cw + c;
-          if (col >= J.k) break;
-          const int F = J.fexp[col];
-          double v;
-          if (F == kOzNonFinite) {
-            v = __longlong_as_double(0x7FF8000000000000ll);
-          } else {
-            v = oz_combine(hi[c], lo[c], F - 62);
-            if (J.scale) v *= J.scale[col];
-          }
-          J.Y[(size_t)col * J.ldy + r] = v;
-        }
-      }
     }
   }
   tc::tc_fence_before();
