@@ -197,20 +197,36 @@ def run_form(H, precision, bufs, fro2, steps, warmup, stream, dist_ctx, eps_rel=
             "leaf_k": max(st_["k"] for st_ in info["_nodes"] if st_["level"] == 1)}
 
 
+E2E_PENDING = 8  # leaves per processing batch in the end-to-end run (max_pending_leaves)
+
+
 def run_e2e(H, precision, host_bufs, dev_bufs, fro2, steps, stream):
     """Same HAPOD through the public API from pinned host buffers: H2D of every leaf and
-    D2H of the result (sigma, modes) inside the timed region."""
+    D2H of the result (sigma, modes) inside the timed region.  The leaf copies are
+    queued up front on a copy stream; each push waits for its leaf's copy, and the
+    context processes leaves in batches of E2E_PENDING (max_pending_leaves, Sec. 3.4)
+    so that the copies of later leaves overlap the processing of earlier ones."""
     import torch
 
     parent, leaves, cols = tree()
     eps = EPS_REL * math.sqrt(fro2)
     h2d = sum(b.numel() * b.element_size() for b in host_bufs)
     d2h = [0]
+    copy_stream = torch.cuda.Stream(dev_bufs[0].device)
 
     def step():
-        ctx = H.hapod_create(parent, cols, eps, OMEGA, N_ROWS, precision, stream=stream)
+        ctx = H.hapod_create(parent, cols, eps, OMEGA, N_ROWS, precision, stream=stream,
+                             max_pending_leaves=E2E_PENDING)
+        copy_stream.wait_stream(stream)
+        done = []
+        with torch.cuda.stream(copy_stream):
+            for i in range(len(leaves)):
+                dev_bufs[i].copy_(host_bufs[i], non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(copy_stream)
+                done.append(ev)
         for i, a in enumerate(leaves):
-            dev_bufs[i].copy_(host_bufs[i], non_blocking=True)
+            stream.wait_event(done[i])
             H.hapod_push(ctx, a, dev_bufs[i].t())
         s, U, st = H.hapod_result(ctx, device=dev_bufs[0].device)
         Uh = U.cpu()
@@ -232,6 +248,14 @@ def run_e2e(H, precision, host_bufs, dev_bufs, fro2, steps, stream):
             "ms_per_step": ms}
 
 
+# DRAM bytes (read + write) of one gram_oz_kernel launch on a 2^20 x 256 leaf, from
+# profiles/digit_slice_kernels_2p20x256.md (3.796 GB read + 0.016 GB written): the
+# digit planes once, the tile re-reads come from L2.  Per leaf launch, as the bench's
+# leaf-level launches; null once the kernel changes.
+OZ_GRAM_TRAFFIC = {"bytes_per_launch": 3.812e9, "launch": "one leaf, n = 2^20, m = 256",
+                   "algorithmic_digit_bytes": 3.758e9}
+
+
 def f64_alu(precision, H):
     """Steps that run on the FP64 FMA pipe: every FP64-ALU step, the X V of the digit-slice form."""
     return precision in (H.HAPOD_FP64, H.HAPOD_FP64_OZAKI)
@@ -243,14 +267,16 @@ def roofline(res, precision, H, hbm, bf16, dom=None):
         dom = max((k for k in steps if steps[k]["launches"] > 0), key=lambda k: steps[k]["ms"])
     d = steps[dom]
     if precision == H.HAPOD_FP64_OZAKI and dom == "gram":
-        # 28 bf16 digit-pair products per FP64 product of the n m (m + 1) / 2 unique Gram
-        # entries (the library reports 2 n m (m + 1) / 2 FP64 flops for the step)
+        # 28 fp16 digit-pair products per FP64 product of the n m (m + 1) / 2 unique Gram
+        # entries (the library reports 2 n m (m + 1) / 2 FP64 flops for the step); the
+        # step's time is the tensor-core Gram kernels and the split reduce (the digit
+        # conversion is the separate "digits" step)
         ach = 28.0 * d["flops"] / (d["ms"] / 1e3) / 1e12
         return dom, {"bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16,
-                     "traffic": None,
-                     "kernel": "gram step (column maxima + digit split + tcgen05 fp16 digit-pair MMAs + "
-                               "reduce; 28 pair products per FP64 product; peak = measured sustained "
-                               "bf16, the fp16 dense rate is the same)"}
+                     "traffic": OZ_GRAM_TRAFFIC,
+                     "kernel": "gram_oz_kernel + oz_reduce_kernel (tcgen05 fp16 digit-pair MMAs, 28 pair "
+                               "products per FP64 product; peak = measured sustained bf16, the fp16 dense "
+                               "rate is the same)"}
     if f64_alu(precision, H) and dom in ("gram", "modes"):
         ach = d["flops"] / (d["ms"] / 1e3) / 1e12
         return dom, {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -343,6 +369,9 @@ def main():
                     help="comma list of forms: 'oz' (digit-slice FP64, the headline when present), "
                          "'fp64' (FP64 ALU), 'mixed' (FP32 snapshots at eps = 1e-2)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-leaf", action="store_true",
+                    help="run two digit-slice Gram + X V calls on one 2^20 x 256 FP64 leaf (k = 19) and exit: "
+                         "the small case for ncu captures of oz_split / gram_oz / modes_oz")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
@@ -370,6 +399,18 @@ def main():
     torch.cuda.set_device(dist_ctx.local)
     device = torch.device("cuda", dist_ctx.local)
     from paper_1607_05210_gb300 import hapod as H
+
+    if args.profile_leaf:
+        torch.manual_seed(SEED)
+        X = torch.randn((COLS, N_ROWS), dtype=torch.float64, device=device).t()  # column-major n x m
+        V = torch.randn((19, COLS), dtype=torch.float64, device=device).t() / 16.0
+        for _ in range(2):
+            G = H.hapod_gram(X, H.HAPOD_FP64_OZAKI)
+            Y = H.hapod_modes(X, V, 19, None, H.HAPOD_FP64_OZAKI)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_leaf": True, "G00": float(G[0, 0]), "Y00": float(Y[0, 0])}))
+        dist_ctx.close()
+        return
 
     hbm, bf16, peak_src = _peaks()
     stream = torch.cuda.Stream(device)
@@ -430,6 +471,7 @@ def main():
                 h_.copy_(b)
             e2e = run_e2e(H, head_prec, host, bufs, fro2, 1, stream)
             e2e["form"] = head_key
+            e2e["max_pending_leaves"] = E2E_PENDING
             del host
         except (RuntimeError, MemoryError) as ex:
             e2e = {"value": None, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,

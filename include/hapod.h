@@ -161,16 +161,21 @@ hapod_status hapod_result(hapod_ctx* ctx, int64_t* k_out, double* sigma_host, vo
 
 /* Per-step accounting of a context created with HAPOD_FLAG_PROFILE.  Index:
  * 0 Gram, 1 eigensolve, 2 truncation, 3 eigenvector gather, 4 modes, 5 copies
- * (pass-through inputs and parked child outputs).  ms = summed device time
- * between CUDA events recorded on the context stream around the step's launches;
- * launches = kernel launches; bytes/flops = algorithmic volume of the step as
- * defined by the method (Gram: b n m bytes and n m (m + 1) flops per node; modes:
- * b n (m + k) bytes and 2 n m k flops; b = element size), zero where not defined. */
+ * (pass-through inputs and parked child outputs), 6 digit conversion of the
+ * digit-slice form (column exponents and digit planes of the Gram inputs; its Gram
+ * step 0 then counts the tensor-core Gram kernels and the split-sum reduce), 7
+ * unused.  ms = summed device time between CUDA events recorded on the context
+ * stream around the step's launches; launches = kernel launches; bytes/flops =
+ * algorithmic volume of the step as defined by the method (Gram: b n m bytes and
+ * n m (m + 1) flops per node; modes: b n (m + k) bytes and 2 n m k flops; b =
+ * element size; digit conversion: 22 n m bytes, the FP64 read and the 7 fp16
+ * digits written), zero where not defined. */
+#define HAPOD_PROFILE_STEPS 8
 typedef struct {
-  double ms[6];
-  int64_t launches[6];
-  double bytes[6];
-  double flops[6];
+  double ms[HAPOD_PROFILE_STEPS];
+  int64_t launches[HAPOD_PROFILE_STEPS];
+  double bytes[HAPOD_PROFILE_STEPS];
+  double flops[HAPOD_PROFILE_STEPS];
 } hapod_profile_info;
 
 /* Accumulated profile since hapod_create (zeros without HAPOD_FLAG_PROFILE).

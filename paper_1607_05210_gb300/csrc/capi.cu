@@ -335,16 +335,20 @@ bool oz_exponents(Env& env, std::vector<Work*>& ws) {
 
 // K1, digit-slice FP64 form: exponents, then per round the digit planes and the
 // tensor-core Gram tiles of its chunks, then one reduce of the split partials.
+constexpr int kStepDigits = 6;  // profile index of the digit conversion (include/hapod.h)
+
 bool step_gram_oz(Env& env, std::vector<Work*>& ws) {
   if (ws.empty()) return true;
   const int nw = (int)ws.size();
-  double bytes = 0, flops = 0;
+  double bytes = 0, flops = 0, dbytes = 0;
   for (Work* w : ws) {
     bytes += 8.0 * w->n * w->m;
     flops += (double)w->n * w->m * (w->m + 1);
+    dbytes += 22.0 * w->n * w->m;
   }
   cudaEvent_t t0 = env.tic();
   if (!oz_exponents(env, ws)) return false;
+  env.toc(t0, kStepDigits, 1, 0.0, 0.0);
   std::vector<OzChunk> chunks;
   std::vector<std::pair<size_t, size_t>> rounds;
   size_t max_round = 0;
@@ -378,7 +382,6 @@ bool step_gram_oz(Env& env, std::vector<Work*>& ws) {
   double* partial = (double*)env.alloc(sizeof(double) * std::max<size_t>(1, total_partial), "alloc gram partials");
   uint16_t* digits = (uint16_t*)env.alloc(std::max<size_t>(16, max_round), "alloc digit planes");
   bool ok = partial && digits;
-  int launches = 1;
   std::vector<void*> job_bufs;
   for (size_t r = 0; r < rounds.size() && ok; ++r) {
     std::vector<OzSplitJob> sj;
@@ -413,9 +416,12 @@ bool step_gram_oz(Env& env, std::vector<Work*>& ws) {
     OzGramJob* gj_d = env.upload(gj, "upload gram jobs");
     job_bufs.push_back(sj_d);
     job_bufs.push_back(gj_d);
-    ok = sj_d && gj_d && env.cuda(launch_oz_split(sj_d, (int)sj.size(), blocks, env.s), "digit split launch") &&
-         env.cuda(launch_gram_oz(gj_d, (int)gj.size(), items, env.err_dev, env.s), "gram launch");
-    launches += 2;
+    cudaEvent_t ts = env.tic();
+    ok = sj_d && gj_d && env.cuda(launch_oz_split(sj_d, (int)sj.size(), blocks, env.s), "digit split launch");
+    env.toc(ts, kStepDigits, 1, r == 0 ? dbytes : 0.0, 0.0);
+    cudaEvent_t tg = env.tic();
+    ok = ok && env.cuda(launch_gram_oz(gj_d, (int)gj.size(), items, env.err_dev, env.s), "gram launch");
+    env.toc(tg, 0, 1, r == 0 ? bytes : 0.0, r == 0 ? flops : 0.0);
   }
   if (ok) {
     std::vector<OzReduceJob> rj(nw);
@@ -432,10 +438,10 @@ bool step_gram_oz(Env& env, std::vector<Work*>& ws) {
     }
     OzReduceJob* rj_d = env.upload(rj, "upload reduce jobs");
     job_bufs.push_back(rj_d);
+    cudaEvent_t tr = env.tic();
     ok = rj_d && env.cuda(launch_oz_reduce(rj_d, nw, cols, env.s), "gram reduce launch");
-    ++launches;
+    env.toc(tr, 0, 1, 0.0, 0.0);
   }
-  env.toc(t0, 0, launches, bytes, flops);
   for (void* p : job_bufs) env.release(p);
   env.release(partial);
   env.release(digits);

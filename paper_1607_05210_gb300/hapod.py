@@ -54,12 +54,12 @@ class hapod_tol(ctypes.Structure):
 
 
 HAPOD_FLAG_PROFILE = 1
-PROFILE_STEPS = ("gram", "eig", "truncate", "gather", "modes", "copy")
+PROFILE_STEPS = ("gram", "eig", "truncate", "gather", "modes", "copy", "digits")
 
 
 class hapod_profile_info(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double * 6), ("launches", ctypes.c_int64 * 6), ("bytes", ctypes.c_double * 6),
-                ("flops", ctypes.c_double * 6)]
+    _fields_ = [("ms", ctypes.c_double * 8), ("launches", ctypes.c_int64 * 8), ("bytes", ctypes.c_double * 8),
+                ("flops", ctypes.c_double * 8)]
 
 
 class hapod_node_info(ctypes.Structure):

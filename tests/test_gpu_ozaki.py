@@ -272,3 +272,27 @@ def test_hapod_streamed_advection_oz(H):
     s, U, st, stats, data = _run_tree(H, parent, cols, X, eps, 0.5, max_pending=1)
     eps_nodes = oracle.tolerances(parent, cols, eps / math.sqrt(S), 0.5)
     assert projection_error(X, U) <= sum(e * e for e in eps_nodes) * (1 + 1e-6) + 1e-22 * float(np.sum(X * X))
+
+
+def test_profile_steps_oz(H):
+    """HAPOD_FLAG_PROFILE: the digit conversion (step 'digits') is accounted apart from
+    the tensor-core Gram (step 'gram'), with the algorithmic volumes of the method."""
+    parent = synth.star_tree(3)
+    cols = [0, 20, 30, 25]
+    n = 5000
+    X = synth.prescribed_spectrum(n, 75, 10.0 ** (-0.1 * np.arange(75)), seed=4, noise=1e-12)
+    leaves, data = leaf_split(X, parent, cols)
+    ctx = H.hapod_create(parent, cols, 1e-4 * float(np.linalg.norm(X)), 0.5, n, H.HAPOD_FP64_OZAKI,
+                         flags=H.HAPOD_FLAG_PROFILE)
+    bufs = {a: to_dev(data[a]) for a in leaves}
+    for a in leaves:
+        H.hapod_push(ctx, a, bufs[a])
+    H.hapod_result(ctx)
+    prof = H.hapod_profile(ctx)
+    stats = [H.hapod_node_stats(ctx, a) for a in range(len(parent))]
+    H.hapod_destroy(ctx)
+    ms = [s_["m"] for s_ in stats if s_["m"] > 0]
+    assert prof["gram"]["ms"] > 0 and prof["digits"]["ms"] > 0 and prof["modes"]["ms"] > 0
+    assert prof["gram"]["launches"] >= 2 * 2 and prof["digits"]["launches"] >= 2 * 2  # two batches
+    assert prof["gram"]["flops"] == pytest.approx(sum(n * m * (m + 1) for m in ms))
+    assert prof["digits"]["bytes"] == pytest.approx(sum(22.0 * n * m for m in ms))
