@@ -15,14 +15,19 @@
 // rounded once to FP64.  The only rounding of the whole Gram is that final one and the FP64
 // sum over row splits.
 //
-// Work item = one 128 x 64 tile (columns 128 I.. x 64 J..) over one row split.  The
-// digit rows hold ceil(m / 8) column groups; a block that runs past them reads the
-// next digits or the buffer's slack, which only reach tile rows / columns >= m, never
-// written back.  One CTA per item, 18 warps:
+// Work item = one 128 x 64 tile (columns 128 I.. x 64 J..) over one row split.  A
+// digit plane of a row group holds ceil(m / 8) column groups; a block that runs past
+// them reads the next plane or the buffer's slack, which only reach tile rows /
+// columns >= m, never written back.  One CTA per item, 18 warps:
 //   warp 0       bulk-copy producer: 4-deep ring of 16-row stages (all 7 digit
-//                planes of the 128 A columns and the 64 B columns, 42 KB)
-//   warp 1       TMEM owner and single-thread UMMA issuer (28 MMAs of 128 x 64 x 16
-//                per stage into 7 level accumulators of 64 TMEM columns)
+//                planes of the 128 A columns and the 64 B columns, 42 KB; one copy
+//                per row group and digit plane of each block)
+//   warp 1       TMEM owner and single-thread UMMA issuer: per stage 10 MMAs
+//                128 x (64..256) x 16, digit t of the A columns against up to 4
+//                consecutive digits u of the B columns (consecutive planes form one
+//                K-major operand; the level accumulators t + u are adjacent 64-column
+//                blocks of TMEM): an MMA costs ~72 cycles at N = 64 and ~150 at
+//                N = 256 (measured), so grouping the planes halves the issue time
 //   warps 2..17  flushers: after every 128-row block, 16 columns x 32 lanes each
 // Every mbarrier wait is bounded: a timeout raises the error flag, the CTA drains
 // its copies and MMAs and frees TMEM.
@@ -35,8 +40,10 @@ namespace {
 
 constexpr int kAGroups = 16;                                  // column groups of the A block (128 columns)
 constexpr int kBGroups = 8;                                   // column groups of the B block (64 columns)
-constexpr int kStageA = 2 * kAGroups * kOzGroupBytes;         // two row groups: 28672 B
-constexpr int kStageB = 2 * kBGroups * kOzGroupBytes;         // 14336 B
+constexpr int kPlaneA = kAGroups * 128;                       // one digit plane of one row group: 2 KB
+constexpr int kPlaneB = kBGroups * 128;                       // 1 KB
+constexpr int kStageA = 2 * kOzDigits * kPlaneA;              // [row group][digit][16 groups]: 28672 B
+constexpr int kStageB = 2 * kOzDigits * kPlaneB;              // [row group][digit][8 groups]: 14336 B
 constexpr int kStageBytes = kStageA + kStageB;
 constexpr int kStages = 4;
 constexpr int kSmemBytes = kStages * kStageBytes + 128;
@@ -123,13 +130,18 @@ __global__ void __launch_bounds__(kThreads, 1) gram_oz_kernel(const OzGramJob* _
         if (k >= kStages && !tc::mbar_wait(&bars.empty[s], ((k / kStages) - 1) & 1, &abort_flag, err)) break;
         tc::mbar_expect_tx(&bars.full[s], kStageBytes);
         const int64_t rg0 = 2 * (int64_t)(st0 + k);
+        const int64_t plane_bytes = (int64_t)J.CGs * 128;  // one digit plane of one row group
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-          const int64_t row = (rg0 + q) * J.CGs;  // the A / B blocks may run past the stored groups
-          tc::bulk_load(stage_a(s) + q * (kStageA / 2), base + (row + kAGroups * TI) * kOzGroupBytes, kStageA / 2,
-                        &bars.full[s]);
-          tc::bulk_load(stage_b(s) + q * (kStageB / 2), base + (row + kBGroups * TJ) * kOzGroupBytes, kStageB / 2,
-                        &bars.full[s]);
+#pragma unroll
+          for (int p = 0; p < kOzDigits; ++p) {
+            // the A / B blocks may run past the stored groups (into the next plane / slack)
+            const uint8_t* row = base + ((rg0 + q) * kOzDigits + p) * plane_bytes;
+            tc::bulk_load(stage_a(s) + (q * kOzDigits + p) * kPlaneA, row + (int64_t)kPlaneA * TI, kPlaneA,
+                          &bars.full[s]);
+            tc::bulk_load(stage_b(s) + (q * kOzDigits + p) * kPlaneB, row + (int64_t)kPlaneB * TJ, kPlaneB,
+                          &bars.full[s]);
+          }
         }
         issued = k + 1;
       }
@@ -144,7 +156,6 @@ __global__ void __launch_bounds__(kThreads, 1) gram_oz_kernel(const OzGramJob* _
   } else if (warp == 1) {
     // ------------------------------------------------------------ UMMA issuer
     if (lane == 0) {
-      constexpr uint32_t idesc = tc::idesc_f16_f32_major(128, 64, 0, 0);
       for (int k = 0; k < nst; ++k) {
         const int s = k % kStages;
         const int pos = k % kBlockStages;
@@ -153,18 +164,19 @@ __global__ void __launch_bounds__(kThreads, 1) gram_oz_kernel(const OzGramJob* _
         if (!tc::mbar_wait(&bars.full[s], (k / kStages) & 1, &abort_flag, err)) break;
         tc::tc_fence_after();
         const uint32_t a0 = tc::smem_u32(stage_a(s)), b0 = tc::smem_u32(stage_b(s));
+        // A (digit t): LBO = row-group stride (K), SBO = 128 (column groups, M).
+        // B (digits u0 .. u0 + len - 1): LBO = row-group stride, SBO = 128 (column
+        // groups of one digit, then of the next: N = 64 len).
 #pragma unroll
-        for (int lv = 2; lv <= kLevels + 1; ++lv) {
-          const int t_lo = 1;
-          const int t_hi = lv - 1;
+        for (int t = 1; t <= kOzDigits; ++t) {
 #pragma unroll
-          for (int t = t_lo; t <= t_hi; ++t) {
-            const int u = lv - t;
-            // A: LBO = row-group stride (K), SBO = column-group stride (M); same for B
-            tc::umma_f16(tbase + (uint32_t)(lv - 2) * kLevelCols,
-                          tc::ns_desc(a0 + (uint32_t)(t - 1) * 128u, kStageA / 2, kOzGroupBytes),
-                          tc::ns_desc(b0 + (uint32_t)(u - 1) * 128u, kStageB / 2, kOzGroupBytes), idesc,
-                          (pos == 0 && t == t_lo) ? 0u : 1u);
+          for (int u0 = 1; u0 <= kLevels + 1 - t; u0 += 4) {
+            const int len = min(4, kLevels + 2 - t - u0);
+            const uint32_t idesc = tc::idesc_f16_f32_major(128, kLevelCols * len, 0, 0);
+            tc::umma_f16(tbase + (uint32_t)(t + u0 - 2) * kLevelCols,
+                         tc::ns_desc(a0 + (uint32_t)(t - 1) * kPlaneA, kOzDigits * kPlaneA, 128u),
+                         tc::ns_desc(b0 + (uint32_t)(u0 - 1) * kPlaneB, kOzDigits * kPlaneB, 128u), idesc,
+                         (pos == 0 && t == 1) ? 0u : 1u);
           }
         }
         tc::umma_commit(&bars.empty[s]);

@@ -103,7 +103,7 @@ struct OzColJob {
 cudaError_t launch_oz_colmax(const OzColJob* jobs_dev, int njobs, int64_t total_cols, cudaStream_t s);
 
 // Digit planes of rows [r0, r0 + rows) of X into `digits`, layout
-// [row group of 8][column group of 8 (CGs)][digit][column % 8][row % 8] (fp16),
+// [row group of 8][digit][column group of 8 (CGs)][column % 8][row % 8] (fp16),
 // RG = 2 ceil(rows / 16) row groups, CGs = ceil(m / 8) column groups; rows >= `rows`
 // and columns >= m are zero.
 struct OzSplitJob {
@@ -122,9 +122,10 @@ cudaError_t launch_oz_split(const OzSplitJob* jobs_dev, int njobs, int64_t total
 __host__ __device__ inline int64_t oz_row_groups(int64_t rows) { return 2 * ((rows + 15) / 16); }
 __host__ __device__ inline int32_t oz_col_groups(int64_t m) { return (int32_t)(16 * ((m + 127) / 128)); }
 __host__ __device__ inline int32_t oz_stored_groups(int64_t m) { return (int32_t)((m + 7) / 8); }
-// A Gram tile reads up to 15 column groups past the stored ones (rows of the tile that
-// are never written back): every digit buffer carries this much readable slack.
-constexpr size_t kOzDigitSlack = 16 * kOzGroupBytes;
+// A Gram tile reads up to 15 column groups past the stored ones of a digit plane (rows
+// of the tile that are never written back): every digit buffer carries this much
+// readable slack.
+constexpr size_t kOzDigitSlack = 16 * 128;
 
 // Gram of one digit block: items (split, tile) in split-major order; tile (I, J) =
 // columns [128 I, 128 I + 128) x [64 J, 64 J + 64), J >= 2 I, 64 J < m.  The item

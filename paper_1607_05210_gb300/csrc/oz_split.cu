@@ -10,10 +10,11 @@
 // so x = sign(x) 2^(E_j+1) sum_t d_t 2^(-8 t) up to the dropped tail (< 2^(E_j - 55)).
 //
 // Layout of a digit block (rows [r0, r0 + rows) of one node):
-//   [row group r/8][column group j/8][digit t][j % 8][r % 8]   (fp16)
-// i.e. 8 x 8 core matrices of 16-byte rows, all 7 digits of one 8 x 8 block
-// together (896 bytes).  Read as columns-by-rows it is the K-major no-swizzle UMMA
-// layout of the Gram (K = rows).
+//   [row group r/8][digit t][column group j/8][j % 8][r % 8]   (fp16)
+// i.e. 8 x 8 core matrices of 16-byte rows; one digit plane of one row group is a
+// contiguous run of ceil(m / 8) column groups.  Read as columns-by-rows it is the
+// K-major no-swizzle UMMA layout of the Gram (K = rows), and consecutive digit
+// planes of a block of column groups form one operand of up to 4 digits.
 #include "hapod_internal.cuh"
 #include "oz_common.cuh"
 
@@ -70,8 +71,8 @@ __global__ void __launch_bounds__(kThreads) oz_colmax_kernel(const OzColJob* __r
 // Block = 64 rows x 32 columns (8 row groups x 4 column groups) of one digit block.
 // The FP64 tile is read column by column (each warp 256-byte runs of one column)
 // into shared memory, then thread (row group, column) converts 8 consecutive rows
-// of one column into one 16-byte core-matrix row per digit; the 8 lanes of one
-// column group write one 128-byte segment per digit.
+// of one column into one 16-byte core-matrix row per digit; the 32 lanes (32
+// consecutive columns) write one 512-byte segment per digit.
 constexpr int kTileRows = 64, kTileCols = 32;
 
 __global__ void __launch_bounds__(kThreads) oz_split_kernel(const OzSplitJob* __restrict__ jobs, int njobs) {
@@ -119,9 +120,9 @@ __global__ void __launch_bounds__(kThreads) oz_split_kernel(const OzSplitJob* __
       for (int q = 0; q < kOzDigits; ++q) w[q][p] = d[q];
     }
   }
-  uint4* out = reinterpret_cast<uint4*>(J.digits) + ((rg * J.CGs + (j >> 3)) * kOzDigits) * 8 + (j & 7);
+  uint4* out = reinterpret_cast<uint4*>(J.digits) + ((rg * kOzDigits) * J.CGs + (j >> 3)) * 8 + (j & 7);
 #pragma unroll
-  for (int q = 0; q < kOzDigits; ++q) out[q * 8] = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+  for (int q = 0; q < kOzDigits; ++q) out[(size_t)q * J.CGs * 8] = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
 }
 
 dim3 grid_for(int64_t blocks) {
