@@ -189,8 +189,16 @@ hapod_status hapod_node_stats(const hapod_ctx* ctx, int32_t node, hapod_node_inf
  * context-free call when ctx is NULL).  Never NULL; owned by the library. */
 const char* hapod_last_error(const hapod_ctx* ctx);
 
-/* Free every resource of the context (waits for its stream).  NULL is a no-op. */
+/* Free every resource of the context (waits for its stream).  NULL is a no-op.
+ * The device memory goes back to the library's stream-ordered pool of the current
+ * device, which keeps it cached for the next context (see hapod_trim_pool). */
 void hapod_destroy(hapod_ctx* ctx);
+
+/* Return the device memory that the library's pool of the current device keeps
+ * cached between calls to the driver (waits for the work queued on `stream`, NULL =
+ * legacy default stream).  Memory still in use by a live context stays allocated.
+ * Errors: CUDA. */
+hapod_status hapod_trim_pool(void* stream);
 
 /* ------------------------------------------------------------------------
  * Single-node steps.  Each runs the same kernels a context uses, on one node,

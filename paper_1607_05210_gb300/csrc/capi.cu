@@ -1361,9 +1361,22 @@ void hapod_destroy(hapod_ctx* c) {
   }
   env.release(c->result);
   cudaStreamSynchronize(env.s);
-  if (env.pool) cudaMemPoolTrimTo(env.pool, 0);
   delete c->prof;
   delete c;
+}
+
+hapod_status hapod_trim_pool(void* stream) {
+  Env env;
+  if (!init_env(env, stream)) {
+    g_thread_error = env.err;
+    return env.code;
+  }
+  if (!env.cuda(cudaStreamSynchronize(env.s), "synchronize") ||
+      !env.cuda(cudaMemPoolTrimTo(env.pool, 0), "cudaMemPoolTrimTo")) {
+    g_thread_error = env.err;
+    return env.code;
+  }
+  return HAPOD_OK;
 }
 
 // ------------------------------------------------------------- single-node steps

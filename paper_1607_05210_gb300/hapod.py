@@ -88,6 +88,7 @@ def _load() -> ctypes.CDLL:
         "hapod_profile": ([vp, ctypes.POINTER(hapod_profile_info)], i32),
         "hapod_last_error": ([vp], ctypes.c_char_p),
         "hapod_destroy": ([vp], None),
+        "hapod_trim_pool": ([vp], i32),
         "hapod_gram": ([i32, i64, i64, vp, i64, vp, vp], i32),
         "hapod_eig": ([i32, i64, vp, vp, vp, pi32, vp], i32),
         "hapod_truncate": ([i64, vp, d, pi64, pd, vp], i32),
@@ -104,7 +105,7 @@ def _load() -> ctypes.CDLL:
 
 _lib = _load()
 EXPORTED = ("hapod_create", "hapod_push", "hapod_result", "hapod_node_stats", "hapod_profile", "hapod_last_error",
-            "hapod_destroy",
+            "hapod_destroy", "hapod_trim_pool",
             "hapod_gram", "hapod_eig", "hapod_truncate", "hapod_modes", "hapod_pod", "hapod_gram_noalloc")
 
 
@@ -218,6 +219,11 @@ def hapod_last_error(ctx: Optional[Context] = None) -> str:
 
 def hapod_destroy(ctx: Context) -> None:
     ctx.close()
+
+
+def hapod_trim_pool(stream=None) -> None:
+    """Return the device memory the library's pool keeps cached between contexts."""
+    _check(_lib.hapod_trim_pool(ctypes.c_void_p(_stream(stream))))
 
 
 # ------------------------------------------------------------------ single-node steps
