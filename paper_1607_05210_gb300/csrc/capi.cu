@@ -386,6 +386,7 @@ bool step_gram_oz(Env& env, std::vector<Work*>& ws) {
   for (size_t r = 0; r < rounds.size() && ok; ++r) {
     std::vector<OzSplitJob> sj;
     std::vector<OzGramJob> gj;
+    std::vector<CUtensorMap> gm;
     size_t off = 0;
     int64_t blocks = 0, items = 0;
     for (size_t c = rounds[r].first; c < rounds[r].second; ++c) {
@@ -411,16 +412,28 @@ bool step_gram_oz(Env& env, std::vector<Work*>& ws) {
       G.tiles = oz_gram_tiles((int32_t)w->m);
       items += (int64_t)C.splits * G.tiles;
       gj.push_back(G);
+      CUtensorMap ma, mb;
+      if (!encode_oz_digits(&ma, dblk, C.CGs, C.RG, kOzGramAGroups) ||
+          !encode_oz_digits(&mb, dblk, C.CGs, C.RG, kOzGramBGroups)) {
+        ok = false;
+        env.fail(HAPOD_ERR_CUDA, "digit tensor map: cuTensorMapEncodeTiled failed");
+        break;
+      }
+      gm.push_back(ma);
+      gm.push_back(mb);
     }
+    if (!ok) break;
     OzSplitJob* sj_d = env.upload(sj, "upload split jobs");
     OzGramJob* gj_d = env.upload(gj, "upload gram jobs");
+    CUtensorMap* gm_d = env.upload(gm, "upload digit tensor maps");
     job_bufs.push_back(sj_d);
     job_bufs.push_back(gj_d);
+    job_bufs.push_back(gm_d);
     cudaEvent_t ts = env.tic();
-    ok = sj_d && gj_d && env.cuda(launch_oz_split(sj_d, (int)sj.size(), blocks, env.s), "digit split launch");
+    ok = sj_d && gj_d && gm_d && env.cuda(launch_oz_split(sj_d, (int)sj.size(), blocks, env.s), "digit split launch");
     env.toc(ts, kStepDigits, 1, r == 0 ? dbytes : 0.0, 0.0);
     cudaEvent_t tg = env.tic();
-    ok = ok && env.cuda(launch_gram_oz(gj_d, (int)gj.size(), items, env.err_dev, env.s), "gram launch");
+    ok = ok && env.cuda(launch_gram_oz(gj_d, gm_d, (int)gj.size(), items, env.err_dev, env.s), "gram launch");
     env.toc(tg, 0, 1, r == 0 ? bytes : 0.0, r == 0 ? flops : 0.0);
   }
   if (ok) {

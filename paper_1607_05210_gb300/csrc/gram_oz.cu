@@ -15,22 +15,23 @@
 // rounded once to FP64.  The only rounding of the whole Gram is that final one and the FP64
 // sum over row splits.
 //
-// Work item = one 128 x 64 tile (columns 128 I.. x 64 J..) over one row split.  A
-// digit plane of a row group holds ceil(m / 8) column groups; a block that runs past
-// them reads the next plane or the buffer's slack, which only reach tile rows /
-// columns >= m, never written back.  One CTA per item, 18 warps:
-//   warp 0       bulk-copy producer: 4-deep ring of 16-row stages (all 7 digit
-//                planes of the 128 A columns and the 64 B columns, 42 KB; one copy
-//                per row group and digit plane of each block)
-//   warp 1       TMEM owner and single-thread UMMA issuer: per stage 10 MMAs
-//                128 x (64..256) x 16, digit t of the A columns against up to 4
-//                consecutive digits u of the B columns (consecutive planes form one
-//                K-major operand; the level accumulators t + u are adjacent 64-column
-//                blocks of TMEM): an MMA costs ~72 cycles at N = 64 and ~150 at
-//                N = 256 (measured), so grouping the planes halves the issue time
-//   warps 2..17  flushers: after every 128-row block, 16 columns x 32 lanes each
-// Every mbarrier wait is bounded: a timeout raises the error flag, the CTA drains
-// its copies and MMAs and frees TMEM.
+// Work item = one 128 x 32 tile (columns 128 I.. x 32 J..) over one row split.  A
+// digit plane of a row group holds ceil(m / 8) column groups; tile rows / columns
+// >= m are never written back.  One CTA per item, 18 warps:
+//   warp 0       TMA producer: 6-deep ring of 16-row stages (all 7 digit planes of
+//                the 128 A columns and the 32 B columns, 35 KB) in two 4-D tensor
+//                copies per stage (one per block: 2 row groups x 7 digits x groups);
+//                column groups past the stored ones read as zero
+//   warp 1       TMEM owner and single-thread UMMA issuer: per stage 7 MMAs
+//                128 x 32 (8 - t) x 16, digit t of the A columns against the digits
+//                u = 1 .. 8 - t of the B columns (consecutive planes form one K-major
+//                operand; the level accumulators t + u are adjacent 32-column blocks of
+//                TMEM).  Two sets of the seven level accumulators (2 x 224 columns)
+//                alternate between 128-row blocks, so the flush of one block runs
+//                under the MMAs of the next.
+//   warps 2..17  flushers: after every 128-row block, 8 columns x 32 lanes each
+// (18 warps put 5 on two of the four SM sub-partitions, whose 16K registers cap a
+// thread at 96).
 #include "hapod_internal.cuh"
 #include "oz_common.cuh"
 #include "tc_common.cuh"
@@ -38,45 +39,52 @@
 namespace hapod {
 namespace {
 
-constexpr int kAGroups = 16;                                  // column groups of the A block (128 columns)
-constexpr int kBGroups = 8;                                   // column groups of the B block (64 columns)
+constexpr int kAGroups = kOzGramAGroups;                      // column groups of the A block (128 columns)
+constexpr int kBGroups = kOzGramBGroups;                      // column groups of the B block (32 columns)
 constexpr int kPlaneA = kAGroups * 128;                       // one digit plane of one row group: 2 KB
-constexpr int kPlaneB = kBGroups * 128;                       // 1 KB
+constexpr int kPlaneB = kBGroups * 128;                       // 512 B
 constexpr int kStageA = 2 * kOzDigits * kPlaneA;              // [row group][digit][16 groups]: 28672 B
-constexpr int kStageB = 2 * kOzDigits * kPlaneB;              // [row group][digit][8 groups]: 14336 B
+constexpr int kStageB = 2 * kOzDigits * kPlaneB;              // [row group][digit][4 groups]: 7168 B
 constexpr int kStageBytes = kStageA + kStageB;
-constexpr int kStages = 4;
+constexpr int kStages = 6;
 constexpr int kSmemBytes = kStages * kStageBytes + 128;
 constexpr int kBlockStages = kOzKBlock / 16;                  // stages per exact block
 constexpr int kThreads = 576;
 constexpr int kFirstFlushWarp = 2;
 constexpr int kFlushWarps = 16;
 constexpr int kLevels = kOzLevels;
-constexpr uint32_t kLevelCols = 64;
+constexpr int kTileCols = kBGroups * 8;                       // 32
+constexpr uint32_t kLevelCols = kTileCols;
+constexpr uint32_t kSetCols = kLevels * kLevelCols;           // 224: one set of level accumulators
 constexpr uint32_t kTmemCols = 512;
+constexpr int kFlushCols = kTileCols / 4;                     // columns per flusher warp
+static_assert(2 * kSetCols <= kTmemCols, "two accumulator sets must fit in TMEM");
+static_assert(kSmemBytes <= 227 * 1024, "shared memory");
 
 struct Bars {
   uint64_t full[kStages];
   uint64_t empty[kStages];
-  uint64_t acc_full;
-  uint64_t acc_empty;
+  uint64_t acc_full[2];
+  uint64_t acc_empty[2];
   uint64_t mma_done;
 };
 
-// tile index -> (I, J), J from 2 I up to ceil(m / 64) - 1
+constexpr int kJPerI = 128 / kTileCols;  // B blocks per A block
+
+// tile index -> (I, J), J from 4 I up to ceil(m / 32) - 1
 __device__ __forceinline__ void tile_of(int tile, int m, int* I, int* J) {
-  const int jmax = (m + 63) / 64;
+  const int jmax = (m + kTileCols - 1) / kTileCols;
   int i = 0;
   for (;; ++i) {
-    const int cnt = jmax - 2 * i;
+    const int cnt = jmax - kJPerI * i;
     if (cnt <= 0 || tile < cnt) break;
     tile -= cnt;
   }
   *I = i;
-  *J = 2 * i + tile;
+  *J = kJPerI * i + tile;
 }
 
-__global__ void __launch_bounds__(kThreads, 1) gram_oz_kernel(const OzGramJob* __restrict__ jobs, int njobs, int* err) {
+__global__ void __launch_bounds__(kThreads, 1) gram_oz_kernel(const OzGramJob* __restrict__ jobs, const CUtensorMap* __restrict__ maps, int njobs, int* err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   __shared__ Bars bars;
@@ -108,8 +116,10 @@ __global__ void __launch_bounds__(kThreads, 1) gram_oz_kernel(const OzGramJob* _
       tc::mbar_init(&bars.full[s], 1);
       tc::mbar_init(&bars.empty[s], 1);
     }
-    tc::mbar_init(&bars.acc_full, 1);
-    tc::mbar_init(&bars.acc_empty, kFlushWarps);
+    for (int a = 0; a < 2; ++a) {
+      tc::mbar_init(&bars.acc_full[a], 1);
+      tc::mbar_init(&bars.acc_empty[a], kFlushWarps);
+    }
     tc::mbar_init(&bars.mma_done, 1);
     abort_flag = 0;
     tc::mbar_fence_init();
@@ -123,26 +133,18 @@ __global__ void __launch_bounds__(kThreads, 1) gram_oz_kernel(const OzGramJob* _
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0 && nst > 0) {
-      const uint8_t* base = reinterpret_cast<const uint8_t*>(J.digits);
+      const CUtensorMap* mapA = maps + 2 * jlo;
+      const CUtensorMap* mapB = mapA + 1;
+      tc::tensormap_acquire(mapA);
+      tc::tensormap_acquire(mapB);
       int issued = 0;
       for (int k = 0; k < nst; ++k) {
         const int s = k % kStages;
         if (k >= kStages && !tc::mbar_wait(&bars.empty[s], ((k / kStages) - 1) & 1, &abort_flag, err)) break;
         tc::mbar_expect_tx(&bars.full[s], kStageBytes);
-        const int64_t rg0 = 2 * (int64_t)(st0 + k);
-        const int64_t plane_bytes = (int64_t)J.CGs * 128;  // one digit plane of one row group
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-#pragma unroll
-          for (int p = 0; p < kOzDigits; ++p) {
-            // the A / B blocks may run past the stored groups (into the next plane / slack)
-            const uint8_t* row = base + ((rg0 + q) * kOzDigits + p) * plane_bytes;
-            tc::bulk_load(stage_a(s) + (q * kOzDigits + p) * kPlaneA, row + (int64_t)kPlaneA * TI, kPlaneA,
-                          &bars.full[s]);
-            tc::bulk_load(stage_b(s) + (q * kOzDigits + p) * kPlaneB, row + (int64_t)kPlaneB * TJ, kPlaneB,
-                          &bars.full[s]);
-          }
-        }
+        const int rg0 = 2 * (st0 + k);
+        tc::tma_load_4d(stage_a(s), mapA, 0, kAGroups * TI, 0, rg0, &bars.full[s]);
+        tc::tma_load_4d(stage_b(s), mapB, 0, kBGroups * TJ, 0, rg0, &bars.full[s]);
         issued = k + 1;
       }
       if (abort_flag) {
@@ -159,28 +161,26 @@ __global__ void __launch_bounds__(kThreads, 1) gram_oz_kernel(const OzGramJob* _
       for (int k = 0; k < nst; ++k) {
         const int s = k % kStages;
         const int pos = k % kBlockStages;
-        if (pos == 0 && k > 0 && !tc::mbar_wait(&bars.acc_empty, ((k / kBlockStages) - 1) & 1, &abort_flag, err))
+        const int kb = k / kBlockStages;
+        const int set = kb & 1;
+        if (pos == 0 && kb >= 2 && !tc::mbar_wait(&bars.acc_empty[set], ((kb >> 1) - 1) & 1, &abort_flag, err))
           break;
         if (!tc::mbar_wait(&bars.full[s], (k / kStages) & 1, &abort_flag, err)) break;
         tc::tc_fence_after();
         const uint32_t a0 = tc::smem_u32(stage_a(s)), b0 = tc::smem_u32(stage_b(s));
+        const uint32_t acc = tbase + (uint32_t)set * kSetCols;
         // A (digit t): LBO = row-group stride (K), SBO = 128 (column groups, M).
-        // B (digits u0 .. u0 + len - 1): LBO = row-group stride, SBO = 128 (column
-        // groups of one digit, then of the next: N = 64 len).
+        // B (digits 1 .. 8 - t): LBO = row-group stride, SBO = 128 (column groups of
+        // one digit, then of the next: N = 32 (8 - t)); D = levels t + 1 .. 8.
 #pragma unroll
         for (int t = 1; t <= kOzDigits; ++t) {
-#pragma unroll
-          for (int u0 = 1; u0 <= kLevels + 1 - t; u0 += 4) {
-            const int len = min(4, kLevels + 2 - t - u0);
-            const uint32_t idesc = tc::idesc_f16_f32_major(128, kLevelCols * len, 0, 0);
-            tc::umma_f16(tbase + (uint32_t)(t + u0 - 2) * kLevelCols,
-                         tc::ns_desc(a0 + (uint32_t)(t - 1) * kPlaneA, kOzDigits * kPlaneA, 128u),
-                         tc::ns_desc(b0 + (uint32_t)(u0 - 1) * kPlaneB, kOzDigits * kPlaneB, 128u), idesc,
-                         (pos == 0 && t == 1) ? 0u : 1u);
-          }
+          const uint32_t idesc = tc::idesc_f16_f32_major(128, kLevelCols * (kLevels + 1 - t), 0, 0);
+          tc::umma_f16(acc + (uint32_t)(t - 1) * kLevelCols,
+                       tc::ns_desc(a0 + (uint32_t)(t - 1) * kPlaneA, kOzDigits * kPlaneA, 128u),
+                       tc::ns_desc(b0, kOzDigits * kPlaneB, 128u), idesc, (pos == 0 && t == 1) ? 0u : 1u);
         }
         tc::umma_commit(&bars.empty[s]);
-        if (pos == kBlockStages - 1 || k == nst - 1) tc::umma_commit(&bars.acc_full);
+        if (pos == kBlockStages - 1 || k == nst - 1) tc::umma_commit(&bars.acc_full[set]);
       }
       tc::umma_commit(&bars.mma_done);
       const long long t0 = clock64();
@@ -190,33 +190,38 @@ __global__ void __launch_bounds__(kThreads, 1) gram_oz_kernel(const OzGramJob* _
   } else {
     // ------------------------------------------------------------ flushers + result
     const int q = warp & 3;                          // TMEM lane quarter
-    const int cw = (warp - kFirstFlushWarp) >> 2;    // 16-column slice of the 64-column tile
+    const int cw = (warp - kFirstFlushWarp) >> 2;    // 8-column slice of the 32-column tile
     const uint32_t lanes = (uint32_t)(32 * q) << 16;
-    long long hi[16], lo[16];
+    long long hi[kFlushCols], lo[kFlushCols];
 #pragma unroll
-    for (int c = 0; c < 16; ++c) hi[c] = lo[c] = 0;
+    for (int c = 0; c < kFlushCols; ++c) hi[c] = lo[c] = 0;
     bool ok = true;
     for (int kb = 0; kb < nkb; ++kb) {
-      if (!tc::mbar_wait_warp(&bars.acc_full, kb & 1, &abort_flag, err)) {
+      const int set = kb & 1;
+      if (!tc::mbar_wait_warp(&bars.acc_full[set], (kb >> 1) & 1, &abort_flag, err)) {
         ok = false;
         break;
       }
       tc::tc_fence_after();
+      // all seven levels in flight at once, then one wait
+      uint32_t r[kLevels][kFlushCols];
+      const uint32_t col = tbase + lanes + (uint32_t)set * kSetCols + (uint32_t)(kFlushCols * cw);
+#pragma unroll
+      for (int lv = 0; lv < kLevels; ++lv) tc::tmem_ld8_raw(col + (uint32_t)lv * kLevelCols, r[lv]);
+      tc::tmem_wait_ld();
 #pragma unroll
       for (int lv = 0; lv < kLevels; ++lv) {
-        float v[16];
-        tc::tmem_ld16(tbase + lanes + (uint32_t)lv * kLevelCols + (uint32_t)(16 * cw), v);
-        tc::tmem_wait_ld();
+        tc::reg_barrier8(r[lv]);  // keep every use of the loaded registers after the wait
         const long long w = oz_level_weight(lv);
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const long long x = (long long)__float2int_rn(v[c]) * w;
+        for (int c = 0; c < kFlushCols; ++c) {
+          const long long x = (long long)__float2int_rn(__uint_as_float(r[lv][c])) * w;
           if (lv < 3) hi[c] += x; else lo[c] += x;
         }
       }
       tc::tc_fence_before();
       __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&bars.acc_empty);
+      if (lane == 0) tc::mbar_arrive(&bars.acc_empty[set]);
     }
     if (__all_sync(0xffffffffu, ok && !abort_flag)) {
       const int mp = J.mp;
@@ -224,8 +229,8 @@ __global__ void __launch_bounds__(kThreads, 1) gram_oz_kernel(const OzGramJob* _
       const int Ei = i < J.m ? J.exps[i] : 0;
       double* out = J.partial + (size_t)sp * mp * mp;
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        const int j = 64 * TJ + 16 * cw + c;
+      for (int c = 0; c < kFlushCols; ++c) {
+        const int j = kTileCols * TJ + kFlushCols * cw + c;
         if (i < J.m && j < J.m) {  // rows / columns past m come from slack digits
           const int Ej = J.exps[j];
           double v;
@@ -274,13 +279,14 @@ dim3 grid_for(int64_t blocks) {
 }  // namespace
 
 int oz_gram_tiles(int32_t m) {
-  const int jmax = (m + 63) / 64;
+  const int jmax = (m + kTileCols - 1) / kTileCols;
   int n = 0;
-  for (int i = 0; 2 * i < jmax; ++i) n += jmax - 2 * i;
+  for (int i = 0; kJPerI * i < jmax; ++i) n += jmax - kJPerI * i;
   return n;
 }
 
-cudaError_t launch_gram_oz(const OzGramJob* jobs_dev, int njobs, int64_t total_items, int* err_flag, cudaStream_t s) {
+cudaError_t launch_gram_oz(const OzGramJob* jobs_dev, const CUtensorMap* maps_dev, int njobs, int64_t total_items,
+                           int* err_flag, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(gram_oz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
@@ -288,7 +294,7 @@ cudaError_t launch_gram_oz(const OzGramJob* jobs_dev, int njobs, int64_t total_i
     attr = true;
   }
   if (njobs <= 0 || total_items <= 0) return cudaSuccess;
-  gram_oz_kernel<<<grid_for(total_items), kThreads, kSmemBytes, s>>>(jobs_dev, njobs, err_flag);
+  gram_oz_kernel<<<grid_for(total_items), kThreads, kSmemBytes, s>>>(jobs_dev, maps_dev, njobs, err_flag);
   return cudaGetLastError();
 }
 

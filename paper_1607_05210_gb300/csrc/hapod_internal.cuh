@@ -122,15 +122,19 @@ cudaError_t launch_oz_split(const OzSplitJob* jobs_dev, int njobs, int64_t total
 __host__ __device__ inline int64_t oz_row_groups(int64_t rows) { return 2 * ((rows + 15) / 16); }
 __host__ __device__ inline int32_t oz_col_groups(int64_t m) { return (int32_t)(16 * ((m + 127) / 128)); }
 __host__ __device__ inline int32_t oz_stored_groups(int64_t m) { return (int32_t)((m + 7) / 8); }
-// A Gram tile reads up to 15 column groups past the stored ones of a digit plane (rows
-// of the tile that are never written back): every digit buffer carries this much
-// readable slack.
+// Readable slack after every digit buffer (one A block of column groups).
 constexpr size_t kOzDigitSlack = 16 * 128;
+// Tensor map of one digit block [RG row groups][7 digits][CGs column groups][64 fp16]
+// with a box of 2 row groups x 7 digits x box_groups column groups (out-of-range
+// groups read as zero).
+bool encode_oz_digits(CUtensorMap* out, const void* base, int32_t CGs, int64_t RG, int box_groups);
+constexpr int kOzGramAGroups = 16;  // column groups of a Gram tile's A block (128 columns)
+constexpr int kOzGramBGroups = 4;   // column groups of its B block (32 columns)
 
 // Gram of one digit block: items (split, tile) in split-major order; tile (I, J) =
-// columns [128 I, 128 I + 128) x [64 J, 64 J + 64), J >= 2 I, 64 J < m.  The item
-// writes the entries i, j < m of its FP64 128 x 64 block into partial slot `split`
-// (mp x mp, ld mp).
+// columns [128 I, 128 I + 128) x [32 J, 32 J + 32), J >= 4 I, 32 J < m.  The item
+// writes the entries i, j < m of its FP64 128 x 32 block into partial slot `split`
+// (mp x mp, ld mp).  maps[2 k], maps[2 k + 1]: the A and B boxes of job k.
 struct OzGramJob {
   const uint16_t* digits;
   const int32_t* exps;
@@ -146,7 +150,8 @@ struct OzGramJob {
   int32_t pad;
 };
 int oz_gram_tiles(int32_t m);
-cudaError_t launch_gram_oz(const OzGramJob* jobs_dev, int njobs, int64_t total_items, int* err_flag, cudaStream_t s);
+cudaError_t launch_gram_oz(const OzGramJob* jobs_dev, const CUtensorMap* maps_dev, int njobs, int64_t total_items,
+                           int* err_flag, cudaStream_t s);
 // G (m x m, ld m) = sum of `slots` partials (upper triangle, mirrored).
 struct OzReduceJob {
   const double* partial;
