@@ -19,9 +19,10 @@
 // digit plane of a row group holds ceil(m / 8) column groups; tile rows / columns
 // >= m are never written back.  One CTA per item, 18 warps:
 //   warp 0       TMA producer: 6-deep ring of 16-row stages (all 7 digit planes of
-//                the 128 A columns and the 32 B columns, 35 KB) in two 4-D tensor
-//                copies per stage (one per block: 2 row groups x 7 digits x groups);
-//                column groups past the stored ones read as zero
+//                the 128 A columns and the 32 B columns, 35 KB) in two 3-D tensor
+//                copies per stage (one per block: 2 row groups x 7 digits x one run
+//                of whole column groups); column groups past the stored ones read
+//                as zero
 //   warp 1       TMEM owner and single-thread UMMA issuer: per stage 7 MMAs
 //                128 x 32 (8 - t) x 16, digit t of the A columns against the digits
 //                u = 1 .. 8 - t of the B columns (consecutive planes form one K-major
@@ -143,8 +144,8 @@ __global__ void __launch_bounds__(kThreads, 1) gram_oz_kernel(const OzGramJob* _
         if (k >= kStages && !tc::mbar_wait(&bars.empty[s], ((k / kStages) - 1) & 1, &abort_flag, err)) break;
         tc::mbar_expect_tx(&bars.full[s], kStageBytes);
         const int rg0 = 2 * (st0 + k);
-        tc::tma_load_4d(stage_a(s), mapA, 0, kAGroups * TI, 0, rg0, &bars.full[s]);
-        tc::tma_load_4d(stage_b(s), mapB, 0, kBGroups * TJ, 0, rg0, &bars.full[s]);
+        tc::tma_load_3d(stage_a(s), mapA, 16 * kAGroups * TI, 0, rg0, &bars.full[s]);
+        tc::tma_load_3d(stage_b(s), mapB, 16 * kBGroups * TJ, 0, rg0, &bars.full[s]);
         issued = k + 1;
       }
       if (abort_flag) {

@@ -342,13 +342,14 @@ bool encode_colmajor_f64(CUtensorMap* out, const void* base, int64_t rows, int64
 
 bool encode_oz_digits(CUtensorMap* out, const void* base, int32_t CGs, int64_t RG, int box_groups) {
   EncodeTiledFn fn = encode_fn();
-  if (!fn || !base || reinterpret_cast<uintptr_t>(base) % 16 != 0 || CGs < 1 || RG < 2) return false;
-  // [row group][digit][column group][64 fp16]: one box = 2 row groups x 7 digits x box_groups groups
-  cuuint64_t dims[4] = {64, (cuuint64_t)CGs, (cuuint64_t)kOzDigits, (cuuint64_t)RG};
-  cuuint64_t strides[3] = {128, (cuuint64_t)CGs * 128, (cuuint64_t)CGs * 128 * kOzDigits};
-  cuuint32_t box[4] = {64, (cuuint32_t)box_groups, (cuuint32_t)kOzDigits, 2};
-  cuuint32_t es[4] = {1, 1, 1, 1};
-  return fn(out, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, const_cast<void*>(base), dims, strides, box, es,
+  if (!fn || !base || reinterpret_cast<uintptr_t>(base) % 16 != 0 || CGs < 1 || RG < 2 || box_groups > 16) return false;
+  // [row group][digit][column groups x 128 B], addressed in 8-byte units so that a box
+  // row is box_groups whole column groups (up to 2 KB) of one digit plane
+  cuuint64_t dims[3] = {(cuuint64_t)CGs * 16, (cuuint64_t)kOzDigits, (cuuint64_t)RG};
+  cuuint64_t strides[2] = {(cuuint64_t)CGs * 128, (cuuint64_t)CGs * 128 * kOzDigits};
+  cuuint32_t box[3] = {(cuuint32_t)box_groups * 16, (cuuint32_t)kOzDigits, 2};
+  cuuint32_t es[3] = {1, 1, 1};
+  return fn(out, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<void*>(base), dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }

@@ -125,8 +125,8 @@ __host__ __device__ inline int32_t oz_stored_groups(int64_t m) { return (int32_t
 // Readable slack after every digit buffer (one A block of column groups).
 constexpr size_t kOzDigitSlack = 16 * 128;
 // Tensor map of one digit block [RG row groups][7 digits][CGs column groups][64 fp16]
-// with a box of 2 row groups x 7 digits x box_groups column groups (out-of-range
-// groups read as zero).
+// with a box of 2 row groups x 7 digits x box_groups (<= 16) column groups
+// (out-of-range groups read as zero).
 bool encode_oz_digits(CUtensorMap* out, const void* base, int32_t CGs, int64_t RG, int box_groups);
 constexpr int kOzGramAGroups = 16;  // column groups of a Gram tile's A block (128 columns)
 constexpr int kOzGramBGroups = 4;   // column groups of its B block (32 columns)

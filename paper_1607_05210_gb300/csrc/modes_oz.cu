@@ -312,7 +312,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     int uses[2] = {0, 0};
     int kbg = 0;
     for (int64_t it = blockIdx.x; it < total_items; it += gridDim.x) {
-      const OzModesJob& J = jobs[find_job(jobs, njobs, it)];
+      // by value: the stores to Y must not force reloads of the job's fields
+      const OzModesJob J = jobs[find_job(jobs, njobs, it)];
       const int64_t local = it - J.item_base;
       const int64_t rt = local % J.row_tiles;
       const int nt = (int)(local / J.row_tiles);
@@ -328,37 +329,48 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tc::tc_fence_after();
         const bool last = kb == nkb - 1;
+        // mode chunks of 8 that hold a mode < k (the rest of the tile is padding)
+        const int nc8 = min(NT / 8, (J.k - nt * NT + 7) / 8);
 #pragma unroll 1
-        for (int c8 = 0; c8 < NT / 8; ++c8) {
+        for (int c8 = 0; c8 < nc8; ++c8) {
+          const int col0 = nt * NT + 8 * c8;
+          // the partial sums of the earlier blocks, the column exponents and scales are
+          // loaded first, under the TMEM loads
+          double yp[8], sc[8];
+          int F[8];
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const bool in = col0 + c < J.k;
+            yp[c] = (kb > 0 && r < J.n && in) ? J.Y[(size_t)(col0 + c) * J.ldy + r] : 0.0;
+            F[c] = in ? __ldg(J.fexp + col0 + c) : 0;
+            sc[c] = (last && in && J.scale) ? __ldg(J.scale + col0 + c) : 1.0;
+          }
+          uint32_t lv8[kLevels][8];
+#pragma unroll
+          for (int lv = 0; lv < kLevels; ++lv) tc::tmem_ld8_raw(acc + (uint32_t)(lv * NT + 8 * c8), lv8[lv]);
+          tc::tmem_wait_ld();
           long long hi[8], lo[8];
 #pragma unroll
           for (int c = 0; c < 8; ++c) hi[c] = lo[c] = 0;
 #pragma unroll
           for (int lv = 0; lv < kLevels; ++lv) {
-            float v[8];
-            tc::tmem_ld8(acc + (uint32_t)(lv * NT + 8 * c8), v);
-            tc::tmem_wait_ld();
+            tc::reg_barrier8(lv8[lv]);  // every use of the loaded registers after the wait
             const long long w = oz_level_weight(lv);
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
-              const long long xv = (long long)__float2int_rn(v[c]) * w;
+              const long long xv = (long long)__float2int_rn(__uint_as_float(lv8[lv][c])) * w;
               if (lv < 3) hi[c] += xv; else lo[c] += xv;
             }
           }
           if (r < J.n) {
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
-              const int col = nt * NT + 8 * c8 + c;
+              const int col = col0 + c;
               if (col >= J.k) break;
-              const int F = J.fexp[col];
-              double* y = J.Y + (size_t)col * J.ldy + r;
-              double v = F == kOzNonFinite ? 0.0 : oz_combine(hi[c], lo[c], F - 62);
-              if (kb > 0) v += *y;
-              if (last) {
-                if (F == kOzNonFinite) v = __longlong_as_double(0x7FF8000000000000ll);
-                else if (J.scale) v *= J.scale[col];
-              }
-              *y = v;
+              double v = F[c] == kOzNonFinite ? 0.0 : oz_combine(hi[c], lo[c], F[c] - 62);
+              v += yp[c];
+              if (last) v = F[c] == kOzNonFinite ? __longlong_as_double(0x7FF8000000000000ll) : v * sc[c];
+              J.Y[(size_t)col * J.ldy + r] = v;
             }
           }
         }
