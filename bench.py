@@ -151,16 +151,17 @@ def tree():
 
 
 # ----------------------------------------------------------------- our arm
-def run_form(H, precision, bufs, fro2, steps, warmup, stream, dist_ctx, eps_rel=EPS_REL):
+def run_form(H, precision, bufs, fro2, steps, warmup, stream, dist_ctx, eps_rel=EPS_REL, shape=None,
+             omega=OMEGA, n_rows=N_ROWS):
     import torch
 
-    parent, leaves, cols = tree()
+    parent, leaves, cols = shape if shape is not None else tree()
     eps = eps_rel * math.sqrt(fro2)
     launches = [0]
     info = {}
 
     def step(profile):
-        ctx = H.hapod_create(parent, cols, eps, OMEGA, N_ROWS, precision, stream=stream,
+        ctx = H.hapod_create(parent, cols, eps, omega, n_rows, precision, stream=stream,
                              flags=H.HAPOD_FLAG_PROFILE if profile else 0)
         for i, a in enumerate(leaves):
             H.hapod_push(ctx, a, bufs[i].t())
@@ -195,11 +196,13 @@ def run_form(H, precision, bufs, fro2, steps, warmup, stream, dist_ctx, eps_rel=
     ms = dist_ctx.max(ms)
     # algorithmic bytes of the whole HAPOD (b n (2 m + k) per node)
     es = 4 if precision == H.HAPOD_MIXED_BF16X3 else 8
-    alg_bytes = sum(es * N_ROWS * (2 * st_["m"] + max(0, st_["k"])) for st_ in info["_nodes"] if st_["m"] > 0)
+    alg_bytes = sum(es * n_rows * (2 * st_["m"] + max(0, st_["k"])) for st_ in info["_nodes"] if st_["m"] > 0)
     per = {k: {f: v[f] / steps for f in v} for k, v in info.items() if not k.startswith("_")}
     return {"ms": ms, "alg_bytes": alg_bytes, "steps": per, "launches_per_step": launches[0] // steps,
             "k": info["_k"], "status": info["_status"],
-            "max_inner_k": max(st_["k"] for st_ in info["_nodes"] if st_["level"] > 1 and st_["level"] < 7),
+            "max_inner_k": max([st_["k"] for a, st_ in enumerate(info["_nodes"])
+                                if st_["level"] > 1 and parent[a] >= 0] or [0]),
+            "max_intermediate_k": max([st_["k"] for a, st_ in enumerate(info["_nodes"]) if parent[a] >= 0] or [0]),
             "leaf_k": max(st_["k"] for st_ in info["_nodes"] if st_["level"] == 1)}
 
 
@@ -369,6 +372,69 @@ class Dist:
             self.pg.destroy_process_group()
 
 
+SWEEP_OMEGAS = (0.1, 0.25, 0.5, 0.75, 0.9, 0.95, 0.99, 0.999)
+SWEEP_PARTITIONS = ((10, 1000), (40, 250), (100, 100), (400, 25), (1000, 10))  # blocks x columns (10^4)
+SWEEP_DEPTHS = (2, 3, 4, 5)
+
+
+def direct_pod_rank(sigma, eps):
+    """N of POD(S, eps) (Def. truncated POD) from all singular values of S."""
+    tail = 0.0
+    for j in range(len(sigma) - 1, -1, -1):
+        if tail + sigma[j] ** 2 > eps * eps:
+            return j + 1
+        tail += sigma[j] ** 2
+    return 0
+
+
+def run_sweep(kind, H, device, dist_ctx):
+    """Sec. 5.3 (omega) and Sec. 5.2 (tree shape) on the digit-slice FP64 form: one
+    JSON line per configuration (1 warm-up + 2 timed HAPODs).  The direct POD's
+    rank comes from the closed form sigma(X) = sqrt(n/2) sigma(C) of the
+    advection-diffusion snapshots X = B C."""
+    import numpy as np
+    import torch
+
+    from paper_1607_05210_gb300 import synth
+
+    stream = torch.cuda.Stream(device)
+    prec = H.HAPOD_FP64_OZAKI
+    if kind == "omega":
+        bufs, fro2 = make_inputs(torch.float64, device)
+        sig = math.sqrt(N_ROWS / 2.0) * np.linalg.svd(synth.advection_diffusion_coeffs(LEAVES * COLS, SEED),
+                                                     compute_uv=False)
+        k_pod = direct_pod_rank(sig, EPS_REL * math.sqrt(fro2))
+        for w in SWEEP_OMEGAS:
+            r = run_form(H, prec, bufs, fro2, 2, 1, stream, dist_ctx, EPS_REL, omega=w)
+            print(json.dumps({"sweep": "omega", "omega": w, "workload": WORKLOAD.replace("omega=0.5", f"omega={w}"),
+                              "value": LEAVES * COLS / (r["ms"] / 1e3), "unit": UNIT, "ms_per_step": r["ms"],
+                              "k_root": r["k"], "direct_pod_k": k_pod, "additional_modes": r["k"] - k_pod,
+                              "max_intermediate_k": r["max_intermediate_k"], "status": r["status"]}), flush=True)
+        return
+    total = 10_000
+    Xt = synth.advection_diffusion_device(N_ROWS, total, SEED, torch.float64, device)  # total x n
+    fro2 = sum(float(torch.sum(Xt[i:i + 500] ** 2)) for i in range(0, total, 500))
+    sig = math.sqrt(N_ROWS / 2.0) * np.linalg.svd(synth.advection_diffusion_coeffs(total, SEED), compute_uv=False)
+    k_pod = direct_pod_rank(sig, EPS_REL * math.sqrt(fro2))
+    for s_blocks, c in SWEEP_PARTITIONS:
+        bufs = [Xt[i * c:(i + 1) * c] for i in range(s_blocks)]
+        for d in SWEEP_DEPTHS:
+            parent = synth.nary_tree(s_blocks, d)
+            leaves = synth.leaves_of(parent)
+            cols = [0] * len(parent)
+            for a in leaves:
+                cols[a] = c
+            r = run_form(H, prec, bufs, fro2, 2, 1, stream, dist_ctx, EPS_REL, shape=(parent, leaves, cols))
+            arity = 1
+            while arity ** d < s_blocks:
+                arity += 1
+            print(json.dumps({"sweep": "trees", "blocks": s_blocks, "block_cols": c, "edge_depth": d,
+                              "levels": d + 1, "arity": arity, "nodes": len(parent),
+                              "value": total / (r["ms"] / 1e3), "unit": UNIT, "ms_per_step": r["ms"],
+                              "k_root": r["k"], "direct_pod_k": k_pod, "max_intermediate_k": r["max_intermediate_k"],
+                              "status": r["status"], "n": N_ROWS, "eps_rel": EPS_REL, "omega": OMEGA}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -383,6 +449,10 @@ def main():
                     help="run two digit-slice Gram + X V calls on one 2^20 x 256 FP64 leaf (k = 19) and exit: "
                          "the small case for ncu captures of oz_split / gram_oz / modes_oz")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep", choices=["omega", "trees"],
+                    help="print one JSON line per configuration and exit: 'omega' runs the benchmark "
+                         "workload for omega in 0.1 .. 0.999 (Sec. 5.3); 'trees' runs 10^4 advection-diffusion "
+                         "columns in 10 x 1000 .. 1000 x 10 blocks on balanced trees of edge depth 2..5 (Sec. 5.2)")
     args = ap.parse_args()
     os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
     dist_ctx = Dist()
@@ -419,6 +489,12 @@ def main():
             Y = H.hapod_modes(X, V, 19, None, H.HAPOD_FP64_OZAKI)
         torch.cuda.synchronize()
         print(json.dumps({"profile_leaf": True, "G00": float(G[0, 0]), "Y00": float(Y[0, 0])}))
+        dist_ctx.close()
+        return
+
+    if args.sweep:
+        if dist_ctx.rank == 0:
+            run_sweep(args.sweep, H, device, dist_ctx)
         dist_ctx.close()
         return
 

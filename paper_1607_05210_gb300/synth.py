@@ -60,6 +60,16 @@ def balanced_tree(arity: int, edge_depth: int, num_leaves: Optional[int] = None)
     return [(-1 if parent[a] < 0 else remap[parent[a]]) for a in range(len(parent)) if keep[a]]
 
 
+def nary_tree(num_leaves: int, edge_depth: int) -> List[int]:
+    """Tree-shape workload of Sec. 5.2: ``num_leaves`` blocks on the first leaf slots
+    of a balanced n-ary tree of edge depth ``edge_depth``, n the smallest arity with
+    n**edge_depth >= num_leaves (n = ceil(s^(1/depth)))."""
+    arity = 1
+    while arity ** edge_depth < num_leaves:
+        arity += 1
+    return balanced_tree(arity, edge_depth, num_leaves)
+
+
 def chain_of_subtrees(num_subtrees: int, subtree_edge_depth: int) -> List[int]:
     """Left-deep incremental chain (Sec. 3.2, skinny tree) whose inputs are roots of
     balanced binary subtrees: alpha_1 = subtree_1 root, alpha_l = POD(alpha_{l-1} U
