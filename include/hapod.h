@@ -26,8 +26,10 @@
  *     Digit-slice FP64 form (HAPOD_FP64_OZAKI): snapshots and results as in the
  *     FP64 form; the Gram and X V are formed on the fp16 tensor cores from an exact
  *     7-digit balanced base-256 fixed-point representation of each column (relative
- *     to a power-of-two bound of its largest entry, truncated below 2^-55 of it),
- *     with integer-exact accumulation and one FP64 rounding per entry.
+ *     to a power-of-two bound 2^E of its largest entry, truncated below 2^(E-55)),
+ *     each row's product x_i x_j represented to within 1.26 * 2^(E_i+E_j-53), with
+ *     integer-exact accumulation, one FP64 rounding per entry and row split (Gram)
+ *     or per 128-column block (X V), and FP64 sums over the splits / blocks.
  *     Mixed form (HAPOD_MIXED_BF16X3): snapshots are IEEE float; the Gram runs on
  *     the tensor cores as TF32 hi/lo products (x = hi + lo, hi*hi + hi*lo + lo*hi)
  *     accumulated in FP32 over short row chunks and summed in FP64, X V in FP32.
@@ -254,9 +256,10 @@ hapod_status hapod_truncate(int64_t m, const double* lambda, double eps, int64_t
  * double or float by precision); V: device m x >= N FP64 (ld ldv); scale: device N
  * doubles or NULL; Y: device n x N (ld ldy), same type as X.  The digit-slice form
  * computes Y from exact digit products (X as for hapod_gram, V column c against a
- * power-of-two bound of max_j 2^E_j |V_jc|), rounds once per entry, synchronises
- * the stream, and returns NaN columns if X or V holds Inf or NaN; TIMEOUT if a
- * bounded device-side wait ran out.
+ * power-of-two bound of max_j 2^E_j |V_jc|), rounds once per entry and 128-column
+ * block of X and sums the blocks in FP64, synchronises the stream, and returns NaN
+ * columns if X or V holds Inf or NaN; TIMEOUT if a bounded device-side wait ran
+ * out.
  */
 hapod_status hapod_modes(int32_t precision, int64_t n, int64_t m, const void* X, int64_t ldx, const double* V,
                          int64_t ldv, int64_t N, const double* scale, void* Y, int64_t ldy, void* stream);
