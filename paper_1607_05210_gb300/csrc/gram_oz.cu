@@ -5,17 +5,16 @@
 // With x_ri = 2^(E_i+1) sum_t d_t(r,i) 2^(-8t) (7 balanced base-256 digits),
 //   G_ij = 2^(E_i + E_j + 2) sum_{s=2}^{8} 2^(-8 s) L_s(i, j),
 //   L_s(i, j) = sum_r sum_{t+u=s} d_t(r,i) d_u(r,j),
-// keeping the 28 digit pairs with t + u <= 8 (the dropped pairs weigh at most
-// 6.02 * 2^(E_i + E_j - 56) per row, the six level-9 pairs of digits in [-128, 127];
+// keeping the 28 digit pairs with t + u <= 8.  The dropped pairs weigh at most
+// 6.02 * 2^(E_i + E_j - 56) per row (the six level-9 pairs of digits in [-128, 127]);
 // with the digit truncation, 2^(E_i + E_j - 54), a row's product is off by less than
-// 1.26 * 2^(E_i + E_j - 53)).  Over a block of 128
-// rows every level sum is an integer below 7 * 2^21 < 2^24, so the FP32 tensor-core
-// accumulation of digit products is exact; after each block the seven level
-// accumulators are converted to integers and added exactly into two int64
-// fixed-point sums per entry: hi = sum (L_2 2^16 + L_3 2^8 + L_4),
-// lo = sum (L_5 2^24 + L_6 2^16 + L_7 2^8 + L_8), G_ij = 2^(E_i+E_j-62) (hi 2^32 + lo),
-// rounded once to FP64.  The only rounding of the whole Gram is that final one and the FP64
-// sum over row splits.
+// 1.26 * 2^(E_i + E_j - 53).  Over a block of 128 rows every level sum is an integer
+// below 7 * 2^21 < 2^24, so the FP32 tensor-core accumulation of digit products is
+// exact; after each block the seven level accumulators are converted to integers and
+// added exactly into two int64 fixed-point sums per entry:
+//   hi = sum (L_2 2^16 + L_3 2^8 + L_4),   lo = sum (L_5 2^24 + L_6 2^16 + L_7 2^8 + L_8),
+//   G_ij = 2^(E_i + E_j - 62) (hi 2^32 + lo), rounded once to FP64 per row split;
+// the splits are summed in FP64 (oz_reduce_kernel).
 //
 // Work item = one 128 x 32 tile (columns 128 I.. x 32 J..) over one row split.  A
 // digit plane of a row group holds ceil(m / 8) column groups; tile rows / columns
