@@ -1,0 +1,67 @@
+"""Host-side helpers of the sweeps (no GPU): the tree-shape builder of Sec. 5.2 and
+the direct-POD rank used to count additional HAPOD modes (Sec. 5.3)."""
+import math
+
+import numpy as np
+import pytest
+
+import bench
+import oracle
+from paper_1607_05210_gb300 import synth
+
+
+def _depths(parent):
+    d = []
+    for a in range(len(parent)):
+        k, b = 0, a
+        while parent[b] >= 0:
+            b = parent[b]
+            k += 1
+        d.append(k)
+    return d
+
+
+@pytest.mark.parametrize("blocks,depth", [(10, 2), (40, 2), (100, 2), (100, 3), (400, 4), (1000, 5), (1, 3), (64, 6)])
+def test_nary_tree_shape(blocks, depth):
+    """s blocks on the first leaf slots of a balanced n-ary tree of the given edge
+    depth, n the smallest arity with n^depth >= s; one root, every leaf at the full
+    depth, no inner node without a leaf below it."""
+    parent = synth.nary_tree(blocks, depth)
+    leaves = synth.leaves_of(parent)
+    assert len(leaves) == blocks
+    assert parent.count(-1) == 1
+    arity = next(a for a in range(1, blocks + 2) if a ** depth >= blocks)
+    kids = [0] * len(parent)
+    for p in parent:
+        if p >= 0:
+            kids[p] += 1
+    assert max(kids) == (arity if blocks > 1 else 1)
+    d = _depths(parent)
+    assert all(d[a] == depth for a in leaves)
+    assert all(kids[a] > 0 for a in range(len(parent)) if a not in set(leaves))
+
+
+def test_nary_tree_matches_the_benchmark_tree():
+    """64 blocks at edge depth 6 is the benchmark's balanced binary tree."""
+    assert synth.nary_tree(64, 6) == synth.balanced_tree(2, 6)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_direct_pod_rank_matches_oracle_truncation(seed):
+    """The bench's rank from a spectrum equals the oracle's POD rank (Def. truncated
+    POD, inclusive threshold) on a matrix with that spectrum."""
+    rng = np.random.default_rng(seed)
+    m = 12
+    sigma = np.sort(rng.uniform(0.0, 1.0, m) ** 3)[::-1]
+    X = np.zeros((20, m))
+    X[:m, :m] = np.diag(sigma)
+    for eps in (0.0, 1e-3, float(sigma[m // 2]), 0.3, 10.0):
+        k_ref = oracle.pod(X, eps).N if eps > 0 else m
+        assert bench.direct_pod_rank(sigma, eps) == k_ref
+
+
+def test_direct_pod_rank_inclusive_threshold():
+    # tail after keeping 1 is exactly eps^2: keep 1 (the comparison is <=)
+    assert bench.direct_pod_rank([2.0, 1.0], 1.0) == 1
+    assert bench.direct_pod_rank([2.0, 1.0], 0.999) == 2
+    assert bench.direct_pod_rank([2.0, 1.0], math.sqrt(5.0)) == 0
