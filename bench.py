@@ -388,7 +388,7 @@ def direct_pod_rank(sigma, eps):
 
 
 def run_sweep(kind, H, device, dist_ctx):
-    """Sec. 5.3 (omega) and Sec. 5.2 (tree shape) on the digit-slice FP64 form: one
+    """Sec. 4.3 (omega) and Sec. 4.2 (tree shape) on the digit-slice FP64 form: one
     JSON line per configuration (1 warm-up + 2 timed HAPODs).  The direct POD's
     rank comes from the closed form sigma(X) = sqrt(n/2) sigma(C) of the
     advection-diffusion snapshots X = B C."""
@@ -451,8 +451,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep", choices=["omega", "trees"],
                     help="print one JSON line per configuration and exit: 'omega' runs the benchmark "
-                         "workload for omega in 0.1 .. 0.999 (Sec. 5.3); 'trees' runs 10^4 advection-diffusion "
-                         "columns in 10 x 1000 .. 1000 x 10 blocks on balanced trees of edge depth 2..5 (Sec. 5.2)")
+                         "workload for omega in 0.1 .. 0.999 (Sec. 4.3); 'trees' runs 10^4 advection-diffusion "
+                         "columns in 10 x 1000 .. 1000 x 10 blocks on balanced trees of edge depth 2..5 (Sec. 4.2)")
     args = ap.parse_args()
     os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
     dist_ctx = Dist()

@@ -61,7 +61,7 @@ def balanced_tree(arity: int, edge_depth: int, num_leaves: Optional[int] = None)
 
 
 def nary_tree(num_leaves: int, edge_depth: int) -> List[int]:
-    """Tree-shape workload of Sec. 5.2: ``num_leaves`` blocks on the first leaf slots
+    """Tree-shape workload of Sec. 4.2: ``num_leaves`` blocks on the first leaf slots
     of a balanced n-ary tree of edge depth ``edge_depth``, n the smallest arity with
     n**edge_depth >= num_leaves (n = ceil(s^(1/depth)))."""
     arity = 1

@@ -16,7 +16,7 @@ HAPOD, node by node, and its root modes, mapped back through B / sqrt(n/2), are
 the full-size modes.  Checked: every node's rank (up to a genuine tie at eps(a)^2),
 the root's singular values (1e-6 relative above 1e-5 sigma_max) and the largest
 principal angle between the GPU's and the oracle's root modes.  The same check
-runs for other omega (Sec. 5.3) and for the tree shapes of Sec. 5.2 (10^4 columns
+runs for other omega (Sec. 4.3) and for the tree shapes of Sec. 4.2 (10^4 columns
 in blocks on balanced n-ary trees, at n = 2^14 rows).
 """
 import math
@@ -105,7 +105,7 @@ def test_bench_workload_against_closed_form_oracle(workload):
 
 @pytest.mark.parametrize("omega", [0.1, 0.95])
 def test_bench_workload_other_omega(workload, omega):
-    """Sec. 5.3's trade-off parameter: smaller omega gives more final modes."""
+    """Sec. 4.3's trade-off parameter: smaller omega gives more final modes."""
     from paper_1607_05210_gb300 import hapod as H
 
     bufs, fro2 = workload
@@ -119,7 +119,7 @@ def test_bench_workload_other_omega(workload, omega):
 
 @pytest.mark.parametrize("blocks,edge_depth", [(40, 2), (100, 3), (400, 4), (1000, 5)])
 def test_tree_shapes_against_closed_form_oracle(blocks, edge_depth):
-    """Sec. 5.2's tree shapes: 10^4 columns in `blocks` equal blocks on the balanced
+    """Sec. 4.2's tree shapes: 10^4 columns in `blocks` equal blocks on the balanced
     n-ary tree of the given edge depth, n = 2^14 rows."""
     from paper_1607_05210_gb300 import hapod as H
 

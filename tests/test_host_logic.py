@@ -1,5 +1,5 @@
-"""Host-side helpers of the sweeps (no GPU): the tree-shape builder of Sec. 5.2 and
-the direct-POD rank used to count additional HAPOD modes (Sec. 5.3)."""
+"""Host-side helpers of the sweeps (no GPU): the tree-shape builder of Sec. 4.2 and
+the direct-POD rank used to count additional HAPOD modes (Sec. 4.3)."""
 import math
 
 import numpy as np
