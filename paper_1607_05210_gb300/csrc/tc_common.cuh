@@ -1,11 +1,10 @@
 // Shared device helpers for the tensor-core (tcgen05) kernels: mbarrier waits with
-// a bounded spin, TMA tiled and bulk loads, UMMA descriptors, TMEM allocation and
-// loads, and the split of FP32 values into bf16 hi + lo pieces.
+// a bounded spin, TMA tiled and bulk loads, UMMA descriptors, TMEM allocation,
+// loads and stores, and compensated FP32 accumulation.
 // Inline PTX for sm_103a (tcgen05 / cp.async.bulk.tensor / mbarrier).
 #pragma once
 
 #include <cuda.h>
-#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -118,11 +117,6 @@ __device__ __forceinline__ uint64_t ns_desc(uint32_t saddr, uint32_t lbo, uint32
 __host__ __device__ constexpr uint32_t idesc_f16_f32_major(uint32_t M, uint32_t N, uint32_t a_mn, uint32_t b_mn) {
   return (1u << 4) | (a_mn << 15) | (b_mn << 16) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }
-// Instruction descriptor: bf16 x bf16 -> FP32 with the A / B major-ness given
-// (0 = K-major, 1 = MN-major), M x N.
-__host__ __device__ constexpr uint32_t idesc_bf16_f32_major(uint32_t M, uint32_t N, uint32_t a_mn, uint32_t b_mn) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | (a_mn << 15) | (b_mn << 16) | ((N >> 3) << 17) | ((M >> 4) << 24);
-}
 
 // Untiled bulk copy global -> shared (16-byte aligned addresses, size a multiple of
 // 16), completing `bytes` transaction bytes on bar.
@@ -131,11 +125,6 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
                    smem_u32(dst)),
                "l"(src), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
-}
-
-// Instruction descriptor: bf16 x bf16 -> FP32, both operands K-major, M x N.
-__host__ __device__ constexpr uint32_t idesc_bf16_f32(uint32_t M, uint32_t N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }
 
 // Instruction descriptor: tf32 x tf32 -> FP32 (kind::tf32), both operands K-major.
@@ -189,15 +178,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
-// 8 consecutive FP32 columns of this warp's 32 TMEM lanes.
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
-  uint32_t r[8];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr));
-#pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-}
 // 8 consecutive FP32 columns as raw registers: valid only after tmem_wait_ld() and a
 // reg_barrier8 on them (the compiler does not know the load completes at the wait).
 __device__ __forceinline__ void tmem_ld8_raw(uint32_t taddr, uint32_t (&r)[8]) {
@@ -225,35 +205,12 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
 }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
-// Byte offset of (row, 16-byte chunk) in a K-major 128-byte-swizzled tile.
-__device__ __forceinline__ uint32_t sw128_offset(uint32_t row, uint32_t chunk) {
-  return (row >> 3) * 1024u + (row & 7u) * 128u + ((chunk ^ (row & 7u)) << 4);
-}
-
-// x = hi + lo with hi = bf16(x), lo = bf16(x - hi) (both round-to-nearest), packed pairs.
-__device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
-  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-  const float2 hf = __bfloat1622float2(h);
-  const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
-  hi = *reinterpret_cast<const uint32_t*>(&h);
-  lo = *reinterpret_cast<const uint32_t*>(&l);
-}
-
 // (s, c) += y with Kahan compensation: c holds the rounding error of s.
 __device__ __forceinline__ void kahan_acc(float& s, float& c, float y) {
   const float yc = y - c;
   const float t = s + yc;
   c = (t - s) - yc;
   s = t;
-}
-
-// (s, c) += y as a compensated FP32 pair (TwoSum): s + c carries ~48 bits.
-__device__ __forceinline__ void two_sum_acc(float& s, float& c, float y) {
-  const float t = s + y;
-  const float bp = t - s;
-  const float e = (s - (t - bp)) + (y - bp);
-  s = t;
-  c += e;
 }
 
 }  // namespace tc
