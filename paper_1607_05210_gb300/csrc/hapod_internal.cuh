@@ -122,7 +122,8 @@ cudaError_t launch_oz_split(const OzSplitJob* jobs_dev, int njobs, int64_t total
 __host__ __device__ inline int64_t oz_row_groups(int64_t rows) { return 2 * ((rows + 15) / 16); }
 __host__ __device__ inline int32_t oz_col_groups(int64_t m) { return (int32_t)(16 * ((m + 127) / 128)); }
 __host__ __device__ inline int32_t oz_stored_groups(int64_t m) { return (int32_t)((m + 7) / 8); }
-// Readable slack after every digit buffer (one A block of column groups).
+// Spare bytes after each round's digit buffers (one A block of column groups).  The
+// Gram's tensor-map reads zero-fill past the stored column groups and do not reach it.
 constexpr size_t kOzDigitSlack = 16 * 128;
 // Tensor map of one digit block [RG row groups][7 digits][CGs column groups][64 fp16]
 // with a box of 2 row groups x 7 digits x box_groups (<= 16) column groups
