@@ -69,3 +69,18 @@ def test_invalid_arguments_are_rejected_without_a_gpu(lib_path):
     # step entry points
     assert lib.hapod_gram(7, 10, 3, None, 10, None, None) == H.HAPOD_ERR_INVALID
     assert lib.hapod_truncate(4, None, -1.0, None, None, None) == H.HAPOD_ERR_INVALID
+
+
+def test_trim_pool_reports_a_missing_device(lib_path):
+    """hapod_trim_pool returns a status, never aborts: without a usable CUDA device it
+    is HAPOD_ERR_CUDA with the runtime's message in hapod_last_error()."""
+    import torch
+
+    from paper_1607_05210_gb300 import hapod as H
+
+    st = H._lib.hapod_trim_pool(None)
+    if torch.cuda.is_available():
+        assert st == H.HAPOD_OK
+    else:
+        assert st == H.HAPOD_ERR_CUDA
+        assert H.hapod_last_error()
