@@ -265,8 +265,9 @@ def run_e2e(H, precision, host_bufs, dev_bufs, fro2, steps, stream):
 # profiles/digit_slice_kernels_2p20x256.md (3.836 GB read + 0.010 GB written): the
 # digit planes once, the tile re-reads come from L2.  Per leaf launch, as the bench's
 # leaf-level launches; null once the kernel changes.
-OZ_GRAM_TRAFFIC = {"bytes_per_launch": 3.846e9, "launch": "one leaf, n = 2^20, m = 256",
-                   "algorithmic_digit_bytes": 3.758e9}
+OZ_GRAM_TRAFFIC = 3.846e9
+OZ_GRAM_TRAFFIC_NOTE = ("dram__bytes_read.sum + dram__bytes_write.sum of one gram_oz_kernel launch on a 2^20 x 256 "
+                        "leaf (the benchmark's leaf launches); the digit planes it reads are 3.758e9 bytes")
 
 
 def f64_alu(precision, H):
@@ -286,7 +287,7 @@ def roofline(res, precision, H, hbm, bf16, dom=None):
         # conversion is the separate "digits" step)
         ach = 28.0 * d["flops"] / (d["ms"] / 1e3) / 1e12
         return dom, {"bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16,
-                     "traffic": OZ_GRAM_TRAFFIC,
+                     "traffic": OZ_GRAM_TRAFFIC, "traffic_note": OZ_GRAM_TRAFFIC_NOTE,
                      "kernel": "gram_oz_kernel + oz_reduce_kernel (tcgen05 fp16 digit-pair MMAs, 28 pair "
                                "products per FP64 product; peak = measured sustained bf16, the fp16 dense "
                                "rate is the same)"}

@@ -65,3 +65,19 @@ def test_direct_pod_rank_inclusive_threshold():
     assert bench.direct_pod_rank([2.0, 1.0], 1.0) == 1
     assert bench.direct_pod_rank([2.0, 1.0], 0.999) == 2
     assert bench.direct_pod_rank([2.0, 1.0], math.sqrt(5.0)) == 0
+
+
+def test_roofline_fields_for_the_digit_slice_gram():
+    """bench.py's roofline object: tensor-bound digit Gram against the measured peak,
+    achieved = 28 fp16 flops per FP64 Gram flop over the step time, numeric traffic."""
+    from paper_1607_05210_gb300 import hapod as H
+
+    res = {"steps": {"gram": {"ms": 100.0, "launches": 64, "bytes": 1e9, "flops": 2e12},
+                     "modes": {"ms": 50.0, "launches": 7, "bytes": 1e9, "flops": 1e11}}}
+    dom, roof = bench.roofline(res, H.HAPOD_FP64_OZAKI, H, 6786.2, 1725.3)
+    assert dom == "gram" and roof["bound"] == "tensor" and roof["unit"] == "TFLOP/s"
+    assert roof["achieved"] == pytest.approx(28 * 2e12 / 0.1 / 1e12)
+    assert roof["frac"] == pytest.approx(roof["achieved"] / 1725.3)
+    assert isinstance(roof["traffic"], float) and roof["traffic"] > 0
+    dom, roof = bench.roofline(res, H.HAPOD_MIXED_BF16X3, H, 6786.2, 1725.3, "gram")
+    assert roof["bound"] == "hbm" and roof["achieved"] == pytest.approx(1e9 / 0.1 / 1e9)
