@@ -449,6 +449,10 @@ def main():
     ap.add_argument("--profile-leaf", action="store_true",
                     help="run two digit-slice Gram + X V calls on one 2^20 x 256 FP64 leaf (k = 19) and exit: "
                          "the small case for ncu captures of oz_split / gram_oz / modes_oz")
+    ap.add_argument("--profile-form", choices=["oz", "fp64", "mixed"], default="oz",
+                    help="with --profile-leaf: 'fp64' runs three FP64 Gram calls on a 2^20 x 64 "
+                         "advection-diffusion leaf (gram_f64_tiles), 'mixed' three mixed-form Gram calls on a "
+                         "2^20 x 256 FP32 one (gram_tc_kernel)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep", choices=["omega", "trees"],
                     help="print one JSON line per configuration and exit: 'omega' runs the benchmark "
@@ -481,6 +485,18 @@ def main():
     device = torch.device("cuda", dist_ctx.local)
     from paper_1607_05210_gb300 import hapod as H
 
+    if args.profile_leaf and args.profile_form != "oz":
+        from paper_1607_05210_gb300 import synth
+
+        cols, dtype, prec = ((64, torch.float64, H.HAPOD_FP64) if args.profile_form == "fp64"
+                             else (COLS, torch.float32, H.HAPOD_MIXED_BF16X3))
+        X = synth.advection_diffusion_device(N_ROWS, cols, SEED, dtype, device).t()  # column-major n x cols
+        for _ in range(3):
+            G = H.hapod_gram(X, prec)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_leaf": True, "form": args.profile_form, "G00": float(G[0, 0])}))
+        dist_ctx.close()
+        return
     if args.profile_leaf:
         torch.manual_seed(SEED)
         X = torch.randn((COLS, N_ROWS), dtype=torch.float64, device=device).t()  # column-major n x m
