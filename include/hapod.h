@@ -270,7 +270,8 @@ hapod_status hapod_modes(int32_t precision, int64_t n, int64_t m, const void* X,
  * *N_host; sigma (device, capacity m doubles, first N written, descending);
  * Y (device n x capacity m, ld ldy, first N columns = sigma_j phi_j; for eps == 0
  * Y = X and sigma = 1); *tail_host = discarded sum of sigma^2.  Synchronises the
- * stream.
+ * stream.  Errors: INVALID (also m > 13000 with eps > 0: the eigensolver's limit),
+ * CUDA, OOM, TIMEOUT, NONFINITE.
  */
 hapod_status hapod_pod(int32_t precision, int64_t n, int64_t m, const void* X, int64_t ldx, double eps,
                        int64_t* N_host, double* sigma, void* Y, int64_t ldy, double* tail_host, void* stream);

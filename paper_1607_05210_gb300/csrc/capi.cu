@@ -1456,6 +1456,10 @@ hapod_status hapod_eig(int32_t precision, int64_t m, const double* G, double* la
     g_thread_error = "hapod_eig: invalid argument";
     return HAPOD_ERR_INVALID;
   }
+  if (m > kEigMaxM) {  // checked on the host before any CUDA call, like the other arguments
+    g_thread_error = "hapod_eig: node wider than the eigensolver supports (13000 columns)";
+    return HAPOD_ERR_INVALID;
+  }
   if (sweeps_host) *sweeps_host = 0;
   if (m == 0) return HAPOD_OK;
   Env env;
@@ -1607,6 +1611,10 @@ hapod_status hapod_pod(int32_t precision, int64_t n, int64_t m, const void* X, i
   if (!valid_precision(precision) || n < 1 || m < 0 || m > INT32_MAX || ldx < n || ldy < n || !(eps >= 0.0) ||
       !N_host || (m > 0 && (!X || !Y || !sigma))) {
     g_thread_error = "hapod_pod: invalid argument";
+    return HAPOD_ERR_INVALID;
+  }
+  if (eps > 0.0 && m > kEigMaxM) {
+    g_thread_error = "hapod_pod: node wider than the eigensolver supports (13000 columns)";
     return HAPOD_ERR_INVALID;
   }
   Env env;

@@ -84,3 +84,34 @@ def test_trim_pool_reports_a_missing_device(lib_path):
     else:
         assert st == H.HAPOD_ERR_CUDA
         assert H.hapod_last_error()
+
+
+def test_single_node_steps_validate_arguments_on_the_host(lib_path):
+    """Each single-node entry point rejects bad arguments with HAPOD_ERR_INVALID and a
+    message before touching CUDA (so the same status comes back with or without a GPU)."""
+    from paper_1607_05210_gb300 import hapod as H
+
+    lib = H._lib
+    buf = (ctypes.c_double * 16)()
+    N, tail = ctypes.c_int64(0), ctypes.c_double(0.0)
+    calls = {
+        "modes N > m": lambda: lib.hapod_modes(0, 10, 3, buf, 10, buf, 3, 5, None, buf, 10, None),
+        "modes ldx < n": lambda: lib.hapod_modes(0, 10, 3, buf, 5, buf, 3, 2, None, buf, 10, None),
+        "modes null X": lambda: lib.hapod_modes(0, 10, 3, None, 10, buf, 3, 2, None, buf, 10, None),
+        "modes precision": lambda: lib.hapod_modes(9, 10, 3, buf, 10, buf, 3, 2, None, buf, 10, None),
+        "eig null G": lambda: lib.hapod_eig(0, 3, None, buf, buf, None, None),
+        "eig m > 13000": lambda: lib.hapod_eig(0, 13001, buf, buf, buf, None, None),
+        "pod eps < 0": lambda: lib.hapod_pod(0, 10, 3, buf, 10, -1.0, ctypes.byref(N), buf, buf, 10,
+                                             ctypes.byref(tail), None),
+        "pod ldy < n": lambda: lib.hapod_pod(0, 10, 3, buf, 10, 1.0, ctypes.byref(N), buf, buf, 5,
+                                             ctypes.byref(tail), None),
+        "pod m > 13000": lambda: lib.hapod_pod(0, 20000, 13001, buf, 20000, 1.0, ctypes.byref(N), buf, buf, 20000,
+                                               ctypes.byref(tail), None),
+        "gram ldx < n": lambda: lib.hapod_gram(0, 10, 3, buf, 5, buf, None),
+        "gram null G": lambda: lib.hapod_gram(0, 10, 3, buf, 10, None, None),
+        "noalloc m > 2816": lambda: lib.hapod_gram_noalloc(10, 2817, buf, 10, buf, None),
+        "truncate m < 0": lambda: lib.hapod_truncate(-1, buf, 1.0, ctypes.byref(N), ctypes.byref(tail), None),
+    }
+    for name, call in calls.items():
+        assert call() == H.HAPOD_ERR_INVALID, name
+        assert H.hapod_last_error(), name
