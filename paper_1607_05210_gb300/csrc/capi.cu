@@ -1272,7 +1272,10 @@ hapod_status hapod_create(const hapod_tree* tree, const hapod_tol* tol, int64_t 
 }
 
 hapod_status hapod_push(hapod_ctx* c, int32_t leaf, const void* dev_snapshots, int64_t ld, int64_t ncols) {
-  if (!c) return HAPOD_ERR_INVALID;
+  if (!c) {
+    g_thread_error = "hapod_push: null context";
+    return HAPOD_ERR_INVALID;
+  }
   if (c->poisoned) return HAPOD_ERR_STATE;
   if (leaf < 0 || leaf >= (int)c->nodes.size()) {
     c->err = "hapod_push: node index out of range";
@@ -1306,7 +1309,11 @@ hapod_status hapod_push(hapod_ctx* c, int32_t leaf, const void* dev_snapshots, i
 }
 
 hapod_status hapod_result(hapod_ctx* c, int64_t* k_out, double* sigma_host, void* dev_modes, int64_t ld_modes) {
-  if (!c || !k_out) return HAPOD_ERR_INVALID;
+  if (!c || !k_out) {
+    if (c) c->err = "hapod_result: null k_out";
+    g_thread_error = c ? "hapod_result: null k_out" : "hapod_result: null context";
+    return HAPOD_ERR_INVALID;
+  }
   if (c->poisoned) return HAPOD_ERR_STATE;
   if (c->leaves_pushed != c->leaves_total) {
     c->err = "hapod_result: not every leaf has been pushed";
@@ -1339,7 +1346,10 @@ hapod_status hapod_result(hapod_ctx* c, int64_t* k_out, double* sigma_host, void
 }
 
 hapod_status hapod_profile(hapod_ctx* c, hapod_profile_info* info) {
-  if (!c || !info) return HAPOD_ERR_INVALID;
+  if (!c || !info) {
+    g_thread_error = c ? "hapod_profile: null info" : "hapod_profile: null context";
+    return HAPOD_ERR_INVALID;
+  }
   memset(info, 0, sizeof(*info));
   if (!c->prof) return HAPOD_OK;
   if (!c->env.cuda(cudaStreamSynchronize(c->env.s), "synchronize")) return ctx_fail(c);
@@ -1349,7 +1359,11 @@ hapod_status hapod_profile(hapod_ctx* c, hapod_profile_info* info) {
 }
 
 hapod_status hapod_node_stats(const hapod_ctx* c, int32_t node, hapod_node_info* info) {
-  if (!c || !info || node < 0 || node >= (int)c->nodes.size()) return HAPOD_ERR_INVALID;
+  if (!c || !info || node < 0 || node >= (int)c->nodes.size()) {
+    g_thread_error = !c ? "hapod_node_stats: null context"
+                        : !info ? "hapod_node_stats: null info" : "hapod_node_stats: node index out of range";
+    return HAPOD_ERR_INVALID;
+  }
   const NodeRT& A = c->nodes[node];
   info->m = A.state == 2 ? A.m : 0;
   info->k = A.state == 2 ? A.k : -1;

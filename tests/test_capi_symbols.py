@@ -115,3 +115,20 @@ def test_single_node_steps_validate_arguments_on_the_host(lib_path):
     for name, call in calls.items():
         assert call() == H.HAPOD_ERR_INVALID, name
         assert H.hapod_last_error(), name
+
+
+def test_null_context_calls_fail_with_a_message(lib_path):
+    from paper_1607_05210_gb300 import hapod as H
+
+    lib = H._lib
+    info = H.hapod_node_info()
+    k = ctypes.c_int64(0)
+    checks = [
+        (lambda: lib.hapod_push(None, 0, None, 0, 0), "hapod_push"),
+        (lambda: lib.hapod_result(None, ctypes.byref(k), None, None, 0), "hapod_result"),
+        (lambda: lib.hapod_node_stats(None, 0, ctypes.byref(info)), "hapod_node_stats"),
+    ]
+    for call, name in checks:
+        assert call() == H.HAPOD_ERR_INVALID
+        assert name in H.hapod_last_error()
+    lib.hapod_destroy(None)  # a no-op
