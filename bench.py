@@ -195,7 +195,7 @@ def run_form(H, precision, bufs, fro2, steps, warmup, stream, dist_ctx, eps_rel=
     ms = ev0.elapsed_time(ev1) / steps
     ms = dist_ctx.max(ms)
     # algorithmic bytes of the whole HAPOD (b n (2 m + k) per node)
-    es = 4 if precision == H.HAPOD_MIXED_BF16X3 else 8
+    es = 4 if precision == H.HAPOD_MIXED_TF32X3 else 8
     alg_bytes = sum(es * n_rows * (2 * st_["m"] + max(0, st_["k"])) for st_ in info["_nodes"] if st_["m"] > 0)
     per = {k: {f: v[f] / steps for f in v} for k, v in info.items() if not k.startswith("_")}
     return {"ms": ms, "alg_bytes": alg_bytes, "steps": per, "launches_per_step": launches[0] // steps,
@@ -261,13 +261,31 @@ def run_e2e(H, precision, host_bufs, dev_bufs, fro2, steps, stream):
             "ms_per_step": ms, "h2d_ms": copy_ms, "h2d_gbs": h2d / (copy_ms / 1e3) / 1e9}
 
 
-# DRAM bytes (read + write) of one gram_oz_kernel launch on a 2^20 x 256 leaf, from
-# profiles/digit_slice_kernels_2p20x256.md (3.836 GB read + 0.010 GB written): the
-# digit planes once, the tile re-reads come from L2.  Per leaf launch, as the bench's
-# leaf-level launches; null once the kernel changes.
-OZ_GRAM_TRAFFIC = 3.846e9
-OZ_GRAM_TRAFFIC_NOTE = ("dram__bytes_read.sum + dram__bytes_write.sum of one gram_oz_kernel launch on a 2^20 x 256 "
-                        "leaf (the benchmark's leaf launches); the digit planes it reads are 3.758e9 bytes")
+# DRAM traffic of the dominant kernels, from one ncu capture per kernel
+# (dram__bytes_read.sum + dram__bytes_write.sum of a single launch), stored in
+# profiles/traffic.json with the SHA-256 of the kernel's source file at capture
+# time.  A kernel whose source changed since then reports traffic = null.
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def kernel_traffic(kernel: str):
+    """(bytes per launch, note) of the last capture of `kernel`, or (None, why)."""
+    import hashlib
+
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f)[kernel]
+    except (OSError, KeyError, ValueError):
+        return None, "no capture recorded"
+    src = rec["source"] if os.path.isabs(rec["source"]) else os.path.join(ROOT, rec["source"])
+    try:
+        with open(src, "rb") as f:
+            digest = hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None, "kernel source missing"
+    if digest != rec["sha256"]:
+        return None, f"{rec['source']} changed since the capture"
+    return float(rec["bytes_per_launch"]), rec["note"]
 
 
 def f64_alu(precision, H):
@@ -281,16 +299,17 @@ def roofline(res, precision, H, hbm, bf16, dom=None):
         dom = max((k for k in steps if steps[k]["launches"] > 0), key=lambda k: steps[k]["ms"])
     d = steps[dom]
     if precision == H.HAPOD_FP64_OZAKI and dom == "gram":
-        # 28 fp16 digit-pair products per FP64 product of the n m (m + 1) / 2 unique Gram
-        # entries (the library reports 2 n m (m + 1) / 2 FP64 flops for the step); the
-        # step's time is the tensor-core Gram kernels and the split reduce (the digit
-        # conversion is the separate "digits" step)
-        ach = 28.0 * d["flops"] / (d["ms"] / 1e3) / 1e12
-        return dom, {"bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16,
-                     "traffic": OZ_GRAM_TRAFFIC, "traffic_note": OZ_GRAM_TRAFFIC_NOTE,
-                     "kernel": "gram_oz_kernel + oz_reduce_kernel (tcgen05 fp16 digit-pair MMAs, 28 pair "
-                               "products per FP64 product; peak = measured sustained bf16, the fp16 dense "
-                               "rate is the same)"}
+        # the method's bytes: one pass over the FP64 snapshots, b n m per node (the
+        # library's step accounting); the digit-pair tensor work (28 fp16 products per
+        # FP64 product of the upper triangle) is reported beside it
+        ach = d["bytes"] / (d["ms"] / 1e3) / 1e9
+        traffic, note = kernel_traffic("gram_oz_kernel")
+        return dom, {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                     "traffic": traffic, "traffic_note": note,
+                     "digit_tflops": 28.0 * d["flops"] / (d["ms"] / 1e3) / 1e12,
+                     "kernel": "gram_oz_kernel + oz_reduce_kernel (tcgen05 fp16 digit-pair MMAs); achieved = "
+                               "8 n m algorithmic bytes per node over the step's CUDA-event time; digit_tflops = "
+                               "28 fp16 pair products per FP64 product of the upper triangle over the same time"}
     if f64_alu(precision, H) and dom in ("gram", "modes"):
         ach = d["flops"] / (d["ms"] / 1e3) / 1e12
         return dom, {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -489,7 +508,7 @@ def main():
         from paper_1607_05210_gb300 import synth
 
         cols, dtype, prec = ((64, torch.float64, H.HAPOD_FP64) if args.profile_form == "fp64"
-                             else (COLS, torch.float32, H.HAPOD_MIXED_BF16X3))
+                             else (COLS, torch.float32, H.HAPOD_MIXED_TF32X3))
         X = synth.advection_diffusion_device(N_ROWS, cols, SEED, dtype, device).t()  # column-major n x cols
         for _ in range(3):
             G = H.hapod_gram(X, prec)
@@ -539,9 +558,9 @@ def main():
     if "mixed" in args.forms:
         bufs, fro2 = make_inputs(torch.float32, device)
         try:
-            rm = run_form(H, H.HAPOD_MIXED_BF16X3, bufs, fro2, args.steps, args.warmup, stream, dist_ctx,
+            rm = run_form(H, H.HAPOD_MIXED_TF32X3, bufs, fro2, args.steps, args.warmup, stream, dist_ctx,
                           MIXED_EPS_REL)
-            forms[f"mixed@{MIXED_EPS_REL:g}"] = summarise(rm, H.HAPOD_MIXED_BF16X3, MIXED_EPS_REL, "gram")
+            forms[f"mixed@{MIXED_EPS_REL:g}"] = summarise(rm, H.HAPOD_MIXED_TF32X3, MIXED_EPS_REL, "gram")
             forms[f"mixed@{MIXED_EPS_REL:g}"]["launches_per_step"] = rm["launches_per_step"]
         except H.HapodError as e:
             forms[f"mixed@{MIXED_EPS_REL:g}"] = {"unavailable": str(e)}
@@ -558,6 +577,8 @@ def main():
         head_prec = H.HAPOD_FP64_OZAKI
         forms[f"fp64_ozaki@{EPS_REL:g}"] = summarise(head, H.HAPOD_FP64_OZAKI, EPS_REL)
     e2e = None
+
+    steps_e2e = args.steps
 
     def measure_e2e(prec, key):
         # right after the headline form, with the pool's cached blocks returned first
@@ -576,7 +597,7 @@ def main():
             c1.record(stream)
         torch.cuda.synchronize()
         idle_gbs = sum(h_.numel() * 8 for h_ in host) / (c0.elapsed_time(c1) / 1e3) / 1e9
-        r = run_e2e(H, prec, host, bufs, fro2, 1, stream)
+        r = run_e2e(H, prec, host, bufs, fro2, steps_e2e, stream)
         r["form"] = key
         r["max_pending_leaves"] = E2E_PENDING
         r["h2d_gbs_alone"] = idle_gbs

@@ -30,9 +30,14 @@
  *     each row's product x_i x_j represented to within 1.26 * 2^(E_i+E_j-53), with
  *     integer-exact accumulation, one FP64 rounding per entry and row split (Gram)
  *     or per 128-column block (X V), and FP64 sums over the splits / blocks.
- *     Mixed form (HAPOD_MIXED_BF16X3): snapshots are IEEE float; the Gram runs on
- *     the tensor cores as TF32 hi/lo products (x = hi + lo, hi*hi + hi*lo + lo*hi)
+ *     Mixed TF32 form (HAPOD_MIXED_TF32X3): snapshots are IEEE float; the Gram runs
+ *     on the tensor cores as TF32 hi/lo products (x = hi + lo, hi*hi + hi*lo + lo*hi)
  *     accumulated in FP32 over short row chunks and summed in FP64, X V in FP32.
+ *     Mixed split-BF16 form (HAPOD_MIXED_BF16X3): snapshots are IEEE float; every
+ *     value is split exactly into three bf16 pieces and the Gram and X V are formed
+ *     from the six piece products whose levels add to at most 2 (dropped terms below
+ *     2^-26 |x_i x_j|), FP32 tensor-core accumulation over 64-row segments summed in
+ *     compensated FP32 pairs and FP64; eigensolve with FP64 rotations.
  *     Eigensolve, tail sums and truncation use FP64 arithmetic on FP64 data except
  *     where stated.
  */
@@ -60,11 +65,16 @@ typedef enum {
 
 typedef enum {
   HAPOD_FP64 = 0,           /* double snapshots, FP64 arithmetic everywhere */
-  HAPOD_MIXED_BF16X3 = 1,   /* float snapshots, tensor-core (TF32 hi/lo split) Gram, FP32 X V */
-  HAPOD_FP64_OZAKI = 2      /* double snapshots and results; Gram and X V from exact 8-bit
+  HAPOD_MIXED_TF32X3 = 1,   /* float snapshots, tensor-core (TF32 hi/lo split) Gram, FP32 X V */
+  HAPOD_FP64_OZAKI = 2,     /* double snapshots and results; Gram and X V from exact 8-bit
                                digit products on the fp16 tensor cores (error-free splitting
                                of Ozaki et al. 2012, integer-exact accumulation, one final
                                FP64 rounding per entry); eigensolver in FP64 */
+  HAPOD_MIXED_BF16X3 = 3    /* float snapshots; Gram and X V on the tensor cores from the exact
+                               three-piece bf16 split x = b1 + b2 + b3 (six products per
+                               entry, FP32 accumulation over 64-row segments, compensated
+                               sums, FP64 over row splits); Jacobi eigensolve with FP64
+                               rotations, FP64 truncation, CholQR2 at the root */
 } hapod_precision;
 
 /*
@@ -291,7 +301,10 @@ hapod_status hapod_pod(int32_t precision, int64_t n, int64_t m, const void* X, i
  * message in hapod_last_error(NULL).  All calls share the array: calls whose
  * work overlaps on the GPU (unordered streams) race on it.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.
+ * device current and keeps it until the process exits; make that first call
+ * before any stream capture (a first call made inside a capture returns
+ * HAPOD_ERR_INVALID).  A cudaDeviceReset of that device invalidates the kept
+ * address: do not call this entry point again in that process afterwards.
  * Errors: INVALID, CUDA.
  */
 hapod_status hapod_gram_noalloc(int64_t n, int64_t m, const double* X, int64_t ldx, double* G, void* stream);

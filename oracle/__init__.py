@@ -19,5 +19,4 @@ from .core import (  # noqa: F401
     tolerances,
     hapod,
     projection_error,
-    orthonormal_basis,
 )

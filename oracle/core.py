@@ -91,6 +91,8 @@ def svd(X, want_vectors: bool = True):
     st = _load().oracle_svd(n, m, _ptr(X), max(n, 1), _ptr(sigma), _ptr(US), _ptr(V))
     if st == -2:
         raise MemoryError("oracle_svd: allocation failed")
+    if st == -1:
+        raise ArithmeticError("oracle_svd: one-sided Jacobi did not converge in 60 sweeps")
     return sigma, US, V, st
 
 
@@ -123,6 +125,8 @@ def pod(X, eps: float) -> PodResult:
                             ctypes.byref(tail))
     if st == -2:
         raise MemoryError("oracle_pod: allocation failed")
+    if st == -1:
+        raise ArithmeticError("oracle_pod: one-sided Jacobi did not converge in 60 sweeps")
     k = N.value
     return PodResult(k, sigma[:k].copy(), np.asfortranarray(Y[:, :k]), tail.value, st, eps == 0.0)
 
@@ -226,13 +230,6 @@ def hapod(parent: Sequence[int], leaf_data: Dict[int, np.ndarray], eps: Sequence
 
 
 # ------------------------------------------------------------------ error measures
-def orthonormal_basis(Y) -> np.ndarray:
-    """Orthonormal basis of span(Y) (left singular vectors with nonzero sigma)."""
-    sig, US, _, _ = svd(Y)
-    keep = sig > 0
-    return US[:, keep] / sig[keep]
-
-
 def projection_error(X, Q) -> float:
     """sum_s ||s - Q Q^T s||^2 with the residual formed explicitly (Thm. hapod_bound)."""
     X = np.asarray(X, dtype=np.float64)

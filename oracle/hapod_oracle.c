@@ -243,7 +243,9 @@ void oracle_tail_sums(int64_t r, const double* sigma, double* tail) {
  *   eps >  0 : N = min{N' : sum_{j >= N'} sigma_j^2 <= eps^2} (0-based j).
  * Outputs: *N_out; sigma_out (capacity min(n, m), or m when eps == 0);
  * Y_out (n x capacity, ld n): column j = sigma_j * phi_j; *tail_out =
- * sum of the discarded sigma^2.  Returns the SVD status (>= 0 on success).
+ * sum of the discarded sigma^2.  Returns the SVD's sweep count (>= 0) on
+ * success, -1 when the one-sided Jacobi did not converge (no output is then
+ * defined) and -2 when an allocation failed.
  */
 int oracle_pod(int64_t n, int64_t m, const double* X, int64_t ldx, double eps, int64_t* N_out,
                double* sigma_out, double* Y_out, double* tail_out) {
@@ -260,7 +262,7 @@ int oracle_pod(int64_t n, int64_t m, const double* X, int64_t ldx, double eps, i
   double* tail = (double*)malloc(sizeof(double) * (size_t)(r + 1));
   if (!tail) return -2;
   const int st = oracle_svd(n, m, X, ldx, sigma_out, Y_out, NULL);
-  if (st < 0 && st != -1) {
+  if (st < 0) {  /* an unconverged SVD is not a POD: the caller gets the failure */
     free(tail);
     return st;
   }

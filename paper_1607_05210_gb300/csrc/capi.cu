@@ -158,15 +158,37 @@ struct Env {
   }
 };
 
+// Debug only: HAPOD_DEBUG_WAIT_CYCLES=N (N > 0) shortens every bounded device-side
+// wait of the tensor-core kernels to N clock cycles, so that a test can make one run
+// out on a healthy kernel; unset, the budget is about one second.  The value is read at
+// every call and stored in err[1] of the kernels' error flag.
+int debug_wait_cycles() {
+  const char* e = getenv("HAPOD_DEBUG_WAIT_CYCLES");
+  if (!e || !*e) return 0;
+  const long long v = atoll(e);
+  return v > 0 ? (int)std::min<long long>(v, 1 << 30) : 0;
+}
+
+// err[0] = 0 and err[1] = 0 are set by the caller's memset; this stores the debug budget.
+bool init_err_flag(Env& env, int* err) {
+  static thread_local int budget = 0;  // staged by the copy before it returns (pageable source)
+  budget = debug_wait_cycles();
+  if (budget <= 0) return true;
+  return env.cuda(cudaMemcpyAsync(err + 1, &budget, sizeof(int), cudaMemcpyHostToDevice, env.s), "set wait budget");
+}
+
 bool init_env(Env& env, void* stream) {
   env.s = static_cast<cudaStream_t>(stream);
   if (!env.cuda(cudaGetDevice(&env.dev), "cudaGetDevice")) return false;
   return env.cuda(get_pool(env.dev, &env.pool), "memory pool");
 }
 
-bool valid_precision(int p) { return p == HAPOD_FP64 || p == HAPOD_MIXED_BF16X3 || p == HAPOD_FP64_OZAKI; }
-// FP64 snapshots (the FP64 and digit-slice forms) versus FP32 snapshots (mixed form)
-bool f64_data(int p) { return p != HAPOD_MIXED_BF16X3; }
+bool valid_precision(int p) {
+  return p == HAPOD_FP64 || p == HAPOD_MIXED_TF32X3 || p == HAPOD_FP64_OZAKI || p == HAPOD_MIXED_BF16X3;
+}
+// FP64 snapshots (the FP64 and digit-slice forms) versus FP32 snapshots (mixed forms)
+bool f64_data(int p) { return p == HAPOD_FP64 || p == HAPOD_FP64_OZAKI; }
+bool mixed_form(int p) { return p == HAPOD_MIXED_TF32X3 || p == HAPOD_MIXED_BF16X3; }
 size_t elem_size(int p) { return f64_data(p) ? sizeof(double) : sizeof(float); }
 
 // ------------------------------------------------------------- batched steps
@@ -564,6 +586,7 @@ bool step_gram(Env& env, int precision, std::vector<Work*>& ws) {
   if (ws.empty()) return true;
   if (precision == HAPOD_FP64_OZAKI) return step_gram_oz(env, ws);
   const bool fp64 = precision == HAPOD_FP64;
+  const bool bf3 = precision == HAPOD_MIXED_BF16X3;
   std::vector<GramJob> jobs(ws.size());
   for (size_t i = 0; i < ws.size(); ++i) {
     GramJob& J = jobs[i];
@@ -587,8 +610,8 @@ bool step_gram(Env& env, int precision, std::vector<Work*>& ws) {
   if (!fp64) {
     maps.resize(ws.size());
     for (size_t i = 0; i < ws.size(); ++i)
-      if (!encode_colmajor_f32(&maps[i], ws[i]->X, ws[i]->n, ws[i]->m, ws[i]->ldx, gram_tc_rows_per_stage(), 128,
-                               true))
+      if (!encode_colmajor_f32(&maps[i], ws[i]->X, ws[i]->n, ws[i]->m, ws[i]->ldx,
+                               bf3 ? gram_bf3_rows_per_stage() : gram_tc_rows_per_stage(), 128, true))
         return env.fail(HAPOD_ERR_CUDA, "cuTensorMapEncodeTiled failed for a Gram input");
   }
   GramJob* jobs_d = env.upload(jobs, "upload gram jobs");
@@ -608,6 +631,8 @@ bool step_gram(Env& env, int precision, std::vector<Work*>& ws) {
     cudaEvent_t t0 = env.tic();
     if (fp64)
       e = launch_gram_f64(jobs_d, items_d, plan.num_items, red_d, plan.num_reduce, partials, env.s);
+    else if (bf3)
+      e = launch_gram_bf3(jobs_d, maps_d, items_d, plan.num_items, red_d, plan.num_reduce, partials, errf, env.s);
     else
       e = launch_gram_tc(jobs_d, maps_d, items_d, plan.num_items, red_d, plan.num_reduce, partials, errf, env.s);
     env.toc(t0, 0, 1 + (plan.num_reduce > 0), bytes, flops);
@@ -621,8 +646,19 @@ bool step_gram(Env& env, int precision, std::vector<Work*>& ws) {
   return ok;
 }
 
+// Eigensolver variant of a form: FP64 rotations (FP64 forms), FP32 rotations (mixed
+// TF32 form), or FP32 sweeps followed by FP64 sweeps to the FP64 stopping rule
+// (mixed split-BF16 form).
+int eig_mode(int precision) {
+  return precision == HAPOD_MIXED_TF32X3 ? kEigF32 : precision == HAPOD_MIXED_BF16X3 ? kEigF32F64 : kEigF64;
+}
+// Relative level of a form's Gram error (the pivoted Cholesky does not factor below it).
+double gram_floor_rel(int precision) { return precision == HAPOD_MIXED_BF16X3 ? 1e-10 : 0.0; }
+// Eigenvectors are stored in FP64 except by the mixed TF32 form (FP32).
+bool eigvec_f64(int precision) { return precision != HAPOD_MIXED_TF32X3; }
+
 // K2 for every node (w->G -> lambda, perm, V); results land in res_d[i].
-bool step_eig(Env& env, bool fp64, std::vector<Work*>& ws, NodeResult* res_d) {
+bool step_eig(Env& env, int precision, std::vector<Work*>& ws, NodeResult* res_d) {
   if (ws.empty()) return true;
   std::vector<EigJob> jobs(ws.size());
   int max_m = 1;
@@ -639,13 +675,15 @@ bool step_eig(Env& env, bool fp64, std::vector<Work*>& ws, NodeResult* res_d) {
     J.perm = w->perm;
     J.result = res_d + i;
     J.eps2 = w->eps * w->eps;
+    J.floor_rel = gram_floor_rel(precision);
     J.m = (int32_t)w->m;
     max_m = std::max(max_m, (int)w->m);
   }
   EigJob* jobs_d = env.upload(jobs, "upload eig jobs");
   if (!jobs_d) return false;
   cudaEvent_t t0 = env.tic();
-  bool ok = env.cuda(launch_eig(fp64, jobs_d, (int)jobs.size(), max_m, kMaxSweeps, env.s), "eigensolver launch");
+  bool ok = env.cuda(launch_eig(eig_mode(precision), jobs_d, (int)jobs.size(), max_m, kMaxSweeps, env.s),
+                     "eigensolver launch");
   env.toc(t0, 1, 1, 0.0, 0.0);
   env.release(jobs_d);
   return ok;
@@ -674,7 +712,7 @@ bool step_truncate(Env& env, std::vector<Work*>& ws, NodeResult* res_d) {
 bool run_pod_front(Env& env, int precision, std::vector<Work*>& ws) {
   if (ws.empty()) return true;
   const bool fp64 = f64_data(precision);
-  if (!alloc_work(env, ws, fp64)) return false;
+  if (!alloc_work(env, ws, eigvec_f64(precision))) return false;
   if (!fp64) {
     // TMA reads need a 16-byte aligned base and pitch; copy the rare input that has neither
     for (Work* w : ws) {
@@ -693,9 +731,10 @@ bool run_pod_front(Env& env, int precision, std::vector<Work*>& ws) {
   NodeResult* res_d = (NodeResult*)env.alloc(sizeof(NodeResult) * ws.size() + sizeof(int) * 4, "alloc results");
   if (!res_d) return false;
   env.err_dev = reinterpret_cast<int*>(res_d + ws.size());
-  bool ok = env.cuda(cudaMemsetAsync(res_d, 0, sizeof(NodeResult) * ws.size() + sizeof(int) * 4, env.s), "memset");
+  bool ok = env.cuda(cudaMemsetAsync(res_d, 0, sizeof(NodeResult) * ws.size() + sizeof(int) * 4, env.s), "memset") &&
+            init_err_flag(env, env.err_dev);
   ok = ok && step_gram(env, precision, ws);
-  ok = ok && step_eig(env, fp64, ws, res_d);
+  ok = ok && step_eig(env, precision, ws, res_d);
   ok = ok && step_truncate(env, ws, res_d);
   std::vector<NodeResult> res(ws.size());
   int dev_err = 0;
@@ -748,7 +787,7 @@ bool run_pod_back(Env& env, int precision, std::vector<Work*>& ws) {
   }
   GatherJob* gd = env.upload(gj, "upload gather jobs");
   cudaEvent_t tg = env.tic();
-  bool ok = gd && env.cuda(launch_gather(fp64, gd, (int)gj.size(), env.s), "gather launch");
+  bool ok = gd && env.cuda(launch_gather(eigvec_f64(precision), gd, (int)gj.size(), env.s), "gather launch");
   env.toc(tg, 3, 1, 0.0, 0.0);
   env.release(gd);
   if (!ok) return false;
@@ -832,17 +871,17 @@ bool modes_pass_mixed(Env& env, const void* X, int64_t ldx, int64_t n, int m, co
 // CholQR2 of the root's sigma-scaled modes Y (mixed form): U (orthonormal columns,
 // written to `out`) and refreshed sigma (host).  Sec. 2 footnote of the
 // method-of-snapshots remark: the Gram route loses orthogonality as cond(X)^2.
-bool root_cholqr2(Env& env, const void* Y, int64_t n, int64_t ldn, int k, void* out, std::vector<double>& sigma,
-                  bool* rank_deficient) {
+bool root_cholqr2(Env& env, int precision, const void* Y, int64_t n, int64_t ldn, int k, void* out,
+                  std::vector<double>& sigma, bool* rank_deficient) {
   const size_t kk = (size_t)k * k;
   // layout (doubles): W | W2 | R1 | M1 | M | work (4 k^2) | sigma (k)
   double* W = (double*)env.alloc(sizeof(double) * (9 * kk + k), "alloc CholQR2 work");
   void* Q1 = env.alloc(sizeof(float) * ldn * k, "alloc CholQR2 Q1");
-  int* flag = (int*)env.alloc(sizeof(int) * 2, "alloc flag");
+  int* flag = (int*)env.alloc(sizeof(int) * 4, "alloc flag");
   if (!W || !Q1 || !flag) return false;
   double *W2 = W + kk, *R1 = W + 2 * kk, *M1 = W + 3 * kk, *M = W + 4 * kk, *work = W + 5 * kk;
   double* sig_d = W + 9 * kk;
-  bool ok = env.cuda(cudaMemsetAsync(flag, 0, sizeof(int) * 2, env.s), "memset");
+  bool ok = env.cuda(cudaMemsetAsync(flag, 0, sizeof(int) * 4, env.s), "memset") && init_err_flag(env, flag + 1);
   Work g;
   g.X = Y;
   g.ldx = ldn;
@@ -851,12 +890,12 @@ bool root_cholqr2(Env& env, const void* Y, int64_t n, int64_t ldn, int k, void* 
   g.G = W;
   std::vector<Work*> ws{&g};
   env.err_dev = flag + 1;
-  ok = ok && step_gram(env, HAPOD_MIXED_BF16X3, ws);
+  ok = ok && step_gram(env, precision, ws);
   ok = ok && env.cuda(launch_cholqr_first(W, R1, M1, k, flag, env.s), "cholqr launch");
   ok = ok && modes_pass_mixed(env, Y, ldn, n, k, M1, k, Q1, ldn);
   g.X = Q1;
   g.G = W2;
-  ok = ok && step_gram(env, HAPOD_MIXED_BF16X3, ws);
+  ok = ok && step_gram(env, precision, ws);
   ok = ok && env.cuda(launch_cholqr_second(W2, R1, work, M, sig_d, k, flag, env.s), "cholqr launch");
   ok = ok && modes_pass_mixed(env, Q1, ldn, n, k, M, k, out, ldn);
   int hflag[2] = {0, 0};
@@ -1048,7 +1087,7 @@ bool run_batch(hapod_ctx* c, const std::vector<int>& batch) {
     if (A.eps > 0.0 && A.m > 0) {
       w.Y = dst;
       w.ldy = c->ldn;
-      if (A.parent < 0 && c->precision == HAPOD_MIXED_BF16X3 && A.k <= 256) {
+      if (A.parent < 0 && mixed_form(c->precision) && A.k <= 256) {
         // mixed form: unscaled Y to a temporary; CholQR2 writes U into the result below
         root_tmp = env.alloc(pitch * A.k, "alloc root modes");
         if (!root_tmp) {
@@ -1065,7 +1104,9 @@ bool run_batch(hapod_ctx* c, const std::vector<int>& batch) {
         if (!w.scale) ok = false;
         scales.push_back(w.scale);
         // resolution floor of the method of snapshots (Sec. 2 footnote: cond(G) = cond(X)^2)
-        const double u = f64_data(c->precision) ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
+        const double u = f64_data(c->precision)                    ? 1.1102230246251565e-16
+                         : c->precision == HAPOD_MIXED_BF16X3 ? gram_floor_rel(c->precision)
+                                                              : 5.9604644775390625e-08;
         if (A.sigma[A.k - 1] < A.sigma[0] * std::sqrt((double)A.m * u)) {
           A.status = HAPOD_WARN_BELOW_FLOOR;
           if (c->warning == HAPOD_OK) c->warning = HAPOD_WARN_BELOW_FLOOR;
@@ -1083,7 +1124,7 @@ bool run_batch(hapod_ctx* c, const std::vector<int>& batch) {
   if (ok && root_work) {
     NodeRT& R = c->nodes[root_node];
     bool deficient = false;
-    ok = root_cholqr2(env, root_tmp, c->n, c->ldn, (int)R.k, c->result, R.sigma, &deficient);
+    ok = root_cholqr2(env, c->precision, root_tmp, c->n, c->ldn, (int)R.k, c->result, R.sigma, &deficient);
     if (ok && deficient) {
       R.status = HAPOD_WARN_BELOW_FLOOR;
       if (c->warning == HAPOD_OK) c->warning = HAPOD_WARN_BELOW_FLOOR;
@@ -1438,7 +1479,7 @@ hapod_status hapod_gram(int32_t precision, int64_t n, int64_t m, const void* X, 
   }
   // tensor-core forms: aligned input for TMA (mixed form), device error flag read back here
   bool ok = true;
-  if (precision == HAPOD_MIXED_BF16X3 && !tma_compatible_f32(X, ldx)) {
+  if (mixed_form(precision) && !tma_compatible_f32(X, ldx)) {
     const int64_t ld = (n + 31) / 32 * 32;
     w.X_tmp = env.alloc(sizeof(float) * ld * m, "alloc aligned input");
     ok = w.X_tmp && env.cuda(cudaMemcpy2DAsync(w.X_tmp, ld * sizeof(float), X, ldx * sizeof(float),
@@ -1447,9 +1488,9 @@ hapod_status hapod_gram(int32_t precision, int64_t n, int64_t m, const void* X, 
     w.X = w.X_tmp;
     w.ldx = ld;
   }
-  env.err_dev = ok ? (int*)env.alloc(sizeof(int), "alloc flag") : nullptr;
-  ok = ok && env.err_dev && env.cuda(cudaMemsetAsync(env.err_dev, 0, sizeof(int), env.s), "memset") &&
-       step_gram(env, precision, ws);
+  env.err_dev = ok ? (int*)env.alloc(sizeof(int) * 2, "alloc flag") : nullptr;
+  ok = ok && env.err_dev && env.cuda(cudaMemsetAsync(env.err_dev, 0, sizeof(int) * 2, env.s), "memset") &&
+       init_err_flag(env, env.err_dev) && step_gram(env, precision, ws);
   int dev_err = 0;
   if (ok) ok = env.cuda(cudaMemcpyAsync(&dev_err, env.err_dev, sizeof(int), cudaMemcpyDeviceToHost, env.s), "read flag");
   env.release(env.err_dev);
@@ -1478,18 +1519,18 @@ hapod_status hapod_eig(int32_t precision, int64_t m, const double* G, double* la
   if (m == 0) return HAPOD_OK;
   Env env;
   if (!init_env(env, stream)) return step_error(env);
-  const bool fp64 = f64_data(precision);
+  const bool vf64 = eigvec_f64(precision);
   Work w;
   w.m = m;
   std::vector<Work*> ws{&w};
-  if (!alloc_work(env, ws, fp64)) {
+  if (!alloc_work(env, ws, vf64)) {
     free_work(env, ws);
     return step_error(env);
   }
   NodeResult* res_d = (NodeResult*)env.alloc(sizeof(NodeResult), "alloc result");
   bool ok = res_d && env.cuda(cudaMemsetAsync(res_d, 0, sizeof(NodeResult), env.s), "memset") &&
             env.cuda(cudaMemcpyAsync(w.G, G, sizeof(double) * m * m, cudaMemcpyDeviceToDevice, env.s), "copy G") &&
-            step_eig(env, fp64, ws, res_d);
+            step_eig(env, precision, ws, res_d);
   if (ok) {
     GatherJob g;
     g.V = w.V;
@@ -1499,7 +1540,7 @@ hapod_status hapod_eig(int32_t precision, int64_t m, const double* G, double* la
     g.k = (int32_t)m;
     std::vector<GatherJob> gj{g};
     GatherJob* gd = env.upload(gj, "upload gather");
-    ok = gd && env.cuda(launch_gather(fp64, gd, 1, env.s), "gather launch") &&
+    ok = gd && env.cuda(launch_gather(vf64, gd, 1, env.s), "gather launch") &&
          env.cuda(cudaMemcpyAsync(lambda, w.lambda, sizeof(double) * m, cudaMemcpyDeviceToDevice, env.s), "copy");
     env.release(gd);
   }
@@ -1571,9 +1612,9 @@ hapod_status hapod_modes(int32_t precision, int64_t n, int64_t m, const void* X,
     w.ldy = ldy;
     w.res.k = (int32_t)N;
     std::vector<Work*> ws{&w};
-    env.err_dev = (int*)env.alloc(sizeof(int), "alloc flag");
-    bool ok = env.err_dev && env.cuda(cudaMemsetAsync(env.err_dev, 0, sizeof(int), env.s), "memset") &&
-              step_modes_oz(env, ws);
+    env.err_dev = (int*)env.alloc(sizeof(int) * 2, "alloc flag");
+    bool ok = env.err_dev && env.cuda(cudaMemsetAsync(env.err_dev, 0, sizeof(int) * 2, env.s), "memset") &&
+              init_err_flag(env, env.err_dev) && step_modes_oz(env, ws);
     int dev_err = 0;
     if (ok)
       ok = env.cuda(cudaMemcpyAsync(&dev_err, env.err_dev, sizeof(int), cudaMemcpyDeviceToHost, env.s), "read flag");

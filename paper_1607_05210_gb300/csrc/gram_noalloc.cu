@@ -16,8 +16,12 @@
 // each partial tile is written in full before it is read, so nothing has to start
 // at zero, but two calls whose kernels overlap on the GPU (different streams
 // without ordering) race on it.  The first call on a device looks up the scratch
-// address with cudaGetSymbolAddress (once per device, with that device current);
-// make that first call before any stream capture.
+// address with cudaGetSymbolAddress (once per device, with that device current)
+// and keeps it for the life of the process; make that first call before any stream
+// capture (a first call inside a capture is rejected with HAPOD_ERR_INVALID).  The
+// kept address belongs to the device context that existed at that call: after
+// cudaDeviceReset on that device this entry point must not be called again in the
+// same process.
 #include <algorithm>
 #include <mutex>
 #include <string>
@@ -151,13 +155,28 @@ hapod_status hapod_gram_noalloc(int64_t n, int64_t m, const double* X, int64_t l
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= 64) {
+  if (e != cudaSuccess) {
+    cudaGetLastError();
     return fail(HAPOD_ERR_CUDA, std::string("hapod_gram_noalloc: cudaGetDevice: ") + cudaGetErrorString(e));
+  }
+  if (dev < 0 || dev >= 64) {
+    return fail(HAPOD_ERR_INVALID, "hapod_gram_noalloc: device ordinals of 64 and above are not supported");
   }
   double* scratch;
   {
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_scratch_ptr[dev]) {
+      // The address lookup may load the library's device image; inside a stream
+      // capture that would break the caller's capture, so the set-up call has to
+      // come first, outside any capture.
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      e = cudaStreamIsCapturing(s, &cs);
+      if (e != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return fail(HAPOD_ERR_INVALID,
+                    "hapod_gram_noalloc: the first call on a device must be made outside stream capture "
+                    "(it looks up the fixed scratch array's device address)");
+      }
       void* p = nullptr;
       e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
       if (e != cudaSuccess || !p) {

@@ -110,6 +110,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_oz_kernel(const OzGramJob* _
   const int nst = max(0, min(total_stages - st0, J.stages_per_split));
   const int nkb = (nst + kBlockStages - 1) / kBlockStages;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const tc::WaitBudget wb = tc::wait_budget(err);
   auto stage_a = [&](int s) -> uint8_t* { return smem + (size_t)s * kStageBytes; };
   auto stage_b = [&](int s) -> uint8_t* { return smem + (size_t)s * kStageBytes + kStageA; };
 
@@ -142,7 +143,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_oz_kernel(const OzGramJob* _
       int issued = 0;
       for (int k = 0; k < nst; ++k) {
         const int s = k % kStages;
-        if (k >= kStages && !tc::mbar_wait(&bars.empty[s], ((k / kStages) - 1) & 1, &abort_flag, err)) break;
+        if (k >= kStages && !tc::mbar_wait(&bars.empty[s], ((k / kStages) - 1) & 1, &abort_flag, err, wb)) break;
         tc::mbar_expect_tx(&bars.full[s], kStageBytes);
         const int rg0 = 2 * (st0 + k);
         tc::tma_load_3d(stage_a(s), mapA, 16 * kAGroups * TI, 0, rg0, &bars.full[s]);
@@ -165,9 +166,9 @@ __global__ void __launch_bounds__(kThreads, 1) gram_oz_kernel(const OzGramJob* _
         const int pos = k % kBlockStages;
         const int kb = k / kBlockStages;
         const int set = kb & 1;
-        if (pos == 0 && kb >= 2 && !tc::mbar_wait(&bars.acc_empty[set], ((kb >> 1) - 1) & 1, &abort_flag, err))
+        if (pos == 0 && kb >= 2 && !tc::mbar_wait(&bars.acc_empty[set], ((kb >> 1) - 1) & 1, &abort_flag, err, wb))
           break;
-        if (!tc::mbar_wait(&bars.full[s], (k / kStages) & 1, &abort_flag, err)) break;
+        if (!tc::mbar_wait(&bars.full[s], (k / kStages) & 1, &abort_flag, err, wb)) break;
         tc::tc_fence_after();
         const uint32_t a0 = tc::smem_u32(stage_a(s)), b0 = tc::smem_u32(stage_b(s));
         const uint32_t acc = tbase + (uint32_t)set * kSetCols;
@@ -200,7 +201,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_oz_kernel(const OzGramJob* _
     bool ok = true;
     for (int kb = 0; kb < nkb; ++kb) {
       const int set = kb & 1;
-      if (!tc::mbar_wait_warp(&bars.acc_full[set], (kb >> 1) & 1, &abort_flag, err)) {
+      if (!tc::mbar_wait_warp(&bars.acc_full[set], (kb >> 1) & 1, &abort_flag, err, wb)) {
         ok = false;
         break;
       }

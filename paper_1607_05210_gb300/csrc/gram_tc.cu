@@ -79,9 +79,9 @@ __device__ __forceinline__ void make_lo(const float* __restrict__ hi, float* __r
 // pair (s, c) in TMEM for this warp's 32 lanes and columns 64 h .. 64 h + 63, then
 // hand the accumulator back to the issuer.  Segment 0 initialises s and c.
 __device__ __forceinline__ bool flush_segment(int j, uint32_t tbase, int q, int h, int lane, Bars& bars,
-                                              volatile int* abort_flag, int* err) {
+                                              volatile int* abort_flag, int* err, tc::WaitBudget wb) {
   const int b = j & 1;
-  if (!tc::mbar_wait_warp(&bars.acc_full[b], (j >> 1) & 1, abort_flag, err)) return false;
+  if (!tc::mbar_wait_warp(&bars.acc_full[b], (j >> 1) & 1, abort_flag, err, wb)) return false;
   tc::tc_fence_after();
   const uint32_t lanes = (uint32_t)(32 * q) << 16;
 #pragma unroll 1
@@ -133,6 +133,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int nst = r1 > r0 ? (int)((r1 - r0 + kRowsPerStage - 1) / kRowsPerStage) : 0;
   const int nseg = (nst + kSegStages - 1) / kSegStages;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const tc::WaitBudget wb = tc::wait_budget(err);
   // hi ring slot s: [A hi | B hi]; lo ring slot t (after the hi ring): [A lo | B lo]; 16 KB each
   auto hi_blk = [&](int s, int panel) -> uint8_t* { return smem + (size_t)s * kPairBytes + (size_t)panel * kBlockBytes; };
   auto lo_blk = [&](int t, int panel) -> uint8_t* {
@@ -168,7 +169,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       int issued = 0;
       for (int k = 0; k < nst; ++k) {
         const int s = k % kStages;
-        if (k >= kStages && !tc::mbar_wait(&bars.empty[s], ((k / kStages) - 1) & 1, &abort_flag, err)) break;
+        if (k >= kStages && !tc::mbar_wait(&bars.empty[s], ((k / kStages) - 1) & 1, &abort_flag, err, wb)) break;
         tc::mbar_expect_tx(&bars.full[s], bytes);
         const int row = (int)(r0 + (int64_t)k * kRowsPerStage);
         tc::tma_load_2d(hi_blk(s, 0), map, row, ti * kPanelCols, &bars.full[s]);
@@ -195,9 +196,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         const bool seg_last = (k % kSegStages) == kSegStages - 1 || k == nst - 1;
         const int b = seg & 1;
         if (seg_first && seg >= 2 &&
-            !tc::mbar_wait(&bars.acc_empty[b], ((seg >> 1) - 1) & 1, &abort_flag, err))
+            !tc::mbar_wait(&bars.acc_empty[b], ((seg >> 1) - 1) & 1, &abort_flag, err, wb))
           break;
-        if (!tc::mbar_wait(&bars.cvt[s], (k / kStages) & 1, &abort_flag, err)) break;
+        if (!tc::mbar_wait(&bars.cvt[s], (k / kStages) & 1, &abort_flag, err, wb)) break;
         tc::tc_fence_after();
         const int t = k % kLoStages;
         const uint32_t ah = tc::smem_u32(hi_blk(s, 0)), al = tc::smem_u32(lo_blk(t, 0));
@@ -226,8 +227,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int ct = tid - 64;
     for (int k = 0; k < nst; ++k) {
       const int s = k % kStages, t = k % kLoStages;
-      if (!tc::mbar_wait_warp(&bars.full[s], (k / kStages) & 1, &abort_flag, err)) break;
-      if (k >= kLoStages && !tc::mbar_wait_warp(&bars.lo_free[t], ((k / kLoStages) - 1) & 1, &abort_flag, err)) break;
+      if (!tc::mbar_wait_warp(&bars.full[s], (k / kStages) & 1, &abort_flag, err, wb)) break;
+      if (k >= kLoStages && !tc::mbar_wait_warp(&bars.lo_free[t], ((k / kLoStages) - 1) & 1, &abort_flag, err, wb)) break;
       make_lo(reinterpret_cast<const float*>(hi_blk(s, 0)), reinterpret_cast<float*>(lo_blk(t, 0)), ct);
       if (!diag) make_lo(reinterpret_cast<const float*>(hi_blk(s, 1)), reinterpret_cast<float*>(lo_blk(t, 1)), ct);
       tc::fence_async_smem();
@@ -239,7 +240,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int q = warp & 3;                       // TMEM lane quarter this warp may access
     const int h = (warp - kFirstFlushWarp) >> 2;  // column half of the tile
     bool ok = true;
-    for (int j = 0; j < nseg && ok; ++j) ok = flush_segment(j, tbase, q, h, lane, bars, &abort_flag, err);
+    for (int j = 0; j < nseg && ok; ++j) ok = flush_segment(j, tbase, q, h, lane, bars, &abort_flag, err, wb);
     if (__all_sync(0xffffffffu, ok && !abort_flag)) {
       const int a = 32 * q + lane;  // tile row
       const int gi = ti * kPanelCols + a;

@@ -70,6 +70,13 @@ cudaError_t launch_gram_f64(const GramJob* jobs_dev, const int4* items_dev, int 
 cudaError_t launch_gram_tc(const GramJob* jobs_dev, const CUtensorMap* maps_dev, const int4* items_dev, int num_items,
                            const int4* reduce_dev, int num_reduce, double* partials, int* err_flag, cudaStream_t s);
 int gram_tc_rows_per_stage();
+// Mixed split-BF16 form (tcgen05 kind::f16 with bf16 pieces): maps as for gram_tc with a
+// box of gram_bf3_rows_per_stage() rows x 128 columns, 128-byte swizzle; items/reduce as
+// for gram_tc.  err_flag: err[0] timeout flag, err[1] debug wait budget (0 = default).
+cudaError_t launch_gram_bf3(const GramJob* jobs_dev, const CUtensorMap* maps_dev, const int4* items_dev,
+                            int num_items, const int4* reduce_dev, int num_reduce, double* partials, int* err_flag,
+                            cudaStream_t s);
+int gram_bf3_rows_per_stage();
 // TMA needs a 16-byte aligned base and a row pitch that is a multiple of 16 bytes.
 bool tma_compatible_f32(const void* base, int64_t ld);
 bool tma_compatible_f64(const void* base, int64_t ld);
@@ -216,11 +223,17 @@ struct EigJob {
   int32_t* perm;       // m, sorted position -> column of V
   NodeResult* result;
   double eps2;         // the node's eps^2 (caps the factorisation's stopping residual)
+  double floor_rel;    // relative level of the Gram's error: the factorisation stops there at the latest
   int32_t m;
   int32_t pad;
 };
+// Rotation precision: FP64 throughout; FP32 (V in FP32); FP32 sweeps to the FP32 stopping
+// rule followed by FP64 sweeps to the FP64 one (V in FP64).
+constexpr int kEigF64 = 0;
+constexpr int kEigF32 = 1;
+constexpr int kEigF32F64 = 2;
 // One CTA per job; max_m sizes the dynamic shared memory (eig_smem_bytes).
-cudaError_t launch_eig(bool fp64, const EigJob* jobs_dev, int njobs, int max_m, int max_sweeps, cudaStream_t s);
+cudaError_t launch_eig(int mode, const EigJob* jobs_dev, int njobs, int max_m, int max_sweeps, cudaStream_t s);
 int eig_threads();
 size_t eig_smem_bytes(int m);
 constexpr int kEigMaxM = 13000;  // dynamic shared memory bound of the eigensolver

@@ -21,6 +21,8 @@
 // eigensolve costs O(m r^2) per sweep instead of the O(m^3) of a Jacobi sweep on G.
 // Output: lambda descending (clamped >= 0, zero beyond r), V (T, m x m) with
 // column j = w_j / ||w_j|| for j < r and zero otherwise, perm = sorted order.
+#include <type_traits>
+
 #include "hapod_internal.cuh"
 
 namespace hapod {
@@ -116,8 +118,69 @@ __device__ void argmax_block(const double* d, const unsigned char* chosen, int m
   __syncthreads();
 }
 
-template <typename T>
+// One-sided Jacobi sweeps on the r columns (length m) of W in precision U until no
+// pair needs a rotation (|w_p . w_q| <= m u ||w_p|| ||w_q||, u the unit roundoff of U)
+// or max_sweeps sweeps were made.  Block-wide; returns the sweeps made.
+template <typename U>
+__device__ int jacobi_sweeps(U* W, int m, int r, int max_sweeps, bool& converged, int* flag_sh) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int rp = r + (r & 1), npairs = rp / 2;
+  const U rtol = (U)m * Unit<U>::eps();
+  int sweeps = 0;
+  converged = (r <= 1);
+  while (!converged && sweeps < max_sweeps) {
+    ++sweeps;
+    if (tid == 0) *flag_sh = 0;
+    __syncthreads();
+    int rotated = 0;
+    for (int t = 0; t < rp - 1; ++t) {
+      for (int k = warp; k < npairs; k += kWarps) {
+        int p, q;
+        rr_pair(t, k, rp, p, q);
+        if (p >= r || q >= r) continue;
+        U* wp = W + (size_t)p * m;
+        U* wq = W + (size_t)q * m;
+        U al = 0, be = 0, ga = 0;
+        for (int i = lane; i < m; i += 32) {
+          const U x = wp[i], y = wq[i];
+          al = fma(x, x, al);
+          be = fma(y, y, be);
+          ga = fma(x, y, ga);
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        if (ga == U(0) || !(fabs(ga) > rtol * sqrt(al * be))) continue;
+        rotated = 1;
+        const U zeta = (be - al) / (U(2) * ga);
+        // smaller root of t^2 + 2 zeta t - 1 = 0; 1/(2 zeta) once zeta^2 would overflow
+        const U tt = fabs(zeta) > U(1e15) ? U(0.5) / zeta
+                                           : (zeta >= U(0) ? U(1) : U(-1)) / (fabs(zeta) + sqrt(U(1) + zeta * zeta));
+        const U c = U(1) / sqrt(U(1) + tt * tt);
+        const U s = c * tt;
+        for (int i = lane; i < m; i += 32) {
+          const U x = wp[i], y = wq[i];
+          wp[i] = c * x - s * y;
+          wq[i] = s * x + c * y;
+        }
+      }
+      __syncthreads();
+    }
+    if (rotated && lane == 0) *flag_sh = 1;
+    __syncthreads();
+    converged = (*flag_sh == 0);
+    __syncthreads();
+  }
+  return sweeps;
+}
+
+// T: precision of the first rotation phase.  POLISH: after it, the columns are
+// carried to FP64 (into the factor's buffer, no longer needed) and rotated in FP64
+// until the FP64 stopping rule holds; the eigenvectors are then FP64 (J.V holds
+// doubles).  Without POLISH the eigenvectors stay in T.
+template <typename T, bool POLISH>
 __global__ void __launch_bounds__(kThreads) chol_jacobi_kernel(const EigJob* __restrict__ jobs, int max_sweeps) {
+  typedef typename std::conditional<POLISH, double, T>::type V_t;  // element type of the eigenvectors
   const EigJob J = jobs[blockIdx.x];
   const int m = J.m;
   if (m <= 0) return;
@@ -150,9 +213,12 @@ __global__ void __launch_bounds__(kThreads) chol_jacobi_kernel(const EigJob* __r
   const bool finite = flag_sh == 0 && isfinite(trace) && isfinite(dmax0);
   __syncthreads();
   if (!finite && tid == 0) res->status = HAPOD_ERR_NONFINITE;
-  const double tol = (sizeof(T) == sizeof(double)) ? (double)m * 1.1102230246251565e-16 : 1e-7;
-  const double stop_round = tol * (trace > 0.0 ? trace : 0.0);
-  const double stop = J.eps2 > 0.0 ? fmin(stop_round, 1e-2 * J.eps2) : stop_round;
+  const double tol = (sizeof(V_t) == sizeof(double)) ? (double)m * 1.1102230246251565e-16 : 1e-7;
+  const double tr_pos = trace > 0.0 ? trace : 0.0;
+  const double stop_round = tol * tr_pos;
+  double stop = J.eps2 > 0.0 ? fmin(stop_round, 1e-2 * J.eps2) : stop_round;
+  // below the Gram's own error level the remaining pivots would factor rounding noise
+  if (J.floor_rel > 0.0) stop = fmax(stop, J.floor_rel * tr_pos);
   int r = 0;
   double resid = finite && trace > 0.0 ? trace : 0.0;
   if (finite && trace > 0.0) {
@@ -191,56 +257,25 @@ __global__ void __launch_bounds__(kThreads) chol_jacobi_kernel(const EigJob* __r
     }
   }
 
-  // ---------------- one-sided Jacobi on the r columns (precision T)
-  for (size_t e = tid; e < (size_t)m * m; e += blockDim.x) W[e] = e < (size_t)r * m ? (T)L[e] : T(0);
+  // ---------------- one-sided Jacobi on the r columns (precision T, then FP64 if POLISH)
+  for (size_t e = tid; e < (size_t)r * m; e += blockDim.x) W[e] = (T)L[e];
   __syncthreads();
-  const int rp = r + (r & 1), npairs = rp / 2;
-  const T rtol = (T)m * Unit<T>::eps();
-  int sweeps = 0;
-  bool converged = (r <= 1);
-  while (!converged && sweeps < max_sweeps) {
-    ++sweeps;
-    if (tid == 0) flag_sh = 0;
+  bool converged = false;
+  int sweeps = jacobi_sweeps<T>(W, m, r, max_sweeps, converged, &flag_sh);
+  V_t* U = reinterpret_cast<V_t*>(J.V);
+  if (POLISH) {
+    // the FP32 columns move to FP64 in the factor's buffer, are rotated there to the
+    // FP64 stopping rule, and land in J.V (FP64)
+    for (size_t e = tid; e < (size_t)r * m; e += blockDim.x) L[e] = (double)W[e];
     __syncthreads();
-    int rotated = 0;
-    for (int t = 0; t < rp - 1; ++t) {
-      for (int k = warp; k < npairs; k += kWarps) {
-        int p, q;
-        rr_pair(t, k, rp, p, q);
-        if (p >= r || q >= r) continue;
-        T* wp = W + (size_t)p * m;
-        T* wq = W + (size_t)q * m;
-        T al = 0, be = 0, ga = 0;
-        for (int i = lane; i < m; i += 32) {
-          const T x = wp[i], y = wq[i];
-          al = fma(x, x, al);
-          be = fma(y, y, be);
-          ga = fma(x, y, ga);
-        }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        ga = warp_sum(ga);
-        if (ga == T(0) || !(fabs(ga) > rtol * sqrt(al * be))) continue;
-        rotated = 1;
-        const T zeta = (be - al) / (T(2) * ga);
-        // smaller root of t^2 + 2 zeta t - 1 = 0; 1/(2 zeta) once zeta^2 would overflow
-        const T tt = fabs(zeta) > T(1e15) ? T(0.5) / zeta
-                                           : (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-        const T c = T(1) / sqrt(T(1) + tt * tt);
-        const T s = c * tt;
-        for (int i = lane; i < m; i += 32) {
-          const T x = wp[i], y = wq[i];
-          wp[i] = c * x - s * y;
-          wq[i] = s * x + c * y;
-        }
-      }
-      __syncthreads();
-    }
-    if (rotated && lane == 0) flag_sh = 1;
-    __syncthreads();
-    converged = (flag_sh == 0);
-    __syncthreads();
+    bool conv64 = false;
+    sweeps += jacobi_sweeps<double>(L, m, r, max_sweeps, conv64, &flag_sh);
+    converged = conv64;
+    for (size_t e = tid; e < (size_t)m * m; e += blockDim.x) U[e] = (V_t)(e < (size_t)r * m ? L[e] : 0.0);
+  } else {
+    for (size_t e = (size_t)r * m + tid; e < (size_t)m * m; e += blockDim.x) U[e] = V_t(0);
   }
+  __syncthreads();
 
   // ---------------- normalised eigenvectors u_j = w_j / ||w_j||, then FP64 Rayleigh
   // quotients lambda_j = u_j^T G u_j against the original G (second order in the
@@ -248,21 +283,21 @@ __global__ void __launch_bounds__(kThreads) chol_jacobi_kernel(const EigJob* __r
   for (int j = warp; j < m; j += kWarps) {
     double s = 0.0;
     if (j < r) {
-      const T* wj = W + (size_t)j * m;
+      const V_t* wj = U + (size_t)j * m;
       for (int i = lane; i < m; i += 32) s += (double)wj[i] * (double)wj[i];
       s = warp_sum(s);
     }
     if (j < r && s > 0.0) {
       const double inv = 1.0 / sqrt(s);
-      T* wj = W + (size_t)j * m;
-      for (int i = lane; i < m; i += 32) wj[i] = (T)((double)wj[i] * inv);
+      V_t* wj = U + (size_t)j * m;
+      for (int i = lane; i < m; i += 32) wj[i] = (V_t)((double)wj[i] * inv);
     }
   }
   __syncthreads();
   for (int j = warp; j < m; j += kWarps) {
     double acc = 0.0;
     if (j < r) {
-      const T* uj = W + (size_t)j * m;
+      const V_t* uj = U + (size_t)j * m;
       for (int i = lane; i < m; i += 32) {
         double gi = 0.0;  // (G u_j)_i; G symmetric, column-major
         for (int l = 0; l < m; ++l) gi = fma(G[(size_t)l * m + i], (double)uj[l], gi);
@@ -298,10 +333,12 @@ int eig_threads() { return kThreads; }
 
 size_t eig_smem_bytes(int m) { return (size_t)m * (2 * sizeof(double) + 1) + 16; }
 
-cudaError_t launch_eig(bool fp64, const EigJob* jobs_dev, int njobs, int max_m, int max_sweeps, cudaStream_t s) {
+cudaError_t launch_eig(int mode, const EigJob* jobs_dev, int njobs, int max_m, int max_sweeps, cudaStream_t s) {
   if (njobs <= 0) return cudaSuccess;
   const size_t smem = eig_smem_bytes(max_m);
-  const void* fn = fp64 ? (const void*)chol_jacobi_kernel<double> : (const void*)chol_jacobi_kernel<float>;
+  const void* fn = mode == kEigF64   ? (const void*)chol_jacobi_kernel<double, false>
+                   : mode == kEigF32 ? (const void*)chol_jacobi_kernel<float, false>
+                                     : (const void*)chol_jacobi_kernel<float, true>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

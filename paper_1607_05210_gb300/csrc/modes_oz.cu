@@ -83,6 +83,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const tc::WaitBudget wb = tc::wait_budget(err);
   auto stage_a = [&](int s) -> uint8_t* { return smem + (size_t)s * kStageBytes; };
   auto stage_b = [&](int s) -> uint8_t* { return smem + (size_t)s * kStageBytes + kStageA; };
 
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         bool ok = true;
         for (int k = 0; k < nst; ++k) {
           const int x = (int)(gx % kXSlots);
-          if (gx >= kXSlots && !tc::mbar_wait(&bars.xempty[x], ((gx / kXSlots) - 1) & 1, &abort_flag, err)) {
+          if (gx >= kXSlots && !tc::mbar_wait(&bars.xempty[x], ((gx / kXSlots) - 1) & 1, &abort_flag, err, wb)) {
             ok = false;
             break;
           }
@@ -140,7 +141,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc::tma_load_2d(xs + (size_t)x * (kXSlotBytes / 8), maps + jb, row0, 16 * k, &bars.xfull[x]);
           ++gx;
           const int s = (int)(gv % kStages);
-          if (gv >= kStages && !tc::mbar_wait(&bars.empty[s], ((gv / kStages) - 1) & 1, &abort_flag, err)) {
+          if (gv >= kStages && !tc::mbar_wait(&bars.empty[s], ((gv / kStages) - 1) & 1, &abort_flag, err, wb)) {
             ok = false;
             break;
           }
@@ -187,12 +188,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             acc = tbase + (uint32_t)b * kAccCols;
           }
           if (pos == 0 && uses[b] > 0 &&
-              !tc::mbar_wait(&bars.acc_empty[b], (uses[b] - 1) & 1, &abort_flag, err)) {
+              !tc::mbar_wait(&bars.acc_empty[b], (uses[b] - 1) & 1, &abort_flag, err, wb)) {
             ok = false;
             break;
           }
-          if (!tc::mbar_wait(&bars.vfull[s], (gk / kStages) & 1, &abort_flag, err) ||
-              !tc::mbar_wait(&bars.full[s], (gk / kStages) & 1, &abort_flag, err)) {
+          if (!tc::mbar_wait(&bars.vfull[s], (gk / kStages) & 1, &abort_flag, err, wb) ||
+              !tc::mbar_wait(&bars.full[s], (gk / kStages) & 1, &abort_flag, err, wb)) {
             ok = false;
             break;
           }
@@ -252,7 +253,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           En[0] = exps_of(k + 1, 0);
           En[1] = exps_of(k + 1, 1);
         }
-        if (!tc::mbar_wait_warp(&bars.xfull[x], (gk / kXSlots) & 1, &abort_flag, err)) {
+        if (!tc::mbar_wait_warp(&bars.xfull[x], (gk / kXSlots) & 1, &abort_flag, err, wb)) {
           ok = false;
           break;
         }
@@ -284,7 +285,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
         }
-        if (gk >= kStages && !tc::mbar_wait_warp(&bars.empty[s], ((gk / kStages) - 1) & 1, &abort_flag, err)) {
+        if (gk >= kStages && !tc::mbar_wait_warp(&bars.empty[s], ((gk / kStages) - 1) & 1, &abort_flag, err, wb)) {
           ok = false;
           break;
         }
@@ -323,7 +324,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int kb = 0; kb < nkb; ++kb, ++kbg) {
         const int b = kbg & 1;
         const uint32_t acc = tbase + lanes + (uint32_t)b * kAccCols;
-        if (!tc::mbar_wait_warp(&bars.acc_full[b], uses[b] & 1, &abort_flag, err)) {
+        if (!tc::mbar_wait_warp(&bars.acc_full[b], uses[b] & 1, &abort_flag, err, wb)) {
           ok = false;
           break;
         }

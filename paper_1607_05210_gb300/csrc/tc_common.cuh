@@ -27,26 +27,41 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 // One potentially blocking test of the phase: the thread is suspended until the
-// phase completes or about 1 ms passes (suspend-time hint), so waiting threads do
-// not take issue slots from the working warps.
-__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+// phase completes or about `hint_ns` nanoseconds pass (suspend-time hint), so
+// waiting threads do not take issue slots from the working warps.
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity, uint32_t hint_ns = 1000000u) {
   uint32_t ok;
   asm volatile(
       "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity), "r"(1000000u)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
       : "memory");
   return ok != 0;
 }
+
+// Wait budget of a kernel: kWaitBudget cycles, or the shorter debug budget the host
+// stored in err[1] (0 = none).  A debug budget also drops the suspend hint, so that
+// the budget counts from the first poll.
+struct WaitBudget {
+  long long cycles;
+  uint32_t hint_ns;
+};
+__device__ __forceinline__ WaitBudget wait_budget(const int* err) {
+  const int dbg = err ? err[1] : 0;
+  if (dbg > 0) return WaitBudget{(long long)dbg, 0u};
+  return WaitBudget{kWaitBudget, 1000000u};
+}
+
 // Bounded wait: false if the budget ran out or `abort` was raised by another warp;
 // on a timeout it raises `abort` and the global error flag.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort, int* err) {
-  if (mbar_try(bar, parity)) return true;
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort, int* err,
+                                          WaitBudget wb = WaitBudget{kWaitBudget, 1000000u}) {
+  if (mbar_try(bar, parity, wb.hint_ns)) return true;
   const long long t0 = clock64();
   while (true) {
-    if (mbar_try(bar, parity)) return true;
+    if (mbar_try(bar, parity, wb.hint_ns)) return true;
     if (*abort) return false;
-    if (clock64() - t0 > kWaitBudget) {
+    if (clock64() - t0 > wb.cycles) {
       *abort = 1;
       if (err) atomicExch(err, 1);
       return false;
@@ -56,9 +71,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
 
 // Warp-uniform bounded wait: lane 0 polls, the outcome is broadcast and __syncwarp
 // orders the other lanes' later accesses after the observed phase.
-__device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity, volatile int* abort, int* err) {
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity, volatile int* abort, int* err,
+                                               WaitBudget wb = WaitBudget{kWaitBudget, 1000000u}) {
   int ok = 0;
-  if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort, err) ? 1 : 0;
+  if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort, err, wb) ? 1 : 0;
   ok = __shfl_sync(0xffffffffu, ok, 0);
   __syncwarp();
   return ok != 0;
@@ -116,6 +132,11 @@ __device__ __forceinline__ uint64_t ns_desc(uint32_t saddr, uint32_t lbo, uint32
 // given (0 = K-major, 1 = MN-major), M x N.
 __host__ __device__ constexpr uint32_t idesc_f16_f32_major(uint32_t M, uint32_t N, uint32_t a_mn, uint32_t b_mn) {
   return (1u << 4) | (a_mn << 15) | (b_mn << 16) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+// Instruction descriptor: bf16 x bf16 -> FP32 (kind::f16, A and B bf16), major-ness as above.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32_major(uint32_t M, uint32_t N, uint32_t a_mn, uint32_t b_mn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (a_mn << 15) | (b_mn << 16) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }
 
 // Untiled bulk copy global -> shared (16-byte aligned addresses, size a multiple of

@@ -37,9 +37,11 @@ STATUS_NAMES = {0: "OK", 1: "ERR_INVALID", 2: "ERR_TREE", 3: "ERR_STATE", 4: "ER
                 6: "ERR_NONFINITE", 7: "ERR_TIMEOUT", 8: "WARN_NOCONVERGE", 9: "WARN_BELOW_FLOOR"}
 
 HAPOD_FP64 = 0
-HAPOD_MIXED_BF16X3 = 1
+HAPOD_MIXED_TF32X3 = 1
 HAPOD_FP64_OZAKI = 2
-DTYPE = {HAPOD_FP64: torch.float64, HAPOD_MIXED_BF16X3: torch.float32, HAPOD_FP64_OZAKI: torch.float64}
+HAPOD_MIXED_BF16X3 = 3
+DTYPE = {HAPOD_FP64: torch.float64, HAPOD_MIXED_TF32X3: torch.float32, HAPOD_FP64_OZAKI: torch.float64,
+         HAPOD_MIXED_BF16X3: torch.float32}
 
 
 class hapod_tree(ctypes.Structure):

@@ -12,6 +12,9 @@ stand in for the paper's PDE snapshot data (Sec. 4), which is not available:
   on the periodic grid x_i = 2 pi i / n, a_k ~ N(0, k^-2), t_j ~ U[0, 1], nu = 1e-3,
   c = 1.  Expanded as X = B C with B = [sin(k x), cos(k x)] (n x 64) so that large
   matrices are produced by one matrix product on the device.
+* ``advection_pulses``: the advection-diffusion snapshots plus 64 travelling
+  Gaussian pulses sum_p A_p exp(-d(x, x_p + c t)^2 / (2 w^2)), w = 0.01, A_p = 1/p,
+  centres x_p ~ U[0, 2 pi), d the periodic distance (the precision workload).
 * tree builders returning parent arrays (root has parent -1).
 """
 from __future__ import annotations
@@ -194,3 +197,43 @@ def advection_diffusion_device(n: int, num_cols: int, seed: int, dtype, device, 
         out.copy_(Xt)
         return out
     return Xt
+
+
+# --------------------------------------------------- travelling pulses
+NUM_PULSES = 64
+PULSE_WIDTH = 0.01
+
+
+def pulse_params(seed: int):
+    """(centres x_p, amplitudes A_p) of the 64 travelling pulses: x_p ~ U[0, 2 pi) from
+    a stream of its own (seed + 1), A_p = 1/p (1/f decay)."""
+    rng = np.random.default_rng(seed + 1)
+    xp = rng.uniform(0.0, 2.0 * math.pi, NUM_PULSES)
+    amp = 1.0 / np.arange(1, NUM_PULSES + 1, dtype=np.float64)
+    return xp, amp
+
+
+def snapshot_times(num_cols: int, seed: int) -> np.ndarray:
+    """t_j of advection_diffusion_coeffs (the same stream, after the 32 amplitudes)."""
+    rng = np.random.default_rng(seed)
+    rng.standard_normal(NUM_HARMONICS)
+    return rng.uniform(0.0, 1.0, num_cols)
+
+
+def add_pulses(X: np.ndarray, t: np.ndarray, seed: int, c: float = 1.0) -> np.ndarray:
+    """X[:, j] += sum_p A_p exp(-d(x_i, x_p + c t_j)^2 / (2 w^2)) on x_i = 2 pi i / n."""
+    n = X.shape[0]
+    x = 2.0 * math.pi * np.arange(n) / n
+    xp, amp = pulse_params(seed)
+    for p in range(NUM_PULSES):
+        d = (x[:, None] - xp[p] - c * t[None, :] + math.pi) % (2.0 * math.pi) - math.pi
+        X += amp[p] * np.exp(-d * d / (2.0 * PULSE_WIDTH ** 2))
+    return X
+
+
+def advection_pulses(n: int, num_cols: int, seed: int, dtype=np.float64) -> np.ndarray:
+    """Host version of the precision workload's snapshots (n x num_cols)."""
+    X = fourier_basis(n) @ advection_diffusion_coeffs(num_cols, seed)
+    add_pulses(X, snapshot_times(num_cols, seed), seed)
+    return np.asfortranarray(X.astype(dtype))
+

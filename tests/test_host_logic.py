@@ -1,5 +1,6 @@
 """Host-side helpers of the sweeps (no GPU): the tree-shape builder of Sec. 4.2 and
 the direct-POD rank used to count additional HAPOD modes (Sec. 4.3)."""
+import json
 import math
 
 import numpy as np
@@ -68,16 +69,41 @@ def test_direct_pod_rank_inclusive_threshold():
 
 
 def test_roofline_fields_for_the_digit_slice_gram():
-    """bench.py's roofline object: tensor-bound digit Gram against the measured peak,
-    achieved = 28 fp16 flops per FP64 Gram flop over the step time, numeric traffic."""
+    """bench.py's roofline object: the digit Gram step on the method's algorithmic bytes
+    (8 n m per node) against the measured HBM peak, the digit-pair tensor rate beside
+    it, and traffic either a recorded capture of the unchanged kernel or null."""
     from paper_1607_05210_gb300 import hapod as H
 
     res = {"steps": {"gram": {"ms": 100.0, "launches": 64, "bytes": 1e9, "flops": 2e12},
                      "modes": {"ms": 50.0, "launches": 7, "bytes": 1e9, "flops": 1e11}}}
     dom, roof = bench.roofline(res, H.HAPOD_FP64_OZAKI, H, 6786.2, 1725.3)
-    assert dom == "gram" and roof["bound"] == "tensor" and roof["unit"] == "TFLOP/s"
-    assert roof["achieved"] == pytest.approx(28 * 2e12 / 0.1 / 1e12)
-    assert roof["frac"] == pytest.approx(roof["achieved"] / 1725.3)
-    assert isinstance(roof["traffic"], float) and roof["traffic"] > 0
-    dom, roof = bench.roofline(res, H.HAPOD_MIXED_BF16X3, H, 6786.2, 1725.3, "gram")
+    assert dom == "gram" and roof["bound"] == "hbm" and roof["unit"] == "GB/s"
+    assert roof["achieved"] == pytest.approx(1e9 / 0.1 / 1e9)
+    assert roof["frac"] == pytest.approx(roof["achieved"] / 6786.2)
+    assert roof["digit_tflops"] == pytest.approx(28 * 2e12 / 0.1 / 1e12)
+    assert roof["traffic"] is None or (isinstance(roof["traffic"], float) and roof["traffic"] > 0)
+
+
+def test_kernel_traffic_is_null_once_the_source_changed(tmp_path, monkeypatch):
+    src = tmp_path / "k.cu"
+    src.write_text("kernel v1")
+    import hashlib
+
+    rec = {"k": {"source": str(src), "sha256": hashlib.sha256(b"kernel v1").hexdigest(),
+                 "bytes_per_launch": 5.0e9, "note": "capture"}}
+    f = tmp_path / "traffic.json"
+    f.write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(f))
+    assert bench.kernel_traffic("k") == (5.0e9, "capture")
+    src.write_text("kernel v2")
+    assert bench.kernel_traffic("k")[0] is None
+    assert bench.kernel_traffic("missing")[0] is None
+
+
+def test_mixed_gram_roofline_is_hbm_bound():
+    from paper_1607_05210_gb300 import hapod as H
+
+    res = {"steps": {"gram": {"ms": 100.0, "launches": 64, "bytes": 1e9, "flops": 2e12},
+                     "modes": {"ms": 50.0, "launches": 7, "bytes": 1e9, "flops": 1e11}}}
+    dom, roof = bench.roofline(res, H.HAPOD_MIXED_TF32X3, H, 6786.2, 1725.3, "gram")
     assert roof["bound"] == "hbm" and roof["achieved"] == pytest.approx(1e9 / 0.1 / 1e9)
