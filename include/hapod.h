@@ -38,6 +38,14 @@
  *     from the six piece products whose levels add to at most 2 (dropped terms below
  *     2^-26 |x_i x_j|), FP32 tensor-core accumulation over 64-row segments summed in
  *     compensated FP32 pairs and FP64; eigensolve with FP64 rotations.
+ *     Mixed fixed-point form (HAPOD_MIXED_FX3): snapshots are IEEE float; in every
+ *     64-row block each column is scaled by its block maximum's power of two and
+ *     rounded to a 24-bit integer, written as three balanced 8-bit digits; the six
+ *     digit pairs of levels 2..4 are summed exactly on the fp16 tensor cores and in
+ *     int64, so the Gram carries only the representation error (at most 2^-24 of the
+ *     block maximum per value, 2^-22 per row product, unbiased) and one FP64 rounding
+ *     per entry and row split; no FP32 overflow.  X V, eigensolve and root as the
+ *     split-BF16 form.
  *     Eigensolve, tail sums and truncation use FP64 arithmetic on FP64 data except
  *     where stated.
  */
@@ -70,11 +78,16 @@ typedef enum {
                                digit products on the fp16 tensor cores (error-free splitting
                                of Ozaki et al. 2012, integer-exact accumulation, one final
                                FP64 rounding per entry); eigensolver in FP64 */
-  HAPOD_MIXED_BF16X3 = 3    /* float snapshots; Gram and X V on the tensor cores from the exact
+  HAPOD_MIXED_BF16X3 = 3,   /* float snapshots; Gram on the tensor cores from the exact
                                three-piece bf16 split x = b1 + b2 + b3 (six products per
                                entry, FP32 accumulation over 64-row segments, compensated
                                sums, FP64 over row splits); Jacobi eigensolve with FP64
                                rotations, FP64 truncation, CholQR2 at the root */
+  HAPOD_MIXED_FX3 = 4       /* float snapshots; Gram on the fp16 tensor cores from three
+                               balanced 8-bit digits per value, fixed-point per column and
+                               64-row block (six digit pairs, integer-exact sums, int64
+                               accumulation, one FP64 rounding per entry and row split);
+                               eigensolve, truncation and root as HAPOD_MIXED_BF16X3 */
 } hapod_precision;
 
 /*

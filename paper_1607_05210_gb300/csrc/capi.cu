@@ -184,11 +184,12 @@ bool init_env(Env& env, void* stream) {
 }
 
 bool valid_precision(int p) {
-  return p == HAPOD_FP64 || p == HAPOD_MIXED_TF32X3 || p == HAPOD_FP64_OZAKI || p == HAPOD_MIXED_BF16X3;
+  return p == HAPOD_FP64 || p == HAPOD_MIXED_TF32X3 || p == HAPOD_FP64_OZAKI || p == HAPOD_MIXED_BF16X3 ||
+         p == HAPOD_MIXED_FX3;
 }
 // FP64 snapshots (the FP64 and digit-slice forms) versus FP32 snapshots (mixed forms)
 bool f64_data(int p) { return p == HAPOD_FP64 || p == HAPOD_FP64_OZAKI; }
-bool mixed_form(int p) { return p == HAPOD_MIXED_TF32X3 || p == HAPOD_MIXED_BF16X3; }
+bool mixed_form(int p) { return p == HAPOD_MIXED_TF32X3 || p == HAPOD_MIXED_BF16X3 || p == HAPOD_MIXED_FX3; }
 size_t elem_size(int p) { return f64_data(p) ? sizeof(double) : sizeof(float); }
 
 // ------------------------------------------------------------- batched steps
@@ -581,10 +582,56 @@ bool step_modes_oz(Env& env, std::vector<Work*>& ws) {
   return ok;
 }
 
+// K1, mixed fixed-point form: 128 x 64 tiles of exact digit products.
+bool step_gram_fx3(Env& env, std::vector<Work*>& ws) {
+  std::vector<GramJob> jobs(ws.size());
+  std::vector<CUtensorMap> maps(2 * ws.size());
+  double bytes = 0, flops = 0;
+  for (size_t i = 0; i < ws.size(); ++i) {
+    GramJob& J = jobs[i];
+    memset(&J, 0, sizeof(J));
+    J.X = ws[i]->X;
+    J.ldx = ws[i]->ldx;
+    J.n = ws[i]->n;
+    J.m = (int32_t)ws[i]->m;
+    J.G = ws[i]->G;
+    if (!encode_colmajor_f32(&maps[2 * i], ws[i]->X, ws[i]->n, ws[i]->m, ws[i]->ldx, gram_fx3_rows_per_stage(),
+                             gram_fx3_a_cols(), true) ||
+        !encode_colmajor_f32(&maps[2 * i + 1], ws[i]->X, ws[i]->n, ws[i]->m, ws[i]->ldx, gram_fx3_rows_per_stage(),
+                             gram_fx3_b_cols(), true))
+      return env.fail(HAPOD_ERR_CUDA, "cuTensorMapEncodeTiled failed for a Gram input");
+    bytes += 4.0 * ws[i]->n * ws[i]->m;
+    flops += (double)ws[i]->n * ws[i]->m * (ws[i]->m + 1);
+  }
+  std::vector<int4> items, reduce;
+  size_t pbytes = 0;
+  plan_gram_fx3(jobs.data(), (int)jobs.size(), kNumSMs, items, reduce, &pbytes);
+  GramJob* jobs_d = env.upload(jobs, "upload gram jobs");
+  int4* items_d = env.upload(items, "upload gram items");
+  int4* red_d = env.upload(reduce, "upload gram reduce");
+  CUtensorMap* maps_d = env.upload(maps, "upload tensor maps");
+  double* partials = pbytes ? (double*)env.alloc(pbytes, "alloc gram partials") : nullptr;
+  bool ok = jobs_d && items_d && red_d && maps_d && (partials || !pbytes) && env.err_dev;
+  if (ok) {
+    cudaEvent_t t0 = env.tic();
+    ok = env.cuda(launch_gram_fx3(jobs_d, maps_d, items_d, (int)items.size(), red_d, (int)reduce.size(), partials,
+                                  env.err_dev, env.s),
+                  "gram launch");
+    env.toc(t0, 0, 1 + !reduce.empty(), bytes, flops);
+  }
+  env.release(jobs_d);
+  env.release(items_d);
+  env.release(red_d);
+  env.release(maps_d);
+  env.release(partials);
+  return ok;
+}
+
 // K1 for every node of ws into w->G.
 bool step_gram(Env& env, int precision, std::vector<Work*>& ws) {
   if (ws.empty()) return true;
   if (precision == HAPOD_FP64_OZAKI) return step_gram_oz(env, ws);
+  if (precision == HAPOD_MIXED_FX3) return step_gram_fx3(env, ws);
   const bool fp64 = precision == HAPOD_FP64;
   const bool bf3 = precision == HAPOD_MIXED_BF16X3;
   std::vector<GramJob> jobs(ws.size());
@@ -650,10 +697,14 @@ bool step_gram(Env& env, int precision, std::vector<Work*>& ws) {
 // TF32 form), or FP32 sweeps followed by FP64 sweeps to the FP64 stopping rule
 // (mixed split-BF16 form).
 int eig_mode(int precision) {
-  return precision == HAPOD_MIXED_TF32X3 ? kEigF32 : precision == HAPOD_MIXED_BF16X3 ? kEigF32F64 : kEigF64;
+  return precision == HAPOD_MIXED_TF32X3                                      ? kEigF32
+         : (precision == HAPOD_MIXED_BF16X3 || precision == HAPOD_MIXED_FX3) ? kEigF32F64
+                                                                              : kEigF64;
 }
 // Relative level of a form's Gram error (the pivoted Cholesky does not factor below it).
-double gram_floor_rel(int precision) { return precision == HAPOD_MIXED_BF16X3 ? 1e-10 : 0.0; }
+double gram_floor_rel(int precision) {
+  return precision == HAPOD_MIXED_BF16X3 ? 1e-10 : precision == HAPOD_MIXED_FX3 ? 1e-13 : 0.0;
+}
 // Eigenvectors are stored in FP64 except by the mixed TF32 form (FP32).
 bool eigvec_f64(int precision) { return precision != HAPOD_MIXED_TF32X3; }
 
@@ -1105,7 +1156,7 @@ bool run_batch(hapod_ctx* c, const std::vector<int>& batch) {
         scales.push_back(w.scale);
         // resolution floor of the method of snapshots (Sec. 2 footnote: cond(G) = cond(X)^2)
         const double u = f64_data(c->precision)                    ? 1.1102230246251565e-16
-                         : c->precision == HAPOD_MIXED_BF16X3 ? gram_floor_rel(c->precision)
+                         : gram_floor_rel(c->precision) > 0.0 ? gram_floor_rel(c->precision)
                                                               : 5.9604644775390625e-08;
         if (A.sigma[A.k - 1] < A.sigma[0] * std::sqrt((double)A.m * u)) {
           A.status = HAPOD_WARN_BELOW_FLOOR;

@@ -15,7 +15,7 @@
 // Accumulation: the FP32 tensor-core accumulator truncates at every step, so it
 // restarts every kSegStages stages (64 rows, 24 MMAs) and each finished segment is
 // added into a compensated FP32 pair (running sum s, compensation c, TwoSum) kept in
-// TMEM; the item's s + c is written in FP64 and row splits are summed in FP64 by
+// TMEM; the item's compensated sum s - c is written in FP64 and row splits are summed in FP64 by
 // gram_reduce in a fixed order.  GB300 runs FP64 at 1/64 of the FP32 rate, so the
 // per-segment additions stay in FP32 pairs, whose 2^-44 relative resolution is far
 // below the accumulation error of the segments themselves.
@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-          const double v = (double)sv[i] + (double)cv[i];
+          const double v = (double)sv[i] - (double)cv[i];  // the compensated sum: c holds the excess of s
           if (out) {
             out[c0 + i] = v;
           } else {

@@ -1,0 +1,562 @@
+// K1, fixed-point mixed form: Gramian G = X^T X (Sec. 2, Remark
+// def:method_of_snapshots) of FP32 snapshots on the 5th-generation tensor cores
+// (tcgen05, kind::f16, fp16 digit operands) with exact accumulation.
+//
+// The squared condition number of the Gram matrix (footnote of the method-of-
+// snapshots remark) puts the discarded tail sums of a node at 1e-9..1e-10 of its
+// trace for eps = 1e-4..1e-5 rel; the tensor core's FP32 accumulator truncates at
+// every step, unevenly across entries, which leaves noise of that very size on the
+// small eigenvalues.  This form therefore adds nothing inexactly until the very end:
+//
+// Digits: the rows are taken in blocks of 64.  In block b every column j gets the
+// exponent E = E_j^b with max_r |x_rj| < 2^E (computed in the kernel from the block
+// in shared memory), and every value becomes the 24-bit integer A = rint(x 2^(23-E))
+// (|A| <= 2^23) written as three balanced base-256 digits A = d1 2^16 + d2 2^8 + d3,
+// d2, d3 in [-128, 128], |d1| <= 128 (round to nearest at each step, so the pieces
+// are unbiased); the representation error is at most 2^(E-24).
+// Products: x_i x_j = 2^(E_i+E_j-46) sum_{t,u} d_t d_u 2^(48-8(t+u)); the levels
+// s = t + u = 2, 3, 4 are kept (six digit pairs; the dropped ones weigh at most
+// 2^(E_i+E_j-22) per row), each level summed over the block on the tensor cores:
+// L_s <= 64 * 3 * 2^14 < 2^24, an integer the FP32 accumulator holds exactly.
+// Flush: after each block, v = L_2 2^16 + L_3 2^8 + L_4 (exact, < 2^41) is added
+// into an int64 fixed-point sum per entry whose unit is 2^(R_i+R_j-30), R the running
+// maximum of the block exponents (rounding shift; the sum is shifted down when R
+// grows).  The item writes ldexp(sum, R_i + R_j - 30) in FP64 -- one rounding -- and
+// row splits are summed in FP64 in a fixed order.  Columns holding Inf or NaN give
+// NaN rows and columns of G.
+//
+// Work item = one 128 x 64 tile (A columns 128 I.., B columns 64 J.., J >= 2 I) of
+// one node's G over one row split; items are ordered by split first.  One CTA per
+// item, 18 warps:
+//   warp 0        TMA producer: FP32 blocks of 32 rows x 128 A columns (and 64 B
+//                 columns when they are not inside the A panel), 128-byte swizzled,
+//                 4 stages deep
+//   warp 1        TMEM owner and single-thread MMA issuer: per 16 rows three MMAs,
+//                 d1 (A) against [d1 d2 d3] (B, N = 192) into the level accumulators
+//                 L2 | L3 | L4, d2 against [d1 d2] (N = 128) into L3 | L4, d3 against
+//                 d1 (N = 64) into L4; two accumulator sets alternate between blocks
+//   warps 2..9    converters: block column maxima, exponents, digits (K-major 8 x 8
+//                 core matrices, no swizzle), 2 stages deep
+//   warps 10..17  flushers: int64 sums of 32 entries per thread
+// Every mbarrier wait is bounded: a timeout raises the error flag, the CTA drains
+// its copies and MMAs and frees TMEM.
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "hapod_internal.cuh"
+#include "tc_common.cuh"
+
+namespace hapod {
+namespace {
+
+constexpr int kRows = 32;                              // rows per stage (K of two MMAs)
+constexpr int kBlockStages = 2;                        // stages per exponent block (64 rows)
+constexpr int kACols = 128;
+constexpr int kBCols = 64;
+constexpr int kStA = kRows * kACols * 4;               // FP32 staging of the A panel, 16 KB
+constexpr int kStB = kRows * kBCols * 4;               // 8 KB
+constexpr int kStSlot = kStA + kStB;
+constexpr int kStSlots = 4;                            // two blocks in flight
+constexpr int kPlaneA = kRows * kACols * 2;            // one digit plane of A, 8 KB
+constexpr int kPlaneB = kRows * kBCols * 2;            // 4 KB
+constexpr int kOpSlot = 3 * kPlaneA + 3 * kPlaneB;     // 36 KB
+constexpr int kOpSlots = 2;
+constexpr int kExpSlots = 2;
+constexpr int kSmemBytes = kStSlots * kStSlot + kOpSlots * kOpSlot + 1024;
+constexpr int kThreads = 576;
+constexpr int kConvThreads = 256;
+constexpr int kFirstFlushWarp = 10;
+constexpr uint32_t kLbo = 128;                         // next core matrix along K (8 rows)
+constexpr uint32_t kSbo = (kRows / 8) * 128;           // next core matrix along M / N (8 columns)
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kSetCols = 256;                     // one set of L2 | L3 | L4 (192 used)
+constexpr int kExpZero = -4000;                        // exponent of an all-zero column block
+constexpr int kExpBad = 4000;                          // exponent marking Inf / NaN
+static_assert(kSmemBytes <= 227 * 1024, "shared memory");
+
+struct Bars {
+  uint64_t full[kStSlots];     // TMA -> converters
+  uint64_t st_free[kStSlots];  // converters -> TMA
+  uint64_t op_full[kOpSlots];  // converters -> issuer
+  uint64_t op_free[kOpSlots];  // issuer (MMA completion) -> converters
+  uint64_t exp_full[kExpSlots];  // converters -> flushers: block exponents written
+  uint64_t exp_free[kExpSlots];  // flushers -> converters
+  uint64_t acc_full[2];
+  uint64_t acc_empty[2];
+  uint64_t mma_done;
+};
+
+struct Shared {
+  Bars bars;
+  int exps[kExpSlots][kACols + kBCols];  // block exponents: A columns, then B columns
+  int bad[kACols + kBCols];              // sticky: column held Inf or NaN
+  uint32_t tmem_base;
+  int abort_flag;
+};
+
+// Exponent E with max |x| < 2^E from the bit pattern of the block maximum.
+__device__ __forceinline__ int exp_of_max(float mx) {
+  if (!(mx <= 3.402823466e38f)) return kExpBad;  // Inf or NaN
+  if (mx == 0.f) return kExpZero;
+  int e;
+  frexpf(mx, &e);  // mx = f 2^e, f in [0.5, 1): mx < 2^e
+  return e;
+}
+
+// Three balanced base-256 digits of rint(x 2^(23 - E)) (as floats holding integers in
+// [-128, 128]), by round-to-nearest splits with the constants 1.5 2^39, 1.5 2^31 and
+// 1.5 2^23, whose FP32 ulps are 2^16, 2^8 and 1: adding and subtracting one rounds to
+// that multiple, and every remainder is exact in FP32.
+__device__ __forceinline__ void digits3(float x, float s1, float s2, float& d1, float& d2, float& d3) {
+  const float a = (x * s1) * s2;  // |a| < 2^23, exact (power-of-two scaling)
+  const float h1 = (a + 824633720832.0f) - 824633720832.0f;  // 1.5 2^39 (ulp 2^16): rint to a multiple of 2^16
+  const float r1 = a - h1;                                   // |r1| <= 2^15, exact
+  const float h2 = (r1 + 3221225472.0f) - 3221225472.0f;     // 1.5 2^31 (ulp 2^8): rint to a multiple of 2^8
+  const float r2 = r1 - h2;                                  // |r2| <= 2^7, exact
+  const float h3 = (r2 + 12582912.0f) - 12582912.0f;         // 1.5 2^23 (ulp 1): rint
+  d1 = h1 * (1.0f / 65536.0f);
+  d2 = h2 * (1.0f / 256.0f);
+  d3 = h3;
+}
+
+__device__ __forceinline__ uint32_t h2bits(float lo, float hi) {
+  const __half2 v = __floats2half2_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// Scale factors s1 s2 = 2^(23 - E) (two factors so that both stay in range).
+__device__ __forceinline__ void scales(int E, float& s1, float& s2) {
+  if (E <= kExpZero || E >= kExpBad) {
+    s1 = 0.f;
+    s2 = 0.f;
+    return;
+  }
+  const int e = 23 - E;  // in [-105, 172]
+  const int e1 = max(-126, min(127, e));
+  s1 = ldexpf(1.0f, e1);
+  s2 = ldexpf(1.0f, e - e1);
+}
+
+// Convert the unit (column c of a panel of `cols` columns, row octet g) of one stage:
+// 8 values from the 128-byte-swizzled staging, three fp16 digit planes out.
+__device__ __forceinline__ void convert_unit(const uint8_t* __restrict__ st, uint8_t* __restrict__ planes,
+                                             uint32_t plane_bytes, int c, int g, float s1, float s2) {
+  const float4 v0 = *reinterpret_cast<const float4*>(st + c * 128 + (((2 * g) ^ (c & 7)) << 4));
+  const float4 v1 = *reinterpret_cast<const float4*>(st + c * 128 + (((2 * g + 1) ^ (c & 7)) << 4));
+  const float x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+  uint32_t w1[4], w2[4], w3[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float a1, a2, a3, b1, b2, b3;
+    digits3(x[2 * i], s1, s2, a1, a2, a3);
+    digits3(x[2 * i + 1], s1, s2, b1, b2, b3);
+    w1[i] = h2bits(a1, b1);
+    w2[i] = h2bits(a2, b2);
+    w3[i] = h2bits(a3, b3);
+  }
+  const uint32_t off = (uint32_t)(c >> 3) * kSbo + (uint32_t)g * kLbo + (uint32_t)(c & 7) * 16;
+  *reinterpret_cast<uint4*>(planes + off) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+  *reinterpret_cast<uint4*>(planes + plane_bytes + off) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+  *reinterpret_cast<uint4*>(planes + 2 * plane_bytes + off) = make_uint4(w3[0], w3[1], w3[2], w3[3]);
+}
+
+// Round-to-nearest arithmetic right shift of a signed 64-bit value (sh >= 0).
+__device__ __forceinline__ long long rshift_rn(long long v, int sh) {
+  if (sh <= 0) return v;
+  if (sh >= 62) return 0;
+  return (v + (1LL << (sh - 1))) >> sh;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    gram_fx3_kernel(const GramJob* __restrict__ jobs, const CUtensorMap* __restrict__ maps,
+                    const int4* __restrict__ items, double* __restrict__ partials, int* err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ Shared sh;
+  Bars& bars = sh.bars;
+  volatile int* abort_flag = &sh.abort_flag;
+
+  const int4 it = items[blockIdx.x];
+  const GramJob J = jobs[it.x];
+  const CUtensorMap* mapA = maps + 2 * it.x;
+  const CUtensorMap* mapB = maps + 2 * it.x + 1;
+  const int I = it.y, Jt = it.z, sp = it.w;
+  const int a0 = kACols * I, b0 = kBCols * Jt;
+  const bool b_in_a = b0 >= a0 && b0 < a0 + kACols;  // B columns inside the A panel
+  const int64_t r0 = (int64_t)sp * J.rows_per_split;
+  const int64_t r1 = min(J.n, r0 + J.rows_per_split);
+  const int nst = r1 > r0 ? (int)((r1 - r0 + kRows - 1) / kRows) : 0;
+  const int nblk = (nst + kBlockStages - 1) / kBlockStages;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const tc::WaitBudget wb = tc::wait_budget(err);
+  auto st_a = [&](int s) -> uint8_t* { return smem + (size_t)s * kStSlot; };
+  auto st_b = [&](int s) -> uint8_t* { return smem + (size_t)s * kStSlot + kStA; };
+  uint8_t* op_ring = smem + (size_t)kStSlots * kStSlot;
+  auto op_a = [&](int t) -> uint8_t* { return op_ring + (size_t)t * kOpSlot; };
+  auto op_b = [&](int t) -> uint8_t* { return op_ring + (size_t)t * kOpSlot + 3 * kPlaneA; };
+
+  if (tid == 0) {
+    for (int s = 0; s < kStSlots; ++s) {
+      tc::mbar_init(&bars.full[s], 1);
+      tc::mbar_init(&bars.st_free[s], 8);
+    }
+    for (int t = 0; t < kOpSlots; ++t) {
+      tc::mbar_init(&bars.op_full[t], 8);
+      tc::mbar_init(&bars.op_free[t], 1);
+    }
+    for (int e = 0; e < kExpSlots; ++e) {
+      tc::mbar_init(&bars.exp_full[e], 8);
+      tc::mbar_init(&bars.exp_free[e], 8);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&bars.acc_full[b], 1);
+      tc::mbar_init(&bars.acc_empty[b], 8);
+    }
+    tc::mbar_init(&bars.mma_done, 1);
+    sh.abort_flag = 0;
+    tc::mbar_fence_init();
+  }
+  for (int i = tid; i < kACols + kBCols; i += blockDim.x) sh.bad[i] = 0;
+  if (warp == 1) tc::tmem_alloc(&sh.tmem_base, kTmemCols);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tbase = sh.tmem_base;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0 && nst > 0) {
+      tc::tensormap_acquire(mapA);
+      if (!b_in_a) tc::tensormap_acquire(mapB);
+      const uint32_t bytes = (uint32_t)(kStA + (b_in_a ? 0 : kStB));
+      int issued = 0;
+      for (int k = 0; k < nst; ++k) {
+        const int s = k % kStSlots;
+        if (k >= kStSlots && !tc::mbar_wait(&bars.st_free[s], ((k / kStSlots) - 1) & 1, abort_flag, err, wb)) break;
+        tc::mbar_expect_tx(&bars.full[s], bytes);
+        const int row = (int)(r0 + (int64_t)k * kRows);
+        tc::tma_load_2d(st_a(s), mapA, row, a0, &bars.full[s]);
+        if (!b_in_a) tc::tma_load_2d(st_b(s), mapB, row, b0, &bars.full[s]);
+        issued = k + 1;
+      }
+      if (*abort_flag) {
+        for (int k = max(0, issued - kStSlots); k < issued; ++k) {
+          const long long t0 = clock64();
+          while (!tc::mbar_try(&bars.full[k % kStSlots], (k / kStSlots) & 1) && clock64() - t0 < tc::kWaitBudget) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t id192 = tc::idesc_f16_f32_major(128, 192, 0, 0);
+      const uint32_t id128 = tc::idesc_f16_f32_major(128, 128, 0, 0);
+      const uint32_t id64 = tc::idesc_f16_f32_major(128, 64, 0, 0);
+      for (int k = 0; k < nst; ++k) {
+        const int t = k % kOpSlots;
+        const int blk = k / kBlockStages;
+        const bool blk_first = (k % kBlockStages) == 0;
+        const bool blk_last = (k % kBlockStages) == kBlockStages - 1 || k == nst - 1;
+        const int set = blk & 1;
+        if (blk_first && blk >= 2 &&
+            !tc::mbar_wait(&bars.acc_empty[set], ((blk >> 1) - 1) & 1, abort_flag, err, wb))
+          break;
+        if (!tc::mbar_wait(&bars.op_full[t], (k / kOpSlots) & 1, abort_flag, err, wb)) break;
+        tc::tc_fence_after();
+        const uint32_t pa = tc::smem_u32(op_a(t)), pb = tc::smem_u32(op_b(t));
+        const uint32_t d = tbase + (uint32_t)set * kSetCols;
+#pragma unroll
+        for (int kk = 0; kk < kRows / 16; ++kk) {
+          const uint32_t ko = (uint32_t)kk * 2 * kLbo;
+          const uint32_t acc = (blk_first && kk == 0) ? 0u : 1u;
+          // d1 x [d1 d2 d3] -> L2 | L3 | L4
+          tc::umma_f16(d, tc::ns_desc(pa + ko, kLbo, kSbo), tc::ns_desc(pb + ko, kLbo, kSbo), id192, acc);
+          // d2 x [d1 d2] -> L3 | L4
+          tc::umma_f16(d + kBCols, tc::ns_desc(pa + kPlaneA + ko, kLbo, kSbo), tc::ns_desc(pb + ko, kLbo, kSbo),
+                       id128, 1u);
+          // d3 x d1 -> L4
+          tc::umma_f16(d + 2 * kBCols, tc::ns_desc(pa + 2 * kPlaneA + ko, kLbo, kSbo),
+                       tc::ns_desc(pb + ko, kLbo, kSbo), id64, 1u);
+        }
+        tc::umma_commit(&bars.op_free[t]);
+        if (blk_last) tc::umma_commit(&bars.acc_full[set]);
+      }
+      tc::umma_commit(&bars.mma_done);
+      const long long t0 = clock64();
+      while (!tc::mbar_try(&bars.mma_done, 0) && clock64() - t0 < tc::kWaitBudget) {
+      }
+    }
+  } else if (warp < kFirstFlushWarp) {
+    // ------------------------------------------------------------ converters
+    const int cw = warp - 2;  // 0..7
+    const int ct = tid - 64;  // 0..255
+    const int ncols = kACols + (b_in_a ? 0 : kBCols);
+    bool ok = true;
+    for (int blk = 0; blk < nblk && ok; ++blk) {
+      const int k0 = blk * kBlockStages;
+      const int k1 = min(nst, k0 + kBlockStages);
+      for (int k = k0; k < k1 && ok; ++k)
+        ok = tc::mbar_wait_warp(&bars.full[k % kStSlots], (k / kStSlots) & 1, abort_flag, err, wb);
+      const int es = blk % kExpSlots;
+      if (ok && blk >= kExpSlots)
+        ok = tc::mbar_wait_warp(&bars.exp_free[es], ((blk / kExpSlots) - 1) & 1, abort_flag, err, wb);
+      if (!ok) break;
+      // block maxima: four columns per warp instruction, eight lanes per column
+      // (lane l reads physical chunk l % 8 of column 4 w + l / 8: 512 contiguous bytes)
+      for (int c0 = 4 * cw; c0 < ncols; c0 += 32) {
+        const int c = c0 + (lane >> 3);
+        float mx = 0.f;
+        bool badv = false;
+        for (int k = k0; k < k1; ++k) {
+          const int s = k % kStSlots;
+          const uint8_t* base = c < kACols ? st_a(s) + c * 128 : st_b(s) + (c - kACols) * 128;
+          const float4 v = *reinterpret_cast<const float4*>(base + ((lane & 7) << 4));
+          const float m4 = fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w)));
+          badv |= !(fabsf(v.x) <= 3.402823466e38f && fabsf(v.y) <= 3.402823466e38f &&
+                    fabsf(v.z) <= 3.402823466e38f && fabsf(v.w) <= 3.402823466e38f);  // Inf, or NaN (compares false)
+          mx = fmaxf(mx, m4);
+        }
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+          mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+          badv |= __shfl_xor_sync(0xffffffffu, (int)badv, o) != 0;
+        }
+        if ((lane & 7) == 0) {
+          const int E = badv ? kExpBad : exp_of_max(mx);
+          sh.exps[es][c] = E;
+          if (E == kExpBad) sh.bad[c] = 1;
+        }
+      }
+      // every converter warp needs the exponents of all columns: arrive on the block's
+      // exponent barrier, which the flushers also wait on, and wait for the others
+      // (a bounded wait: an aborting warp cannot leave the rest stuck)
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&bars.exp_full[es]);
+      if (!tc::mbar_wait_warp(&bars.exp_full[es], (blk / kExpSlots) & 1, abort_flag, err, wb)) break;
+      // digits of each stage of the block
+      for (int k = k0; k < k1 && ok; ++k) {
+        const int s = k % kStSlots, t = k % kOpSlots;
+        if (k >= kOpSlots) ok = tc::mbar_wait_warp(&bars.op_free[t], ((k / kOpSlots) - 1) & 1, abort_flag, err, wb);
+        if (!ok) break;
+        // A panel: 128 columns x 4 octets = 512 units, two per thread
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int u = ct + h * kConvThreads;
+          const int c = u & (kACols - 1), g = u >> 7;
+          float s1, s2;
+          scales(sh.exps[es][c], s1, s2);
+          convert_unit(st_a(s), op_a(t), kPlaneA, c, g, s1, s2);
+          if (b_in_a && c >= b0 - a0 && c < b0 - a0 + kBCols)
+            convert_unit(st_a(s), op_b(t), kPlaneB, c - (b0 - a0), g, s1, s2);
+        }
+        if (!b_in_a) {  // B panel: 64 columns x 4 octets = 256 units, one per thread
+          const int c = ct & (kBCols - 1), g = ct >> 6;
+          float s1, s2;
+          scales(sh.exps[es][kACols + c], s1, s2);
+          convert_unit(st_b(s), op_b(t), kPlaneB, c, g, s1, s2);
+        }
+        tc::fence_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          tc::mbar_arrive(&bars.st_free[s]);
+          tc::mbar_arrive(&bars.op_full[t]);
+        }
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ flushers + result
+    const int fw = warp - kFirstFlushWarp;  // 0..7
+    const int q = warp & 3;                 // TMEM lane quarter this warp may access
+    const int h = fw >> 2;                  // column half: B columns 32 h .. 32 h + 31
+    const int ai = 32 * q + lane;           // tile row (A column)
+    const uint32_t lanes = (uint32_t)(32 * q) << 16;
+    long long acc[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) acc[i] = 0;
+    int Ri = kExpZero;                 // running exponent of this lane's row
+    int Rj_l = kExpZero;               // running exponent of column 32 h + lane
+    bool ok = true;
+    for (int blk = 0; blk < nblk && ok; ++blk) {
+      const int set = blk & 1, es = blk % kExpSlots;
+      ok = tc::mbar_wait_warp(&bars.acc_full[set], (blk >> 1) & 1, abort_flag, err, wb) &&
+           tc::mbar_wait_warp(&bars.exp_full[es], (blk / kExpSlots) & 1, abort_flag, err, wb);
+      if (!ok) break;
+      tc::tc_fence_after();
+      const int Ei = sh.exps[es][ai];
+      const int Ej_l = b_in_a ? sh.exps[es][b0 - a0 + 32 * h + lane] : sh.exps[es][kACols + 32 * h + lane];
+      const bool vi = Ei > kExpZero && Ei < kExpBad;
+      const bool vj_l = Ej_l > kExpZero && Ej_l < kExpBad;
+      const int Rinew = vi ? max(Ri, Ei) : Ri;
+      const int Rjnew_l = vj_l ? max(Rj_l, Ej_l) : Rj_l;
+      // per column (one per lane): growth of its running exponent, and the distance of
+      // this block's exponent below the new running one (64: not added)
+      const int grow_l = (Rj_l > kExpZero) ? Rjnew_l - Rj_l : 0;
+      const int below_l = vj_l ? Rjnew_l - Ej_l : 64;
+      const int grow_i = (Ri > kExpZero) ? Rinew - Ri : 0;
+      const int below_i = vi ? Rinew - Ei : 64;
+      Ri = Rinew;
+      Rj_l = Rjnew_l;
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {  // 8 columns at a time
+        const uint32_t col = (uint32_t)set * kSetCols + (uint32_t)(32 * h + 8 * g);
+        uint32_t l2[8], l3[8], l4[8];
+        tc::tmem_ld8_raw(tbase + lanes + col, l2);
+        tc::tmem_ld8_raw(tbase + lanes + col + kBCols, l3);
+        tc::tmem_ld8_raw(tbase + lanes + col + 2 * kBCols, l4);
+        tc::tmem_wait_ld();
+        tc::reg_barrier8(l2);
+        tc::reg_barrier8(l3);
+        tc::reg_barrier8(l4);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int jj = 8 * g + i;  // column within the warp's 32
+          const int grow = grow_i + __shfl_sync(0xffffffffu, grow_l, jj);
+          const int below = below_i + __shfl_sync(0xffffffffu, below_l, jj);
+          if (grow > 0) acc[jj] = rshift_rn(acc[jj], grow);  // the unit of the sum grew
+          if (below < 64) {
+            const long long v = (long long)__float2int_rn(__uint_as_float(l2[i])) * 65536LL +
+                                (long long)__float2int_rn(__uint_as_float(l3[i])) * 256LL +
+                                (long long)__float2int_rn(__uint_as_float(l4[i]));
+            acc[jj] += rshift_rn(v, below);
+          }
+        }
+      }
+      tc::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        tc::mbar_arrive(&bars.acc_empty[set]);
+        tc::mbar_arrive(&bars.exp_free[es]);
+      }
+    }
+    if (__all_sync(0xffffffffu, ok && !*abort_flag)) {
+      const int gi = a0 + ai;
+      const bool bad_i = sh.bad[ai] != 0;
+      const int jmax = (J.m + kBCols - 1) / kBCols;
+      const int tile_idx = I * jmax - I * (I - 1) + (Jt - 2 * I);
+      double* out = J.splits > 1 ? partials + ((size_t)J.item_base + (size_t)tile_idx * J.splits + sp) *
+                                                  (size_t)(kACols * kBCols)
+                                 : nullptr;
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) {
+        const int Rj = __shfl_sync(0xffffffffu, Rj_l, jj);
+        const int bj = 32 * h + jj;  // column within the B panel
+        const int gj = b0 + bj;
+        const bool bad_j = b_in_a ? sh.bad[gj - a0] != 0 : sh.bad[kACols + bj] != 0;
+        double v;
+        if (bad_i || bad_j)
+          v = __longlong_as_double(0x7FF8000000000000LL);
+        else if (Ri <= kExpZero || Rj <= kExpZero)
+          v = 0.0;
+        else
+          v = ldexp((double)acc[jj], Ri + Rj - 30);
+        if (out) {
+          out[(size_t)ai * kBCols + bj] = v;
+        } else if (gi < J.m && gj < J.m && gj >= gi) {
+          J.G[(size_t)gj * J.m + gi] = v;
+          J.G[(size_t)gi * J.m + gj] = v;
+        }
+      }
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  if (warp == 1) tc::tmem_dealloc(tbase, kTmemCols);
+}
+
+// Sum the split partials of every reduce-list tile (job, I, J, first) in split order;
+// entries i <= j of G and their mirror images.
+__global__ void gram_fx3_reduce(const GramJob* __restrict__ jobs, const int4* __restrict__ reduce,
+                                const double* __restrict__ partials) {
+  const int4 r = reduce[blockIdx.y];
+  const GramJob J = jobs[r.x];
+  const int I = r.y, Jt = r.z;
+  const int jmax = (J.m + kBCols - 1) / kBCols;
+  const int tile_idx = I * jmax - I * (I - 1) + (Jt - 2 * I);
+  const double* p = partials + ((size_t)J.item_base + (size_t)tile_idx * J.splits) * (size_t)(kACols * kBCols);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < kACols * kBCols; e += gridDim.x * blockDim.x) {
+    const int gi = kACols * I + e / kBCols, gj = kBCols * Jt + e % kBCols;
+    if (gi >= J.m || gj >= J.m || gj < gi) continue;
+    double s = 0.0;
+    for (int sp = 0; sp < J.splits; ++sp) s += p[(size_t)sp * (kACols * kBCols) + e];
+    J.G[(size_t)gj * J.m + gi] = s;
+    J.G[(size_t)gi * J.m + gj] = s;
+  }
+}
+
+}  // namespace
+
+int gram_fx3_rows_per_stage() { return kRows; }
+int gram_fx3_a_cols() { return kACols; }
+int gram_fx3_b_cols() { return kBCols; }
+
+void plan_gram_fx3(GramJob* jobs, int njobs, int target_items, std::vector<int4>& items, std::vector<int4>& reduce,
+                   size_t* partial_bytes) {
+  // tiles (I, J), J >= 2 I, of every job; one split count for the batch chosen as in
+  // plan_gram: the fewest waves of `target_items` CTAs per unit of work
+  int64_t total_tiles = 0, max_n = 1;
+  for (int j = 0; j < njobs; ++j) {
+    const int64_t imax = (jobs[j].m + kACols - 1) / kACols, jmax = (jobs[j].m + kBCols - 1) / kBCols;
+    int64_t t = 0;
+    for (int64_t I = 0; I < imax; ++I) t += std::max<int64_t>(0, jmax - 2 * I);
+    jobs[j].tiles = (int32_t)t;
+    total_tiles += t;
+    max_n = std::max<int64_t>(max_n, jobs[j].n);
+  }
+  const int64_t min_rows = 4096;
+  const int64_t s_cap = std::max<int64_t>(
+      1, std::min<int64_t>(max_n / min_rows, total_tiles > 0 ? 8 * (int64_t)target_items / total_tiles + 1 : 1));
+  int64_t splits = 1;
+  double best = 1e300;
+  for (int64_t s = 1; s <= s_cap && total_tiles > 0; ++s) {
+    const double waves = (double)((total_tiles * s + target_items - 1) / target_items);
+    if (waves / (double)s < best * (1.0 - 1e-9)) {
+      best = waves / (double)s;
+      splits = s;
+    }
+  }
+  int64_t slot = 0;
+  items.clear();
+  reduce.clear();
+  for (int j = 0; j < njobs; ++j) {
+    GramJob& J = jobs[j];
+    int64_t s = std::max<int64_t>(1, std::min(splits, std::max<int64_t>(1, J.n / min_rows)));
+    int64_t rps = (J.n + s - 1) / s;
+    rps = (rps + 63) / 64 * 64;  // whole 64-row exponent blocks
+    s = std::max<int64_t>(1, (J.n + rps - 1) / rps);
+    J.splits = (int32_t)s;
+    J.rows_per_split = rps;
+    J.item_base = slot;
+    const int imax = (J.m + kACols - 1) / kACols, jmax = (J.m + kBCols - 1) / kBCols;
+    for (int I = 0; I < imax; ++I)
+      for (int Jt = 2 * I; Jt < jmax; ++Jt) {
+        if (s > 1) reduce.push_back(make_int4(j, I, Jt, 0));
+        for (int sp = 0; sp < s; ++sp) items.push_back(make_int4(j, I, Jt, sp));
+      }
+    slot += (int64_t)J.tiles * s;
+  }
+  std::stable_sort(items.begin(), items.end(), [](const int4& a, const int4& b) { return a.w < b.w; });
+  *partial_bytes = reduce.empty() ? 0 : (size_t)slot * kACols * kBCols * sizeof(double);
+}
+
+cudaError_t launch_gram_fx3(const GramJob* jobs_dev, const CUtensorMap* maps_dev, const int4* items_dev,
+                            int num_items, const int4* reduce_dev, int num_reduce, double* partials, int* err_flag,
+                            cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(gram_fx3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  if (num_items > 0)
+    gram_fx3_kernel<<<num_items, kThreads, kSmemBytes, s>>>(jobs_dev, maps_dev, items_dev, partials, err_flag);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || num_reduce <= 0) return e;
+  gram_fx3_reduce<<<dim3(8, num_reduce), 256, 0, s>>>(jobs_dev, reduce_dev, partials);
+  return cudaGetLastError();
+}
+
+}  // namespace hapod

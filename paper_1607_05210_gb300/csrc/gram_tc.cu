@@ -21,7 +21,7 @@
 // 48 accumulate steps; the resulting bias is a near-uniform relative shrink of the
 // segment sums) and the flushers add each finished segment into a Kahan-compensated
 // FP32 pair (running sum s and compensation c) kept in the other half of TMEM; the
-// item's result s + c is written in FP64 and splits are summed in FP64 by
+// item's compensated sum s - c is written in FP64 and splits are summed in FP64 by
 // gram_reduce in a fixed order.  Every mbarrier wait is
 // bounded: a timeout raises the error flag, the CTA drains its copies and MMAs and
 // frees TMEM.
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-          const double v = (double)sv[i] + (double)cv[i];
+          const double v = (double)sv[i] - (double)cv[i];  // the compensated sum: c holds the excess of s
           if (out) {
             out[c0 + i] = v;
           } else {

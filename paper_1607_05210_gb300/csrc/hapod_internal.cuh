@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/hapod.h"
 
 namespace hapod {
@@ -77,6 +79,19 @@ cudaError_t launch_gram_bf3(const GramJob* jobs_dev, const CUtensorMap* maps_dev
                             int num_items, const int4* reduce_dev, int num_reduce, double* partials, int* err_flag,
                             cudaStream_t s);
 int gram_bf3_rows_per_stage();
+// Mixed fixed-point form (exact three-digit products, per-64-row-block exponents):
+// 128 x 64 tiles; maps_dev[2 j] / [2 j + 1]: job j's X with boxes of
+// gram_fx3_rows_per_stage() rows x gram_fx3_a_cols() / gram_fx3_b_cols() columns
+// (128-byte swizzle).  plan_gram_fx3 fills the jobs' tiles, splits, rows_per_split,
+// item_base and the item / reduce lists (int4 job, I, J, split).
+void plan_gram_fx3(GramJob* jobs, int njobs, int target_items, std::vector<int4>& items, std::vector<int4>& reduce,
+                   size_t* partial_bytes);
+cudaError_t launch_gram_fx3(const GramJob* jobs_dev, const CUtensorMap* maps_dev, const int4* items_dev,
+                            int num_items, const int4* reduce_dev, int num_reduce, double* partials, int* err_flag,
+                            cudaStream_t s);
+int gram_fx3_rows_per_stage();
+int gram_fx3_a_cols();
+int gram_fx3_b_cols();
 // TMA needs a 16-byte aligned base and a row pitch that is a multiple of 16 bytes.
 bool tma_compatible_f32(const void* base, int64_t ld);
 bool tma_compatible_f64(const void* base, int64_t ld);

@@ -226,7 +226,8 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
 }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
-// (s, c) += y with Kahan compensation: c holds the rounding error of s.
+// (s, c) += y with Kahan compensation: c holds the rounding error committed by s
+// (the amount s exceeds the exact running sum), so the compensated sum is s - c.
 __device__ __forceinline__ void kahan_acc(float& s, float& c, float y) {
   const float yc = y - c;
   const float t = s + yc;

@@ -40,8 +40,9 @@ HAPOD_FP64 = 0
 HAPOD_MIXED_TF32X3 = 1
 HAPOD_FP64_OZAKI = 2
 HAPOD_MIXED_BF16X3 = 3
+HAPOD_MIXED_FX3 = 4
 DTYPE = {HAPOD_FP64: torch.float64, HAPOD_MIXED_TF32X3: torch.float32, HAPOD_FP64_OZAKI: torch.float64,
-         HAPOD_MIXED_BF16X3: torch.float32}
+         HAPOD_MIXED_BF16X3: torch.float32, HAPOD_MIXED_FX3: torch.float32}
 
 
 class hapod_tree(ctypes.Structure):

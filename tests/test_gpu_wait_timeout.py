@@ -32,6 +32,7 @@ CHILD = textwrap.dedent("""
     calls = {
         "gram_bf16x3": lambda: H.hapod_gram(X32, H.HAPOD_MIXED_BF16X3),
         "gram_tf32x3": lambda: H.hapod_gram(X32, H.HAPOD_MIXED_TF32X3),
+        "gram_fixed3": lambda: H.hapod_gram(X32, H.HAPOD_MIXED_FX3),
         "gram_digit_slice": lambda: H.hapod_gram(X64, H.HAPOD_FP64_OZAKI),
         "modes_digit_slice": lambda: H.hapod_modes(X64, V, 12, None, H.HAPOD_FP64_OZAKI),
     }
@@ -47,7 +48,7 @@ CHILD = textwrap.dedent("""
     del os.environ["HAPOD_DEBUG_WAIT_CYCLES"]
     G_ref = (X32.double().t() @ X32.double())
     d = torch.sqrt(torch.diag(G_ref))
-    for name in ("gram_bf16x3", "gram_tf32x3"):
+    for name in ("gram_bf16x3", "gram_tf32x3", "gram_fixed3"):
         G = calls[name]()
         err = float(torch.max(torch.abs(G - G_ref) / torch.outer(d, d)))
         assert err <= 1e-5, (name, err)
@@ -72,6 +73,6 @@ def test_bounded_wait_times_out_and_the_context_recovers(cuda_ok):
     print(r.stdout)
     print(r.stderr[-3000:])
     assert r.returncode == 0
-    for name in ("gram_bf16x3", "gram_tf32x3", "gram_digit_slice", "modes_digit_slice"):
+    for name in ("gram_bf16x3", "gram_tf32x3", "gram_fixed3", "gram_digit_slice", "modes_digit_slice"):
         assert f"TIMEOUT {name}" in r.stdout
     assert "RECOVERED" in r.stdout
