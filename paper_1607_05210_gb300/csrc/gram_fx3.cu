@@ -52,19 +52,21 @@ namespace hapod {
 namespace {
 
 constexpr int kRows = 32;                              // rows per stage (K of two MMAs)
-constexpr int kBlockStages = 2;                        // stages per exponent block (64 rows)
+constexpr int kBlockStagesDiag = 4;                    // stages per exponent block, B inside A (128 rows)
+constexpr int kBlockStagesOff = 2;                     // stages per exponent block, separate B (64 rows)
 constexpr int kACols = 128;
 constexpr int kBCols = 64;
 constexpr int kStA = kRows * kACols * 4;               // FP32 staging of the A panel, 16 KB
 constexpr int kStB = kRows * kBCols * 4;               // 8 KB
 constexpr int kStSlot = kStA + kStB;
-constexpr int kStSlots = 4;                            // two blocks in flight
+constexpr int kStRegion = 128 * 1024;                  // staging ring: two blocks in flight
+constexpr int kStSlotsMax = kStRegion / kStA;          // 8 (B inside A) or kStRegion / kStSlot = 4
 constexpr int kPlaneA = kRows * kACols * 2;            // one digit plane of A, 8 KB
 constexpr int kPlaneB = kRows * kBCols * 2;            // 4 KB
 constexpr int kOpSlot = 3 * kPlaneA + 3 * kPlaneB;     // 36 KB
 constexpr int kOpSlots = 2;
 constexpr int kExpSlots = 2;
-constexpr int kSmemBytes = kStSlots * kStSlot + kOpSlots * kOpSlot + 1024;
+constexpr int kSmemBytes = kStRegion + kOpSlots * kOpSlot + 1024;
 constexpr int kThreads = 576;
 constexpr int kConvThreads = 256;
 constexpr int kFirstFlushWarp = 10;
@@ -77,8 +79,8 @@ constexpr int kExpBad = 4000;                          // exponent marking Inf /
 static_assert(kSmemBytes <= 227 * 1024, "shared memory");
 
 struct Bars {
-  uint64_t full[kStSlots];     // TMA -> converters
-  uint64_t st_free[kStSlots];  // converters -> TMA
+  uint64_t full[kStSlotsMax];     // TMA -> converters
+  uint64_t st_free[kStSlotsMax];  // converters -> TMA
   uint64_t op_full[kOpSlots];  // converters -> issuer
   uint64_t op_free[kOpSlots];  // issuer (MMA completion) -> converters
   uint64_t exp_full[kExpSlots];  // converters -> flushers: block exponents written
@@ -106,19 +108,16 @@ __device__ __forceinline__ int exp_of_max(float mx) {
 }
 
 // Three balanced base-256 digits of rint(x 2^(23 - E)) (as floats holding integers in
-// [-128, 128]), by round-to-nearest splits with the constants 1.5 2^39, 1.5 2^31 and
-// 1.5 2^23, whose FP32 ulps are 2^16, 2^8 and 1: adding and subtracting one rounds to
-// that multiple, and every remainder is exact in FP32.
+// [-128, 128]): each digit is a round to nearest by adding and subtracting 1.5 2^23
+// (whose FP32 ulp is 1) after a power-of-two scaling; the remainders are exact.
 __device__ __forceinline__ void digits3(float x, float s1, float s2, float& d1, float& d2, float& d3) {
-  const float a = (x * s1) * s2;  // |a| < 2^23, exact (power-of-two scaling)
-  const float h1 = (a + 824633720832.0f) - 824633720832.0f;  // 1.5 2^39 (ulp 2^16): rint to a multiple of 2^16
-  const float r1 = a - h1;                                   // |r1| <= 2^15, exact
-  const float h2 = (r1 + 3221225472.0f) - 3221225472.0f;     // 1.5 2^31 (ulp 2^8): rint to a multiple of 2^8
-  const float r2 = r1 - h2;                                  // |r2| <= 2^7, exact
-  const float h3 = (r2 + 12582912.0f) - 12582912.0f;         // 1.5 2^23 (ulp 1): rint
-  d1 = h1 * (1.0f / 65536.0f);
-  d2 = h2 * (1.0f / 256.0f);
-  d3 = h3;
+  const float C = 12582912.0f;                       // 1.5 2^23 (ulp 1): (y + C) - C = rint(y), |y| < 2^22
+  const float a = (x * s1) * s2;                     // |a| < 2^23, exact (power-of-two scaling)
+  d1 = __fadd_rn(__fmaf_rn(a, 1.0f / 65536.0f, C), -C);  // rint(a 2^-16), |d1| <= 128
+  const float r1 = __fmaf_rn(d1, -65536.0f, a);      // |r1| <= 2^15, exact
+  d2 = __fadd_rn(__fmaf_rn(r1, 1.0f / 256.0f, C), -C);   // rint(r1 2^-8)
+  const float r2 = __fmaf_rn(d2, -256.0f, r1);       // |r2| <= 2^7, exact
+  d3 = __fadd_rn(__fadd_rn(r2, C), -C);              // rint(r2)
 }
 
 __device__ __forceinline__ uint32_t h2bits(float lo, float hi) {
@@ -139,10 +138,12 @@ __device__ __forceinline__ void scales(int E, float& s1, float& s2) {
   s2 = ldexpf(1.0f, e - e1);
 }
 
-// Convert the unit (column c of a panel of `cols` columns, row octet g) of one stage:
-// 8 values from the 128-byte-swizzled staging, three fp16 digit planes out.
-__device__ __forceinline__ void convert_unit(const uint8_t* __restrict__ st, uint8_t* __restrict__ planes,
-                                             uint32_t plane_bytes, int c, int g, float s1, float s2) {
+// Convert the unit (column c of the staged panel, row octet g) of one stage: 8 values
+// from the 128-byte-swizzled staging, three fp16 digit planes out at column dc, and
+// again at column dc2 of the second plane set `planes2` when that is not null.
+__device__ __forceinline__ void convert_unit(const uint8_t* __restrict__ st, int c, uint8_t* __restrict__ planes,
+                                             uint32_t plane_bytes, int dc, uint8_t* __restrict__ planes2,
+                                             uint32_t plane_bytes2, int dc2, int g, float s1, float s2) {
   const float4 v0 = *reinterpret_cast<const float4*>(st + c * 128 + (((2 * g) ^ (c & 7)) << 4));
   const float4 v1 = *reinterpret_cast<const float4*>(st + c * 128 + (((2 * g + 1) ^ (c & 7)) << 4));
   const float x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
@@ -156,10 +157,19 @@ __device__ __forceinline__ void convert_unit(const uint8_t* __restrict__ st, uin
     w2[i] = h2bits(a2, b2);
     w3[i] = h2bits(a3, b3);
   }
-  const uint32_t off = (uint32_t)(c >> 3) * kSbo + (uint32_t)g * kLbo + (uint32_t)(c & 7) * 16;
-  *reinterpret_cast<uint4*>(planes + off) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
-  *reinterpret_cast<uint4*>(planes + plane_bytes + off) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
-  *reinterpret_cast<uint4*>(planes + 2 * plane_bytes + off) = make_uint4(w3[0], w3[1], w3[2], w3[3]);
+  const uint4 p1 = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+  const uint4 p2 = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+  const uint4 p3 = make_uint4(w3[0], w3[1], w3[2], w3[3]);
+  const uint32_t off = (uint32_t)(dc >> 3) * kSbo + (uint32_t)g * kLbo + (uint32_t)(dc & 7) * 16;
+  *reinterpret_cast<uint4*>(planes + off) = p1;
+  *reinterpret_cast<uint4*>(planes + plane_bytes + off) = p2;
+  *reinterpret_cast<uint4*>(planes + 2 * plane_bytes + off) = p3;
+  if (planes2) {
+    const uint32_t off2 = (uint32_t)(dc2 >> 3) * kSbo + (uint32_t)g * kLbo + (uint32_t)(dc2 & 7) * 16;
+    *reinterpret_cast<uint4*>(planes2 + off2) = p1;
+    *reinterpret_cast<uint4*>(planes2 + plane_bytes2 + off2) = p2;
+    *reinterpret_cast<uint4*>(planes2 + 2 * plane_bytes2 + off2) = p3;
+  }
 }
 
 // Round-to-nearest arithmetic right shift of a signed 64-bit value (sh >= 0).
@@ -188,17 +198,23 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int64_t r0 = (int64_t)sp * J.rows_per_split;
   const int64_t r1 = min(J.n, r0 + J.rows_per_split);
   const int nst = r1 > r0 ? (int)((r1 - r0 + kRows - 1) / kRows) : 0;
+  // a tile whose B columns lie inside its A panel stages only the A panel (16 KB per
+  // stage, 8 slots) and takes exponent blocks of 128 rows; otherwise A and B (24 KB per
+  // stage, 4 slots) and blocks of 64 rows.  Level sums stay below 128 * 3 * 2^14 < 2^24.
+  const int kBlockStages = b_in_a ? kBlockStagesDiag : kBlockStagesOff;
+  const int kStSlots = b_in_a ? kStRegion / kStA : kStRegion / kStSlot;
+  const int st_bytes = b_in_a ? kStA : kStSlot;
   const int nblk = (nst + kBlockStages - 1) / kBlockStages;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const tc::WaitBudget wb = tc::wait_budget(err);
-  auto st_a = [&](int s) -> uint8_t* { return smem + (size_t)s * kStSlot; };
-  auto st_b = [&](int s) -> uint8_t* { return smem + (size_t)s * kStSlot + kStA; };
-  uint8_t* op_ring = smem + (size_t)kStSlots * kStSlot;
+  auto st_a = [&](int s) -> uint8_t* { return smem + (size_t)s * st_bytes; };
+  auto st_b = [&](int s) -> uint8_t* { return smem + (size_t)s * st_bytes + kStA; };
+  uint8_t* op_ring = smem + (size_t)kStRegion;
   auto op_a = [&](int t) -> uint8_t* { return op_ring + (size_t)t * kOpSlot; };
   auto op_b = [&](int t) -> uint8_t* { return op_ring + (size_t)t * kOpSlot + 3 * kPlaneA; };
 
   if (tid == 0) {
-    for (int s = 0; s < kStSlots; ++s) {
+    for (int s = 0; s < kStSlotsMax; ++s) {
       tc::mbar_init(&bars.full[s], 1);
       tc::mbar_init(&bars.st_free[s], 8);
     }
@@ -348,15 +364,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int c = u & (kACols - 1), g = u >> 7;
           float s1, s2;
           scales(sh.exps[es][c], s1, s2);
-          convert_unit(st_a(s), op_a(t), kPlaneA, c, g, s1, s2);
-          if (b_in_a && c >= b0 - a0 && c < b0 - a0 + kBCols)
-            convert_unit(st_a(s), op_b(t), kPlaneB, c - (b0 - a0), g, s1, s2);
+          const bool dup = b_in_a && c >= b0 - a0 && c < b0 - a0 + kBCols;  // also a B column
+          convert_unit(st_a(s), c, op_a(t), kPlaneA, c, dup ? op_b(t) : nullptr, kPlaneB, c - (b0 - a0), g, s1, s2);
         }
         if (!b_in_a) {  // B panel: 64 columns x 4 octets = 256 units, one per thread
           const int c = ct & (kBCols - 1), g = ct >> 6;
           float s1, s2;
           scales(sh.exps[es][kACols + c], s1, s2);
-          convert_unit(st_b(s), op_b(t), kPlaneB, c, g, s1, s2);
+          convert_unit(st_b(s), c, op_b(t), kPlaneB, c, nullptr, 0, 0, g, s1, s2);
         }
         tc::fence_async_smem();
         __syncwarp();
@@ -399,6 +414,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int below_i = vi ? Rinew - Ei : 64;
       Ri = Rinew;
       Rj_l = Rjnew_l;
+      // the common case, warp-uniform: nothing to shift for any entry of the warp
+      const bool plain = __all_sync(0xffffffffu, grow_l == 0 && below_l == 0 && grow_i == 0 && below_i == 0);
 #pragma unroll
       for (int g = 0; g < 4; ++g) {  // 8 columns at a time
         const uint32_t col = (uint32_t)set * kSetCols + (uint32_t)(32 * h + 8 * g);
@@ -413,14 +430,16 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           const int jj = 8 * g + i;  // column within the warp's 32
-          const int grow = grow_i + __shfl_sync(0xffffffffu, grow_l, jj);
-          const int below = below_i + __shfl_sync(0xffffffffu, below_l, jj);
-          if (grow > 0) acc[jj] = rshift_rn(acc[jj], grow);  // the unit of the sum grew
-          if (below < 64) {
-            const long long v = (long long)__float2int_rn(__uint_as_float(l2[i])) * 65536LL +
-                                (long long)__float2int_rn(__uint_as_float(l3[i])) * 256LL +
-                                (long long)__float2int_rn(__uint_as_float(l4[i]));
-            acc[jj] += rshift_rn(v, below);
+          const long long v = (long long)__float2int_rn(__uint_as_float(l2[i])) * 65536LL +
+                              (long long)__float2int_rn(__uint_as_float(l3[i])) * 256LL +
+                              (long long)__float2int_rn(__uint_as_float(l4[i]));
+          if (plain) {  // no exponent moved and every block exponent is the running one
+            acc[jj] += v;
+          } else {
+            const int grow = grow_i + __shfl_sync(0xffffffffu, grow_l, jj);
+            const int below = below_i + __shfl_sync(0xffffffffu, below_l, jj);
+            if (grow > 0) acc[jj] = rshift_rn(acc[jj], grow);  // the unit of the sum grew
+            if (below < 64) acc[jj] += rshift_rn(v, below);
           }
         }
       }

@@ -9,7 +9,7 @@ Tolerances, derived from the arithmetic of gram_fx3.cu:
     2^(E_i + E_j - 23) + 2^(E_i + E_j - 32) per row; the level sums are exact
     integers and the int64 sums lose at most half a unit of 2^(R_i + R_j - 30) per
     shift.  Per row: |x_i x_j - p| <= (2^-24 + 2^-24 + 2^-23 + 2^-31) 2^(E_i + E_j)
-    <= 2^-20 M_i^b M_j^b, so |G - G_ref| <= 2^-20 sum_b 64 M_i^b M_j^b + the oracle's
+    <= 2^-20 M_i^b M_j^b, so |G - G_ref| <= 2^-20 sum_r M_i^b(r) M_j^b(r) + the oracle's
     FP64 rounding (1e-13 sqrt(n) sqrt(G_ii G_jj)).
   * exact case: small integers are represented exactly and every sum is an exact
     integer, so G equals the oracle's bit for bit.
@@ -47,13 +47,18 @@ def _gram(H, X, ld=None):
 
 
 def _block_bound(X):
-    """2^-20 sum_b 64 M_i^b M_j^b over the 64-row blocks."""
+    """2^-20 sum_r M_i(r) M_j(r), M(r) the maximum of |x| over the exponent block that
+    holds row r: blocks of 64 or 128 rows starting at a multiple of 64 rows, so within
+    the 64-row blocks b - 1, b, b + 1 around r."""
     n, m = X.shape
     nb = (n + 63) // 64
     Xp = np.zeros((nb * 64, m))
     Xp[:n] = np.abs(X)
-    M = Xp.reshape(nb, 64, m).max(axis=1)  # nb x m block maxima
-    return 2.0 ** -20 * 64 * (M.T @ M)
+    M = Xp.reshape(nb, 64, m).max(axis=1)  # nb x m maxima of the 64-row blocks
+    Mn = M.copy()
+    Mn[1:] = np.maximum(Mn[1:], M[:-1])
+    Mn[:-1] = np.maximum(Mn[:-1], M[1:])
+    return 2.0 ** -20 * 64 * (Mn.T @ Mn)
 
 
 @pytest.mark.parametrize("n,m,ld,kind", [(1000, 1, 1000, "gauss"), (10000, 100, 10000, "gauss"),
