@@ -10,31 +10,32 @@
 //
 // Digits: the rows are taken in blocks of 64.  In block b every column j gets the
 // exponent E = E_j^b with max_r |x_rj| < 2^E (computed in the kernel from the block
-// in shared memory), and every value becomes the 24-bit integer A = rint(x 2^(23-E))
-// (|A| <= 2^23) written as three balanced base-256 digits A = d1 2^16 + d2 2^8 + d3,
-// d2, d3 in [-128, 128], |d1| <= 128 (round to nearest at each step, so the pieces
-// are unbiased); the representation error is at most 2^(E-24).
-// Products: x_i x_j = 2^(E_i+E_j-46) sum_{t,u} d_t d_u 2^(48-8(t+u)); the levels
-// s = t + u = 2, 3, 4 are kept (six digit pairs; the dropped ones weigh at most
-// 2^(E_i+E_j-22) per row), each level summed over the block on the tensor cores:
-// L_s <= 64 * 3 * 2^14 < 2^24, an integer the FP32 accumulator holds exactly.
-// Flush: after each block, v = L_2 2^16 + L_3 2^8 + L_4 (exact, < 2^41) is added
-// into an int64 fixed-point sum per entry whose unit is 2^(R_i+R_j-30), R the running
-// maximum of the block exponents (rounding shift; the sum is shifted down when R
-// grows).  The item writes ldexp(sum, R_i + R_j - 30) in FP64 -- one rounding -- and
-// row splits are summed in FP64 in a fixed order.  Columns holding Inf or NaN give
-// NaN rows and columns of G.
+// in shared memory), and every value becomes the 32-bit integer A = rint(x 2^(31-E))
+// written as four balanced base-256 digits A = d1 2^24 + d2 2^16 + d3 2^8 + d4,
+// |d_t| <= 128 (round to nearest at each step, so the pieces are unbiased).  The
+// representation error is at most 2^(E-32): every FP32 value within 2^8 of its
+// block maximum is represented exactly.
+// Products: x_i x_j = 2^(E_i+E_j-62) sum_{t,u} d_t d_u 2^(8(8-t-u)); the levels
+// s = t + u = 2..5 are kept (ten digit pairs; the dropped ones weigh less than
+// 2^(E_i+E_j-30.4) per row), each level summed over the block on the tensor cores:
+// L_s <= 64 * 4 * 2^14 = 2^22, an integer the FP32 accumulator holds exactly.
+// Flush: after each block, v = L_2 2^24 + L_3 2^16 + L_4 2^8 + L_5 (exact, < 2^45) is
+// added into an int64 fixed-point sum per entry whose unit is 2^(R_i+R_j-38), R the
+// running maximum of the block exponents (rounding shift; the sum is shifted down
+// when R grows).  The item writes ldexp(sum, R_i + R_j - 38) in FP64 -- one rounding
+// -- and row splits are summed in FP64 in a fixed order.  Columns holding Inf or NaN
+// give NaN rows and columns of G.
 //
 // Work item = one 128 x 64 tile (A columns 128 I.., B columns 64 J.., J >= 2 I) of
 // one node's G over one row split; items are ordered by split first.  One CTA per
 // item, 18 warps:
 //   warp 0        TMA producer: FP32 blocks of 32 rows x 128 A columns (and 64 B
 //                 columns when they are not inside the A panel), 128-byte swizzled,
-//                 4 stages deep
-//   warp 1        TMEM owner and single-thread MMA issuer: per 16 rows three MMAs,
-//                 d1 (A) against [d1 d2 d3] (B, N = 192) into the level accumulators
-//                 L2 | L3 | L4, d2 against [d1 d2] (N = 128) into L3 | L4, d3 against
-//                 d1 (N = 64) into L4; two accumulator sets alternate between blocks
+//                 6 (A only) or 4 stages deep
+//   warp 1        TMEM owner and single-thread MMA issuer: per 16 rows four MMAs,
+//                 digit t of A against the B digits 1 .. 5 - t (consecutive planes,
+//                 N = 64 (5 - t)) into the adjacent level accumulators L_{t+1} .. L_5;
+//                 two accumulator sets (2 x 256 TMEM columns) alternate between blocks
 //   warps 2..9    converters: block column maxima, exponents, digits (K-major 8 x 8
 //                 core matrices, no swizzle), 2 stages deep
 //   warps 10..17  flushers: int64 sums of 32 entries per thread
@@ -52,18 +53,19 @@ namespace hapod {
 namespace {
 
 constexpr int kRows = 32;                              // rows per stage (K of two MMAs)
-constexpr int kBlockStagesDiag = 4;                    // stages per exponent block, B inside A (128 rows)
+constexpr int kBlockStagesDiag = 2;                    // stages per exponent block, B inside A (64 rows)
 constexpr int kBlockStagesOff = 2;                     // stages per exponent block, separate B (64 rows)
 constexpr int kACols = 128;
 constexpr int kBCols = 64;
 constexpr int kStA = kRows * kACols * 4;               // FP32 staging of the A panel, 16 KB
 constexpr int kStB = kRows * kBCols * 4;               // 8 KB
 constexpr int kStSlot = kStA + kStB;
-constexpr int kStRegion = 128 * 1024;                  // staging ring: two blocks in flight
-constexpr int kStSlotsMax = kStRegion / kStA;          // 8 (B inside A) or kStRegion / kStSlot = 4
+constexpr int kStRegion = 96 * 1024;                   // staging ring: two blocks in flight
+constexpr int kStSlotsMax = kStRegion / kStA;          // 6 (B inside A) or kStRegion / kStSlot = 4
 constexpr int kPlaneA = kRows * kACols * 2;            // one digit plane of A, 8 KB
 constexpr int kPlaneB = kRows * kBCols * 2;            // 4 KB
-constexpr int kOpSlot = 3 * kPlaneA + 3 * kPlaneB;     // 36 KB
+constexpr int kDigits = 4;
+constexpr int kOpSlot = kDigits * (kPlaneA + kPlaneB);  // 48 KB
 constexpr int kOpSlots = 2;
 constexpr int kExpSlots = 2;
 constexpr int kSmemBytes = kStRegion + kOpSlots * kOpSlot + 1024;
@@ -73,7 +75,7 @@ constexpr int kFirstFlushWarp = 10;
 constexpr uint32_t kLbo = 128;                         // next core matrix along K (8 rows)
 constexpr uint32_t kSbo = (kRows / 8) * 128;           // next core matrix along M / N (8 columns)
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kSetCols = 256;                     // one set of L2 | L3 | L4 (192 used)
+constexpr uint32_t kSetCols = 256;                     // one set of L2 | L3 | L4 | L5
 constexpr int kExpZero = -4000;                        // exponent of an all-zero column block
 constexpr int kExpBad = 4000;                          // exponent marking Inf / NaN
 static_assert(kSmemBytes <= 227 * 1024, "shared memory");
@@ -107,17 +109,19 @@ __device__ __forceinline__ int exp_of_max(float mx) {
   return e;
 }
 
-// Three balanced base-256 digits of rint(x 2^(23 - E)) (as floats holding integers in
+// Four balanced base-256 digits of rint(x 2^(31 - E)) (as floats holding integers in
 // [-128, 128]): each digit is a round to nearest by adding and subtracting 1.5 2^23
 // (whose FP32 ulp is 1) after a power-of-two scaling; the remainders are exact.
-__device__ __forceinline__ void digits3(float x, float s1, float s2, float& d1, float& d2, float& d3) {
-  const float C = 12582912.0f;                       // 1.5 2^23 (ulp 1): (y + C) - C = rint(y), |y| < 2^22
-  const float a = (x * s1) * s2;                     // |a| < 2^23, exact (power-of-two scaling)
-  d1 = __fadd_rn(__fmaf_rn(a, 1.0f / 65536.0f, C), -C);  // rint(a 2^-16), |d1| <= 128
-  const float r1 = __fmaf_rn(d1, -65536.0f, a);      // |r1| <= 2^15, exact
-  d2 = __fadd_rn(__fmaf_rn(r1, 1.0f / 256.0f, C), -C);   // rint(r1 2^-8)
-  const float r2 = __fmaf_rn(d2, -256.0f, r1);       // |r2| <= 2^7, exact
-  d3 = __fadd_rn(__fadd_rn(r2, C), -C);              // rint(r2)
+__device__ __forceinline__ void digits4(float x, float s1, float s2, float (&d)[4]) {
+  const float C = 12582912.0f;                        // 1.5 2^23 (ulp 1): (y + C) - C = rint(y), |y| < 2^22
+  const float a = (x * s1) * s2;                      // |a| < 2^31, exact (power-of-two scaling)
+  d[0] = __fadd_rn(__fmaf_rn(a, 1.0f / 16777216.0f, C), -C);  // rint(a 2^-24), |d1| <= 128
+  const float r1 = __fmaf_rn(d[0], -16777216.0f, a);  // |r1| <= 2^23, exact
+  d[1] = __fadd_rn(__fmaf_rn(r1, 1.0f / 65536.0f, C), -C);
+  const float r2 = __fmaf_rn(d[1], -65536.0f, r1);    // |r2| <= 2^15, exact
+  d[2] = __fadd_rn(__fmaf_rn(r2, 1.0f / 256.0f, C), -C);
+  const float r3 = __fmaf_rn(d[2], -256.0f, r2);      // |r3| <= 2^7, exact
+  d[3] = __fadd_rn(__fadd_rn(r3, C), -C);
 }
 
 __device__ __forceinline__ uint32_t h2bits(float lo, float hi) {
@@ -125,21 +129,21 @@ __device__ __forceinline__ uint32_t h2bits(float lo, float hi) {
   return *reinterpret_cast<const uint32_t*>(&v);
 }
 
-// Scale factors s1 s2 = 2^(23 - E) (two factors so that both stay in range).
+// Scale factors s1 s2 = 2^(31 - E) (two factors so that both stay in range).
 __device__ __forceinline__ void scales(int E, float& s1, float& s2) {
   if (E <= kExpZero || E >= kExpBad) {
     s1 = 0.f;
     s2 = 0.f;
     return;
   }
-  const int e = 23 - E;  // in [-105, 172]
+  const int e = 31 - E;  // in [-97, 180]
   const int e1 = max(-126, min(127, e));
   s1 = ldexpf(1.0f, e1);
   s2 = ldexpf(1.0f, e - e1);
 }
 
 // Convert the unit (column c of the staged panel, row octet g) of one stage: 8 values
-// from the 128-byte-swizzled staging, three fp16 digit planes out at column dc, and
+// from the 128-byte-swizzled staging, four fp16 digit planes out at column dc, and
 // again at column dc2 of the second plane set `planes2` when that is not null.
 __device__ __forceinline__ void convert_unit(const uint8_t* __restrict__ st, int c, uint8_t* __restrict__ planes,
                                              uint32_t plane_bytes, int dc, uint8_t* __restrict__ planes2,
@@ -147,28 +151,24 @@ __device__ __forceinline__ void convert_unit(const uint8_t* __restrict__ st, int
   const float4 v0 = *reinterpret_cast<const float4*>(st + c * 128 + (((2 * g) ^ (c & 7)) << 4));
   const float4 v1 = *reinterpret_cast<const float4*>(st + c * 128 + (((2 * g + 1) ^ (c & 7)) << 4));
   const float x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-  uint32_t w1[4], w2[4], w3[4];
+  uint32_t w[kDigits][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    float a1, a2, a3, b1, b2, b3;
-    digits3(x[2 * i], s1, s2, a1, a2, a3);
-    digits3(x[2 * i + 1], s1, s2, b1, b2, b3);
-    w1[i] = h2bits(a1, b1);
-    w2[i] = h2bits(a2, b2);
-    w3[i] = h2bits(a3, b3);
+    float da[kDigits], db[kDigits];
+    digits4(x[2 * i], s1, s2, da);
+    digits4(x[2 * i + 1], s1, s2, db);
+#pragma unroll
+    for (int t = 0; t < kDigits; ++t) w[t][i] = h2bits(da[t], db[t]);
   }
-  const uint4 p1 = make_uint4(w1[0], w1[1], w1[2], w1[3]);
-  const uint4 p2 = make_uint4(w2[0], w2[1], w2[2], w2[3]);
-  const uint4 p3 = make_uint4(w3[0], w3[1], w3[2], w3[3]);
   const uint32_t off = (uint32_t)(dc >> 3) * kSbo + (uint32_t)g * kLbo + (uint32_t)(dc & 7) * 16;
-  *reinterpret_cast<uint4*>(planes + off) = p1;
-  *reinterpret_cast<uint4*>(planes + plane_bytes + off) = p2;
-  *reinterpret_cast<uint4*>(planes + 2 * plane_bytes + off) = p3;
+#pragma unroll
+  for (int t = 0; t < kDigits; ++t)
+    *reinterpret_cast<uint4*>(planes + t * plane_bytes + off) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
   if (planes2) {
     const uint32_t off2 = (uint32_t)(dc2 >> 3) * kSbo + (uint32_t)g * kLbo + (uint32_t)(dc2 & 7) * 16;
-    *reinterpret_cast<uint4*>(planes2 + off2) = p1;
-    *reinterpret_cast<uint4*>(planes2 + plane_bytes2 + off2) = p2;
-    *reinterpret_cast<uint4*>(planes2 + 2 * plane_bytes2 + off2) = p3;
+#pragma unroll
+    for (int t = 0; t < kDigits; ++t)
+      *reinterpret_cast<uint4*>(planes2 + t * plane_bytes2 + off2) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
   }
 }
 
@@ -199,8 +199,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int64_t r1 = min(J.n, r0 + J.rows_per_split);
   const int nst = r1 > r0 ? (int)((r1 - r0 + kRows - 1) / kRows) : 0;
   // a tile whose B columns lie inside its A panel stages only the A panel (16 KB per
-  // stage, 8 slots) and takes exponent blocks of 128 rows; otherwise A and B (24 KB per
-  // stage, 4 slots) and blocks of 64 rows.  Level sums stay below 128 * 3 * 2^14 < 2^24.
+  // stage, 6 slots); otherwise A and B (24 KB per stage, 4 slots).
   const int kBlockStages = b_in_a ? kBlockStagesDiag : kBlockStagesOff;
   const int kStSlots = b_in_a ? kStRegion / kStA : kStRegion / kStSlot;
   const int st_bytes = b_in_a ? kStA : kStSlot;
@@ -211,7 +210,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   auto st_b = [&](int s) -> uint8_t* { return smem + (size_t)s * st_bytes + kStA; };
   uint8_t* op_ring = smem + (size_t)kStRegion;
   auto op_a = [&](int t) -> uint8_t* { return op_ring + (size_t)t * kOpSlot; };
-  auto op_b = [&](int t) -> uint8_t* { return op_ring + (size_t)t * kOpSlot + 3 * kPlaneA; };
+  auto op_b = [&](int t) -> uint8_t* { return op_ring + (size_t)t * kOpSlot + kDigits * kPlaneA; };
 
   if (tid == 0) {
     for (int s = 0; s < kStSlotsMax; ++s) {
@@ -268,9 +267,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      const uint32_t id192 = tc::idesc_f16_f32_major(128, 192, 0, 0);
-      const uint32_t id128 = tc::idesc_f16_f32_major(128, 128, 0, 0);
-      const uint32_t id64 = tc::idesc_f16_f32_major(128, 64, 0, 0);
+      uint32_t idn[kDigits];
+#pragma unroll
+      for (int t = 0; t < kDigits; ++t) idn[t] = tc::idesc_f16_f32_major(128, (uint32_t)(kBCols * (kDigits - t)), 0, 0);
       for (int k = 0; k < nst; ++k) {
         const int t = k % kOpSlots;
         const int blk = k / kBlockStages;
@@ -287,15 +286,12 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int kk = 0; kk < kRows / 16; ++kk) {
           const uint32_t ko = (uint32_t)kk * 2 * kLbo;
-          const uint32_t acc = (blk_first && kk == 0) ? 0u : 1u;
-          // d1 x [d1 d2 d3] -> L2 | L3 | L4
-          tc::umma_f16(d, tc::ns_desc(pa + ko, kLbo, kSbo), tc::ns_desc(pb + ko, kLbo, kSbo), id192, acc);
-          // d2 x [d1 d2] -> L3 | L4
-          tc::umma_f16(d + kBCols, tc::ns_desc(pa + kPlaneA + ko, kLbo, kSbo), tc::ns_desc(pb + ko, kLbo, kSbo),
-                       id128, 1u);
-          // d3 x d1 -> L4
-          tc::umma_f16(d + 2 * kBCols, tc::ns_desc(pa + 2 * kPlaneA + ko, kLbo, kSbo),
-                       tc::ns_desc(pb + ko, kLbo, kSbo), id64, 1u);
+          // digit t of A against the B digits 1 .. 4 - t (consecutive planes, one
+          // operand of N = 64 (4 - t)) into the level accumulators L_{t+1} .. L_5
+#pragma unroll
+          for (int tt = 0; tt < kDigits; ++tt)
+            tc::umma_f16(d + (uint32_t)(kBCols * tt), tc::ns_desc(pa + (uint32_t)tt * kPlaneA + ko, kLbo, kSbo),
+                         tc::ns_desc(pb + ko, kLbo, kSbo), idn[tt], (blk_first && kk == 0 && tt == 0) ? 0u : 1u);
         }
         tc::umma_commit(&bars.op_free[t]);
         if (blk_last) tc::umma_commit(&bars.acc_full[set]);
@@ -419,20 +415,23 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int g = 0; g < 4; ++g) {  // 8 columns at a time
         const uint32_t col = (uint32_t)set * kSetCols + (uint32_t)(32 * h + 8 * g);
-        uint32_t l2[8], l3[8], l4[8];
+        uint32_t l2[8], l3[8], l4[8], l5[8];
         tc::tmem_ld8_raw(tbase + lanes + col, l2);
         tc::tmem_ld8_raw(tbase + lanes + col + kBCols, l3);
         tc::tmem_ld8_raw(tbase + lanes + col + 2 * kBCols, l4);
+        tc::tmem_ld8_raw(tbase + lanes + col + 3 * kBCols, l5);
         tc::tmem_wait_ld();
         tc::reg_barrier8(l2);
         tc::reg_barrier8(l3);
         tc::reg_barrier8(l4);
+        tc::reg_barrier8(l5);
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           const int jj = 8 * g + i;  // column within the warp's 32
-          const long long v = (long long)__float2int_rn(__uint_as_float(l2[i])) * 65536LL +
-                              (long long)__float2int_rn(__uint_as_float(l3[i])) * 256LL +
-                              (long long)__float2int_rn(__uint_as_float(l4[i]));
+          const long long v = (long long)__float2int_rn(__uint_as_float(l2[i])) * 16777216LL +
+                              (long long)__float2int_rn(__uint_as_float(l3[i])) * 65536LL +
+                              (long long)__float2int_rn(__uint_as_float(l4[i])) * 256LL +
+                              (long long)__float2int_rn(__uint_as_float(l5[i]));
           if (plain) {  // no exponent moved and every block exponent is the running one
             acc[jj] += v;
           } else {
@@ -470,7 +469,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         else if (Ri <= kExpZero || Rj <= kExpZero)
           v = 0.0;
         else
-          v = ldexp((double)acc[jj], Ri + Rj - 30);
+          v = ldexp((double)acc[jj], Ri + Rj - 38);
         if (out) {
           out[(size_t)ai * kBCols + bj] = v;
         } else if (gi < J.m && gj < J.m && gj >= gi) {
