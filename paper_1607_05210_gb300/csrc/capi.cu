@@ -693,14 +693,9 @@ bool step_gram(Env& env, int precision, std::vector<Work*>& ws) {
   return ok;
 }
 
-// Eigensolver variant of a form: FP64 rotations (FP64 forms), FP32 rotations (mixed
-// TF32 form), or FP32 sweeps followed by FP64 sweeps to the FP64 stopping rule
-// (mixed split-BF16 form).
-int eig_mode(int precision) {
-  return precision == HAPOD_MIXED_TF32X3                                      ? kEigF32
-         : (precision == HAPOD_MIXED_BF16X3 || precision == HAPOD_MIXED_FX3) ? kEigF32F64
-                                                                              : kEigF64;
-}
+// Eigensolver variant of a form: FP32 rotations for the mixed TF32 form, FP64 rotations
+// for every other form.
+int eig_mode(int precision) { return precision == HAPOD_MIXED_TF32X3 ? kEigF32 : kEigF64; }
 // Relative level of a form's Gram error (the pivoted Cholesky does not factor below it).
 double gram_floor_rel(int precision) {
   return precision == HAPOD_MIXED_BF16X3 ? 1e-10 : precision == HAPOD_MIXED_FX3 ? 1e-13 : 0.0;
@@ -1175,7 +1170,11 @@ bool run_batch(hapod_ctx* c, const std::vector<int>& batch) {
   if (ok && root_work) {
     NodeRT& R = c->nodes[root_node];
     bool deficient = false;
+    // the fixed-point form keeps the eigensolver's singular values (FP64 eigenvalues of a
+    // Gram matrix exact to the representation of the data); CholQR2 orthonormalises U
+    std::vector<double> sig_keep = R.sigma;
     ok = root_cholqr2(env, c->precision, root_tmp, c->n, c->ldn, (int)R.k, c->result, R.sigma, &deficient);
+    if (c->precision == HAPOD_MIXED_FX3) R.sigma = sig_keep;
     if (ok && deficient) {
       R.status = HAPOD_WARN_BELOW_FLOOR;
       if (c->warning == HAPOD_OK) c->warning = HAPOD_WARN_BELOW_FLOOR;

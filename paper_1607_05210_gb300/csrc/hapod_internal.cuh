@@ -242,11 +242,9 @@ struct EigJob {
   int32_t m;
   int32_t pad;
 };
-// Rotation precision: FP64 throughout; FP32 (V in FP32); FP32 sweeps to the FP32 stopping
-// rule followed by FP64 sweeps to the FP64 one (V in FP64).
+// Rotation precision: FP64 (V in FP64) or FP32 (V in FP32).
 constexpr int kEigF64 = 0;
 constexpr int kEigF32 = 1;
-constexpr int kEigF32F64 = 2;
 // One CTA per job; max_m sizes the dynamic shared memory (eig_smem_bytes).
 cudaError_t launch_eig(int mode, const EigJob* jobs_dev, int njobs, int max_m, int max_sweeps, cudaStream_t s);
 int eig_threads();

@@ -5,8 +5,9 @@
 //    G = L L^T + S, choosing at step k the largest remaining diagonal of the Schur
 //    complement S and stopping once trace(S) (the sum of its diagonal, S being PSD)
 //    is below min(tol * trace(G), 1e-2 eps^2) (tol * trace(G) without an eps),
-//    tol = the rounding level of the
-//    form's Gram (m 2^-53 for FP64, 1e-7 for the tensor-core form).  trace(S) is
+//    tol = m 2^-53 (FP64 rotations) or 1e-7 (FP32 rotations), but not below the
+//    form's Gram error level floor_rel * trace(G) (the remaining pivots would factor
+//    rounding noise).  trace(S) is
 //    returned as `resid` and added to every tail of the truncation, so the dropped
 //    part is accounted for exactly: no eigenvalue of G exceeds that of L L^T by more
 //    than ||S|| <= trace(S).
@@ -21,8 +22,6 @@
 // eigensolve costs O(m r^2) per sweep instead of the O(m^3) of a Jacobi sweep on G.
 // Output: lambda descending (clamped >= 0, zero beyond r), V (T, m x m) with
 // column j = w_j / ||w_j|| for j < r and zero otherwise, perm = sorted order.
-#include <type_traits>
-
 #include "hapod_internal.cuh"
 
 namespace hapod {
@@ -174,13 +173,10 @@ __device__ int jacobi_sweeps(U* W, int m, int r, int max_sweeps, bool& converged
   return sweeps;
 }
 
-// T: precision of the first rotation phase.  POLISH: after it, the columns are
-// carried to FP64 (into the factor's buffer, no longer needed) and rotated in FP64
-// until the FP64 stopping rule holds; the eigenvectors are then FP64 (J.V holds
-// doubles).  Without POLISH the eigenvectors stay in T.
-template <typename T, bool POLISH>
+// T: precision of the rotations and of the eigenvectors.
+template <typename T>
 __global__ void __launch_bounds__(kThreads) chol_jacobi_kernel(const EigJob* __restrict__ jobs, int max_sweeps) {
-  typedef typename std::conditional<POLISH, double, T>::type V_t;  // element type of the eigenvectors
+  typedef T V_t;
   const EigJob J = jobs[blockIdx.x];
   const int m = J.m;
   if (m <= 0) return;
@@ -257,24 +253,13 @@ __global__ void __launch_bounds__(kThreads) chol_jacobi_kernel(const EigJob* __r
     }
   }
 
-  // ---------------- one-sided Jacobi on the r columns (precision T, then FP64 if POLISH)
+  // ---------------- one-sided Jacobi on the r columns (precision T)
   for (size_t e = tid; e < (size_t)r * m; e += blockDim.x) W[e] = (T)L[e];
   __syncthreads();
   bool converged = false;
-  int sweeps = jacobi_sweeps<T>(W, m, r, max_sweeps, converged, &flag_sh);
-  V_t* U = reinterpret_cast<V_t*>(J.V);
-  if (POLISH) {
-    // the FP32 columns move to FP64 in the factor's buffer, are rotated there to the
-    // FP64 stopping rule, and land in J.V (FP64)
-    for (size_t e = tid; e < (size_t)r * m; e += blockDim.x) L[e] = (double)W[e];
-    __syncthreads();
-    bool conv64 = false;
-    sweeps += jacobi_sweeps<double>(L, m, r, max_sweeps, conv64, &flag_sh);
-    converged = conv64;
-    for (size_t e = tid; e < (size_t)m * m; e += blockDim.x) U[e] = (V_t)(e < (size_t)r * m ? L[e] : 0.0);
-  } else {
-    for (size_t e = (size_t)r * m + tid; e < (size_t)m * m; e += blockDim.x) U[e] = V_t(0);
-  }
+  const int sweeps = jacobi_sweeps<T>(W, m, r, max_sweeps, converged, &flag_sh);
+  V_t* U = W;
+  for (size_t e = (size_t)r * m + tid; e < (size_t)m * m; e += blockDim.x) U[e] = V_t(0);
   __syncthreads();
 
   // ---------------- normalised eigenvectors u_j = w_j / ||w_j||, then FP64 Rayleigh
@@ -336,9 +321,8 @@ size_t eig_smem_bytes(int m) { return (size_t)m * (2 * sizeof(double) + 1) + 16;
 cudaError_t launch_eig(int mode, const EigJob* jobs_dev, int njobs, int max_m, int max_sweeps, cudaStream_t s) {
   if (njobs <= 0) return cudaSuccess;
   const size_t smem = eig_smem_bytes(max_m);
-  const void* fn = mode == kEigF64   ? (const void*)chol_jacobi_kernel<double, false>
-                   : mode == kEigF32 ? (const void*)chol_jacobi_kernel<float, false>
-                                     : (const void*)chol_jacobi_kernel<float, true>;
+  const void* fn =
+      mode == kEigF32 ? (const void*)chol_jacobi_kernel<float> : (const void*)chol_jacobi_kernel<double>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

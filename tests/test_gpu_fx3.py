@@ -1,16 +1,16 @@
-"""Mixed fixed-point form (FP32 snapshots; tcgen05 Gram from three balanced 8-bit
+"""Mixed fixed-point form (FP32 snapshots; tcgen05 Gram from four balanced 8-bit
 digits per value, fixed-point per column and 64-row block, integer-exact sums) versus
 the CPU FP64 oracle run on the same FP32 values.
 
 Tolerances, derived from the arithmetic of gram_fx3.cu:
-  * Gram: in block b (rows 64 b .. 64 b + 63) column j is represented as an integer
-    multiple of 2^(E_j - 23) with |x - x~| <= 2^(E_j - 24), 2^(E_j - 1) <= M_j^b < 2^E_j
-    (M the block maximum of |x|); the six kept digit pairs leave out at most
-    2^(E_i + E_j - 23) + 2^(E_i + E_j - 32) per row; the level sums are exact
-    integers and the int64 sums lose at most half a unit of 2^(R_i + R_j - 30) per
-    shift.  Per row: |x_i x_j - p| <= (2^-24 + 2^-24 + 2^-23 + 2^-31) 2^(E_i + E_j)
-    <= 2^-20 M_i^b M_j^b, so |G - G_ref| <= 2^-20 sum_r M_i^b(r) M_j^b(r) + the oracle's
-    FP64 rounding (1e-13 sqrt(n) sqrt(G_ii G_jj)).
+  * Gram: in a 64-row exponent block b column j is represented as an integer
+    multiple of 2^(E_j - 31) with |x - x~| <= 2^(E_j - 32), 2^(E_j - 1) <= M_j^b < 2^E_j
+    (M the block maximum of |x|); the ten kept digit pairs (levels 2..5) leave out
+    less than 2^(E_i + E_j - 30.4) per row; the level sums are exact integers and the
+    int64 sums lose at most half a unit of 2^(R_i + R_j - 38) per shift.  Per row:
+    |x_i x_j - p| <= (2^-31 + 2^-30.4) 2^(E_i + E_j) <= 2^-27 M_i^b M_j^b, so
+    |G - G_ref| <= 2^-27 sum_r M_i^b(r) M_j^b(r) + the oracle's FP64 rounding
+    (1e-13 sqrt(n) sqrt(G_ii G_jj)).
   * exact case: small integers are represented exactly and every sum is an exact
     integer, so G equals the oracle's bit for bit.
   * the precision workload's leaf tolerance (eps = 1e-4 rel, quaternary tree of depth
@@ -47,9 +47,9 @@ def _gram(H, X, ld=None):
 
 
 def _block_bound(X):
-    """2^-20 sum_r M_i(r) M_j(r), M(r) the maximum of |x| over the exponent block that
-    holds row r: blocks of 64 or 128 rows starting at a multiple of 64 rows, so within
-    the 64-row blocks b - 1, b, b + 1 around r."""
+    """2^-27 sum_r M_i(r) M_j(r), M(r) the maximum of |x| over the 64-row exponent block
+    that holds row r (blocks start at multiples of 64 rows of a row split; bounded here
+    by the 64-row blocks b - 1, b, b + 1 around r)."""
     n, m = X.shape
     nb = (n + 63) // 64
     Xp = np.zeros((nb * 64, m))
@@ -58,7 +58,7 @@ def _block_bound(X):
     Mn = M.copy()
     Mn[1:] = np.maximum(Mn[1:], M[:-1])
     Mn[:-1] = np.maximum(Mn[:-1], M[1:])
-    return 2.0 ** -20 * 64 * (Mn.T @ Mn)
+    return 2.0 ** -27 * 64 * (Mn.T @ Mn)
 
 
 @pytest.mark.parametrize("n,m,ld,kind", [(1000, 1, 1000, "gauss"), (10000, 100, 10000, "gauss"),
