@@ -94,7 +94,8 @@ struct Bars {
 
 struct Shared {
   Bars bars;
-  int exps[kExpSlots][kACols + kBCols];  // block exponents: A columns, then B columns
+  int exps[kExpSlots][kACols + kBCols];  // block digit scales: A columns, then B columns
+  int runE[kACols + kBCols];             // running maximum of the block exponents (converters)
   int bad[kACols + kBCols];              // sticky: column held Inf or NaN
   uint32_t tmem_base;
   int abort_flag;
@@ -172,11 +173,10 @@ __device__ __forceinline__ void convert_unit(const uint8_t* __restrict__ st, int
   }
 }
 
-// Round-to-nearest arithmetic right shift of a signed 64-bit value (sh >= 0).
+// Round-to-nearest arithmetic right shift of a signed 64-bit value, branch-free.
 __device__ __forceinline__ long long rshift_rn(long long v, int sh) {
-  if (sh <= 0) return v;
-  if (sh >= 62) return 0;
-  return (v + (1LL << (sh - 1))) >> sh;
+  sh = min(max(sh, 0), 62);  // |v| < 2^61: a shift of 62 leaves 0
+  return (v + ((1LL << sh) >> 1)) >> sh;
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -233,7 +233,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     sh.abort_flag = 0;
     tc::mbar_fence_init();
   }
-  for (int i = tid; i < kACols + kBCols; i += blockDim.x) sh.bad[i] = 0;
+  for (int i = tid; i < kACols + kBCols; i += blockDim.x) {
+    sh.bad[i] = 0;
+    sh.runE[i] = kExpZero;
+  }
   if (warp == 1) tc::tmem_alloc(&sh.tmem_base, kTmemCols);
   tc::tc_fence_before();
   __syncthreads();
@@ -337,8 +340,15 @@ __global__ void __launch_bounds__(kThreads, 1)
           badv |= __shfl_xor_sync(0xffffffffu, (int)badv, o) != 0;
         }
         if ((lane & 7) == 0) {
+          // the block's digits use the running maximum R of the exponents as their scale
+          // when the block exponent E is within 2 of it (at most 2 bits of the 32 lost):
+          // every entry of such blocks adds into its sum without a shift
           const int E = badv ? kExpBad : exp_of_max(mx);
-          sh.exps[es][c] = E;
+          const int R = sh.runE[c];
+          const bool valid = E > kExpZero && E < kExpBad;
+          const int Rn = valid ? max(R, E) : R;
+          sh.runE[c] = Rn;
+          sh.exps[es][c] = (valid && Rn - E <= 2) ? Rn : E;
           if (E == kExpBad) sh.bad[c] = 1;
         }
       }
@@ -384,6 +394,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int h = fw >> 2;                  // column half: B columns 32 h .. 32 h + 31
     const int ai = 32 * q + lane;           // tile row (A column)
     const uint32_t lanes = (uint32_t)(32 * q) << 16;
+    // rows a0 + 32 q .. of a tile whose B columns are inside its A panel may all lie
+    // below the diagonal of G for this warp's columns: nothing of theirs is kept
+    const bool below_diag = a0 + 32 * q > b0 + 32 * h + 31;
     long long acc[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) acc[i] = 0;
@@ -396,6 +409,14 @@ __global__ void __launch_bounds__(kThreads, 1)
            tc::mbar_wait_warp(&bars.exp_full[es], (blk / kExpSlots) & 1, abort_flag, err, wb);
       if (!ok) break;
       tc::tc_fence_after();
+      if (below_diag) {
+        __syncwarp();
+        if (lane == 0) {
+          tc::mbar_arrive(&bars.acc_empty[set]);
+          tc::mbar_arrive(&bars.exp_free[es]);
+        }
+        continue;
+      }
       const int Ei = sh.exps[es][ai];
       const int Ej_l = b_in_a ? sh.exps[es][b0 - a0 + 32 * h + lane] : sh.exps[es][kACols + 32 * h + lane];
       const bool vi = Ei > kExpZero && Ei < kExpBad;
@@ -449,7 +470,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc::mbar_arrive(&bars.exp_free[es]);
       }
     }
-    if (__all_sync(0xffffffffu, ok && !*abort_flag)) {
+    if (__all_sync(0xffffffffu, ok && !*abort_flag) && !below_diag) {
       const int gi = a0 + ai;
       const bool bad_i = sh.bad[ai] != 0;
       const int jmax = (J.m + kBCols - 1) / kBCols;

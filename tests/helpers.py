@@ -30,6 +30,17 @@ def rank_agrees(k_gpu: int, k_ref: int, tails_ref: np.ndarray, eps: float, rel_w
     return abs(tails_ref[j + 1] - eps * eps) <= rel_window * eps * eps or abs(tails_ref[j] - eps * eps) <= rel_window * eps * eps
 
 
+def rank_within(k_gpu: int, tails_ref: np.ndarray, eps: float, delta: float) -> bool:
+    """k_gpu is the truncation rank of Def. truncated POD for some tolerance whose square
+    lies within delta of eps^2: tails_ref[k] <= eps^2 + delta and, unless k = 0,
+    tails_ref[k - 1] > eps^2 - delta (tails_ref[j] = sum_{i >= j} sigma_i^2 of the oracle).
+    delta is the form's perturbation of the tail sums (e.g. m ||G - G_ref||_2)."""
+    e2 = eps * eps
+    if k_gpu < 0 or k_gpu >= len(tails_ref):
+        return False
+    return tails_ref[k_gpu] <= e2 + delta and (k_gpu == 0 or tails_ref[k_gpu - 1] > e2 - delta)
+
+
 def sigma_close(s_gpu: np.ndarray, s_ref: np.ndarray, rtol: float, floor_rel: float):
     """Relative agreement of singular values above floor_rel * sigma_max."""
     k = min(len(s_gpu), len(s_ref))

@@ -27,7 +27,7 @@ import torch
 
 import oracle
 from paper_1607_05210_gb300 import synth
-from tests.helpers import leaf_split, projection_error, rank_agrees, to_dev, to_host
+from tests.helpers import leaf_split, projection_error, rank_agrees, rank_within, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
 GRAM_WORST = 24 * 2.0 ** -23 + 2.0 ** -24
@@ -126,7 +126,8 @@ def test_pod_bf3(H, n, m, decay, rel):
     G = _gram(H, X)
     u_eff = float(np.linalg.norm(G - oracle.gram(X), 2) / fro2)
     N, s, Y, tail, st = H.hapod_pod(to_dev(X, dtype=torch.float32), eps, H.HAPOD_MIXED_BF16X3)
-    assert rank_agrees(N, ref.N, tails, eps, rel_window=1e-2)
+    # each tail sum moves by at most m ||G - G_ref||_2 (Weyl per eigenvalue)
+    assert rank_within(N, tails, eps, m * u_eff * fro2), (N, ref.N)
     s = s.cpu().numpy()
     k = min(N, ref.N)
     # |d lambda| <= ||E||_2 (Weyl) -> |d sigma| <= u_eff ||X||_F^2 / sigma, with 10x for the eigensolver
@@ -170,7 +171,8 @@ def test_hapod_bf3_trees(H, name, parent):
         kids = [b for b in range(len(parent)) if parent[b] == a]
         Xa = data[a] if not kids else np.concatenate([ref[b].Y for b in kids], axis=1)
         full_s, _, _, _ = oracle.svd(Xa, want_vectors=False)
-        assert rank_agrees(stats[a]["k"], ref[a].N, oracle.tail_sums(full_s), eps_nodes[a], rel_window=0.1), a
+        ua = float(np.linalg.norm(_gram(H, Xa) - oracle.gram(Xa), 2))
+        assert rank_within(stats[a]["k"], oracle.tail_sums(full_s), eps_nodes[a], Xa.shape[1] * ua), a
     # singular values on the common leading part: Gram error of each level (u_eff
     # measured on the leaves) plus, where a node kept a different rank, its extra mode
     u_eff = max(float(np.linalg.norm(_gram(H, data[a]) - oracle.gram(data[a]), 2) / np.sum(data[a] ** 2))

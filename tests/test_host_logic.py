@@ -107,3 +107,16 @@ def test_mixed_gram_roofline_is_hbm_bound():
                      "modes": {"ms": 50.0, "launches": 7, "bytes": 1e9, "flops": 1e11}}}
     dom, roof = bench.roofline(res, H.HAPOD_MIXED_TF32X3, H, 6786.2, 1725.3, "gram")
     assert roof["bound"] == "hbm" and roof["achieved"] == pytest.approx(1e9 / 0.1 / 1e9)
+
+
+def test_rank_within_accepts_only_ranks_of_nearby_tolerances():
+    from tests.helpers import rank_within
+
+    tails = np.array([10.0, 4.0, 1.0, 0.5, 0.0])  # sum_{i >= j} sigma_i^2
+    eps = 1.0
+    assert rank_within(2, tails, eps, 0.0)           # the exact rank (inclusive threshold)
+    assert not rank_within(1, tails, eps, 0.0)
+    assert not rank_within(3, tails, eps, 0.0)
+    assert rank_within(3, tails, eps, 0.01)          # tails[2] = eps^2 within delta
+    assert not rank_within(4, tails, eps, 0.01)
+    assert rank_within(1, tails, math.sqrt(4.0), 0.0) and not rank_within(0, tails, 2.0, 0.0)
