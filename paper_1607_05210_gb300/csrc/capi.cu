@@ -588,8 +588,17 @@ bool step_gram_fx3(Env& env, std::vector<Work*>& ws) {
   std::vector<CUtensorMap> maps(2 * ws.size());
   double bytes = 0, flops = 0;
   for (size_t i = 0; i < ws.size(); ++i) {
+    // column exponents of the node for its X V (filled by the Gram kernel)
+    if (!ws[i]->exps) {
+      ws[i]->exps = (int32_t*)env.alloc(sizeof(int32_t) * std::max<int64_t>(1, ws[i]->m), "alloc exponents");
+      if (!ws[i]->exps ||
+          !env.cuda(cudaMemsetAsync(ws[i]->exps, 0x80, sizeof(int32_t) * std::max<int64_t>(1, ws[i]->m), env.s),
+                    "memset exponents"))
+        return false;
+    }
     GramJob& J = jobs[i];
     memset(&J, 0, sizeof(J));
+    J.col_exp = ws[i]->exps;
     J.X = ws[i]->X;
     J.ldx = ws[i]->ldx;
     J.n = ws[i]->n;
@@ -624,6 +633,85 @@ bool step_gram_fx3(Env& env, std::vector<Work*>& ws) {
   env.release(red_d);
   env.release(maps_d);
   env.release(partials);
+  return ok;
+}
+
+// K4, mixed fixed-point form: Y = X V_k (diag scale) for every w (k = w->res.k > 0,
+// V_k in w->Vk, column exponents in w->exps from the Gram or computed here).
+bool step_modes_fx(Env& env, std::vector<Work*>& ws) {
+  if (ws.empty()) return true;
+  const int nw = (int)ws.size();
+  const int MT = fx_modes_tile();
+  std::vector<FxVSplitJob> vj(nw);
+  std::vector<FxModesJob> mj(nw);
+  std::vector<CUtensorMap> maps(nw);
+  std::vector<void*> bufs;
+  int64_t items = 0;
+  int max_kpad = 1;
+  bool ok = true;
+  double bytes = 0, flops = 0;
+  for (int i = 0; i < nw && ok; ++i) {
+    Work* w = ws[i];
+    if (!w->exps) {
+      w->exps = (int32_t*)env.alloc(sizeof(int32_t) * std::max<int64_t>(1, w->m), "alloc exponents");
+      ok = w->exps && env.cuda(launch_fx_colexp(static_cast<const float*>(w->X), w->ldx, w->n, w->m, w->exps, env.s),
+                               "column exponent launch");
+      if (!ok) break;
+    }
+    const int k = w->res.k;
+    const int mode_tiles = (k + MT - 1) / MT;
+    uint16_t* vdig = (uint16_t*)env.alloc(fx_vdig_bytes(w->m, k), "alloc V digits");
+    int32_t* fexp = (int32_t*)env.alloc(sizeof(int32_t) * mode_tiles * MT, "alloc mode exponents");
+    bufs.push_back(vdig);
+    bufs.push_back(fexp);
+    ok = vdig && fexp;
+    if (!ok) break;
+    FxVSplitJob& V = vj[i];
+    memset(&V, 0, sizeof(V));
+    V.V = w->Vk;
+    V.ldv = w->ldvk ? w->ldvk : w->m;
+    V.exps = w->exps;
+    V.vdig = vdig;
+    V.fexp = fexp;
+    V.m = (int32_t)w->m;
+    V.k = k;
+    V.kpad = mode_tiles * MT;
+    max_kpad = std::max(max_kpad, V.kpad);
+    FxModesJob& M = mj[i];
+    memset(&M, 0, sizeof(M));
+    M.X = static_cast<const float*>(w->X);
+    M.ldx = w->ldx;
+    M.exps = w->exps;
+    M.vdig = vdig;
+    M.fexp = fexp;
+    M.scale = w->scale;
+    M.Y = static_cast<float*>(w->Y);
+    M.ldy = w->ldy;
+    M.n = w->n;
+    M.item_base = items;
+    M.m = (int32_t)w->m;
+    M.k = k;
+    M.row_tiles = (int32_t)((w->n + 127) / 128);
+    M.mode_tiles = mode_tiles;
+    items += (int64_t)M.row_tiles * mode_tiles;
+    if (!encode_colmajor_f32(&maps[i], w->X, w->n, w->m, w->ldx, 128, 16, false))
+      ok = env.fail(HAPOD_ERR_CUDA, "cuTensorMapEncodeTiled failed for an X V input");
+    bytes += 4.0 * w->n * (w->m + k);
+    flops += 2.0 * w->n * w->m * k;
+  }
+  cudaEvent_t t0 = env.tic();
+  if (ok) {
+    FxVSplitJob* vj_d = env.upload(vj, "upload V split jobs");
+    FxModesJob* mj_d = env.upload(mj, "upload modes jobs");
+    CUtensorMap* maps_d = env.upload(maps, "upload tensor maps");
+    bufs.push_back(vj_d);
+    bufs.push_back(mj_d);
+    bufs.push_back(maps_d);
+    ok = vj_d && mj_d && maps_d && env.err_dev &&
+         env.cuda(launch_modes_fx(vj_d, nw, max_kpad, mj_d, maps_d, items, env.err_dev, env.s), "modes launch");
+  }
+  env.toc(t0, 4, 2, bytes, flops);
+  for (void* p : bufs) env.release(p);
   return ok;
 }
 
@@ -837,7 +925,31 @@ bool run_pod_back(Env& env, int precision, std::vector<Work*>& ws) {
   env.toc(tg, 3, 1, 0.0, 0.0);
   env.release(gd);
   if (!ok) return false;
-  if (precision == HAPOD_FP64_OZAKI) return step_modes_oz(env, act);
+  if (precision == HAPOD_FP64_OZAKI || precision == HAPOD_MIXED_FX3) {
+    // tensor-core X V with bounded waits: an error flag of its own, read back here
+    int* prev = env.err_dev;
+    int* flag = prev;
+    if (!flag) {
+      flag = (int*)env.alloc(sizeof(int) * 2, "alloc flag");
+      if (!flag || !env.cuda(cudaMemsetAsync(flag, 0, sizeof(int) * 2, env.s), "memset") ||
+          !init_err_flag(env, flag)) {
+        env.release(prev ? nullptr : flag);
+        return false;
+      }
+      env.err_dev = flag;
+    }
+    ok = precision == HAPOD_FP64_OZAKI ? step_modes_oz(env, act) : step_modes_fx(env, act);
+    int dev_err = 0;
+    if (ok && !prev)
+      ok = env.cuda(cudaMemcpyAsync(&dev_err, flag, sizeof(int), cudaMemcpyDeviceToHost, env.s), "read flag") &&
+           env.cuda(cudaStreamSynchronize(env.s), "synchronize");
+    if (!prev) {
+      env.release(flag);
+      env.err_dev = nullptr;
+    }
+    if (ok && dev_err) return env.fail(HAPOD_ERR_TIMEOUT, "device-side wait timed out in the tensor-core X V kernel");
+    return ok;
+  }
   int max_k = 0;
   for (Work* w : act) max_k = std::max(max_k, w->res.k);
   const int tr = fp64 ? modes_f64_tile_rows(max_k) : modes_mixed_rows_per_block(max_k);
@@ -1648,11 +1760,21 @@ hapod_status hapod_modes(int32_t precision, int64_t n, int64_t m, const void* X,
   if (N == 0 || n == 0) return HAPOD_OK;
   Env env;
   if (!init_env(env, stream)) return step_error(env);
-  if (precision == HAPOD_FP64_OZAKI) {
+  if (precision == HAPOD_FP64_OZAKI || precision == HAPOD_MIXED_FX3) {
     // tensor-core kernel with bounded waits: its error flag is read back here
     Work w;
     w.X = X;
     w.ldx = ldx;
+    if (precision == HAPOD_MIXED_FX3 && !tma_compatible_f32(X, ldx)) {  // TMA: aligned copy
+      const int64_t ld = (n + 31) / 32 * 32;
+      w.X_tmp = env.alloc(sizeof(float) * ld * m, "alloc aligned input");
+      if (!w.X_tmp || !env.cuda(cudaMemcpy2DAsync(w.X_tmp, ld * sizeof(float), X, ldx * sizeof(float),
+                                                  n * sizeof(float), m, cudaMemcpyDeviceToDevice, env.s),
+                                "copy input for TMA"))
+        return step_error(env);
+      w.X = w.X_tmp;
+      w.ldx = ld;
+    }
     w.n = n;
     w.m = m;
     w.Vk = const_cast<double*>(V);
@@ -1664,12 +1786,14 @@ hapod_status hapod_modes(int32_t precision, int64_t n, int64_t m, const void* X,
     std::vector<Work*> ws{&w};
     env.err_dev = (int*)env.alloc(sizeof(int) * 2, "alloc flag");
     bool ok = env.err_dev && env.cuda(cudaMemsetAsync(env.err_dev, 0, sizeof(int) * 2, env.s), "memset") &&
-              init_err_flag(env, env.err_dev) && step_modes_oz(env, ws);
+              init_err_flag(env, env.err_dev) &&
+              (precision == HAPOD_FP64_OZAKI ? step_modes_oz(env, ws) : step_modes_fx(env, ws));
     int dev_err = 0;
     if (ok)
       ok = env.cuda(cudaMemcpyAsync(&dev_err, env.err_dev, sizeof(int), cudaMemcpyDeviceToHost, env.s), "read flag");
     env.release(env.err_dev);
     env.release(w.exps);
+    env.release(w.X_tmp);
     ok = env.cuda(cudaStreamSynchronize(env.s), "synchronize") && ok;
     if (!ok) return step_error(env);
     if (dev_err) {

@@ -76,8 +76,8 @@ constexpr uint32_t kLbo = 128;                         // next core matrix along
 constexpr uint32_t kSbo = (kRows / 8) * 128;           // next core matrix along M / N (8 columns)
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kSetCols = 256;                     // one set of L2 | L3 | L4 | L5
-constexpr int kExpZero = -4000;                        // exponent of an all-zero column block
-constexpr int kExpBad = 4000;                          // exponent marking Inf / NaN
+constexpr int kExpZero = kFxExpZero;                   // exponent of an all-zero column block
+constexpr int kExpBad = kFxExpBad;                     // exponent marking Inf / NaN
 static_assert(kSmemBytes <= 227 * 1024, "shared memory");
 
 struct Bars {
@@ -350,6 +350,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           sh.runE[c] = Rn;
           sh.exps[es][c] = (valid && Rn - E <= 2) ? Rn : E;
           if (E == kExpBad) sh.bad[c] = 1;
+          // column exponents of the whole node, for the X V of the same form
+          if (J.col_exp && c < kACols && a0 + c < J.m && E > kExpZero) atomicMax(&J.col_exp[a0 + c], E);
         }
       }
       // every converter warp needs the exponents of all columns: arrive on the block's

@@ -38,6 +38,7 @@ struct GramJob {
   int64_t rows_per_split;
   double* G;        // m x m, ld = m
   int64_t item_base;
+  int32_t* col_exp; // fixed-point form: receives max over blocks of the column exponents (or null)
   int32_t m;
   int32_t tiles;    // tiles per dimension
   int32_t splits;
@@ -90,6 +91,49 @@ cudaError_t launch_gram_fx3(const GramJob* jobs_dev, const CUtensorMap* maps_dev
                             int num_items, const int4* reduce_dev, int num_reduce, double* partials, int* err_flag,
                             cudaStream_t s);
 int gram_fx3_rows_per_stage();
+// Exponent markers of the fixed-point form: an all-zero column (block) and a column
+// holding Inf / NaN; col_exp arrays start at kFxExpZero.
+constexpr int kFxExpZero = -4000;
+constexpr int kFxExpBad = 4000;
+
+// X V of the fixed-point form.  V_k digits (modes_fx_vsplit): per mode c the exponent
+// F_c (fexp, kpad entries) and four digit planes in the operand layout (vdig,
+// fx_vdig_bytes(m, k) bytes); X columns need their exponents (exps, m entries: from
+// the Gram's col_exp or launch_fx_colexp).
+struct FxVSplitJob {
+  const double* V;
+  int64_t ldv;
+  const int32_t* exps;
+  uint16_t* vdig;
+  int32_t* fexp;
+  int32_t m;
+  int32_t k;
+  int32_t kpad;  // k rounded up to whole mode tiles
+  int32_t pad;
+};
+// Items (row tile, mode tile) of 128 rows x 64 modes of one node; maps_dev[j]: X of job j
+// (encode_colmajor_f32, box 128 rows x 16 columns, no swizzle).
+struct FxModesJob {
+  const float* X;
+  int64_t ldx;
+  const int32_t* exps;
+  const uint16_t* vdig;
+  const int32_t* fexp;
+  const double* scale;  // k or null
+  float* Y;
+  int64_t ldy;
+  int64_t n;
+  int64_t item_base;
+  int32_t m;
+  int32_t k;
+  int32_t row_tiles;
+  int32_t mode_tiles;
+};
+int fx_modes_tile();
+size_t fx_vdig_bytes(int64_t m, int64_t k);
+cudaError_t launch_fx_colexp(const float* X, int64_t ldx, int64_t n, int64_t m, int* exps, cudaStream_t s);
+cudaError_t launch_modes_fx(const FxVSplitJob* vjobs_dev, int njobs, int max_kpad, const FxModesJob* jobs_dev,
+                            const CUtensorMap* maps_dev, int64_t total_items, int* err_flag, cudaStream_t s);
 int gram_fx3_a_cols();
 int gram_fx3_b_cols();
 // TMA needs a 16-byte aligned base and a row pitch that is a multiple of 16 bytes.

@@ -197,3 +197,33 @@ def test_hapod_fx3_trees(H, name, parent):
     dsig = np.abs(s.numpy()[:k] - sr[:k])
     print(f"{name}: k={len(s)} ref={len(sr)} u_eff={u_eff:.2e} max dsig/s0={dsig.max() / sr[0]:.2e} differ={differ}")
     assert np.all(dsig <= 10 * levels * u_eff * fro2 / sr[:k] + 1e-6 * sr[0] + slack), (dsig.max(), u_eff, differ)
+
+
+@pytest.mark.parametrize("n,m,N,ld", [(1000, 100, 37, 1000), (4097, 130, 20, 4100), (300, 1, 1, 300),
+                                      (12345, 64, 64, 12345), (9999, 256, 70, 9999), (50000, 450, 130, 50000)])
+def test_modes_fx3(H, n, m, N, ld):
+    """Y = X V diag(s) from exact digit products: per column pair the representation of
+    x (2^(E_j - 32)) and of V_jc 2^E_j (2^(F_c - 32)) and the dropped digit pairs
+    (2^(F_c - 30.4)) give |Y - X V s| <= (m 2^-27.5 max_j M_j |V_jc| + 2^-24 |X V|) |s_c|
+    (M_j = max_r |x_rj|; the second term is the FP32 rounding of Y)."""
+    rng = np.random.default_rng(n + m)
+    X = _f32(rng.standard_normal((n, m)) * 2.0 ** rng.integers(-3, 4, m))
+    V = np.asfortranarray(rng.standard_normal((m, N)))
+    scale = rng.uniform(0.5, 2.0, N)
+    Y = to_host(H.hapod_modes(to_dev(X, dtype=torch.float32, ld=ld), to_dev(V), N, torch.from_numpy(scale).cuda(),
+                              H.HAPOD_MIXED_FX3))
+    ref = (X @ V) * scale
+    M = np.max(np.abs(X), axis=0)
+    bound = (m * 2.0 ** -27.5 * np.max(M[:, None] * np.abs(V), axis=0) + 2.0 ** -24 * np.abs(X @ V)) * scale
+    err = np.abs(Y - ref)
+    print(f"modes fx3 n={n} m={m} N={N}: max err/bound {np.max(err / bound):.3e}")
+    assert np.all(err <= bound)
+
+
+def test_modes_fx3_exact_integers(H):
+    rng = np.random.default_rng(9)
+    n, m, N = 5000, 200, 50
+    X = rng.integers(-8, 9, (n, m)).astype(np.float64)
+    V = np.asfortranarray(rng.integers(-8, 9, (m, N)).astype(np.float64))
+    Y = to_host(H.hapod_modes(to_dev(X, dtype=torch.float32), to_dev(V), N, None, H.HAPOD_MIXED_FX3))
+    assert np.array_equal(Y, X @ V)
