@@ -94,8 +94,7 @@ struct Bars {
 
 struct Shared {
   Bars bars;
-  int exps[kExpSlots][kACols + kBCols];  // block digit scales: A columns, then B columns
-  int runE[kACols + kBCols];             // running maximum of the block exponents (converters)
+  int exps[kExpSlots][kACols + kBCols];  // block exponents: A columns, then B columns
   int bad[kACols + kBCols];              // sticky: column held Inf or NaN
   uint32_t tmem_base;
   int abort_flag;
@@ -233,10 +232,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     sh.abort_flag = 0;
     tc::mbar_fence_init();
   }
-  for (int i = tid; i < kACols + kBCols; i += blockDim.x) {
-    sh.bad[i] = 0;
-    sh.runE[i] = kExpZero;
-  }
+  for (int i = tid; i < kACols + kBCols; i += blockDim.x) sh.bad[i] = 0;
   if (warp == 1) tc::tmem_alloc(&sh.tmem_base, kTmemCols);
   tc::tc_fence_before();
   __syncthreads();
@@ -340,15 +336,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           badv |= __shfl_xor_sync(0xffffffffu, (int)badv, o) != 0;
         }
         if ((lane & 7) == 0) {
-          // the block's digits use the running maximum R of the exponents as their scale
-          // when the block exponent E is within 2 of it (at most 2 bits of the 32 lost):
-          // every entry of such blocks adds into its sum without a shift
           const int E = badv ? kExpBad : exp_of_max(mx);
-          const int R = sh.runE[c];
-          const bool valid = E > kExpZero && E < kExpBad;
-          const int Rn = valid ? max(R, E) : R;
-          sh.runE[c] = Rn;
-          sh.exps[es][c] = (valid && Rn - E <= 2) ? Rn : E;
+          sh.exps[es][c] = E;
           if (E == kExpBad) sh.bad[c] = 1;
           // column exponents of the whole node, for the X V of the same form
           if (J.col_exp && c < kACols && a0 + c < J.m && E > kExpZero) atomicMax(&J.col_exp[a0 + c], E);
