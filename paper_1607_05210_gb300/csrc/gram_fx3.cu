@@ -96,6 +96,7 @@ struct Shared {
   Bars bars;
   int exps[kExpSlots][kACols + kBCols];  // block exponents: A columns, then B columns
   int bad[kACols + kBCols];              // sticky: column held Inf or NaN
+  int colmax[kACols];                    // running maximum of the A columns' block exponents
   uint32_t tmem_base;
   int abort_flag;
 };
@@ -232,7 +233,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     sh.abort_flag = 0;
     tc::mbar_fence_init();
   }
-  for (int i = tid; i < kACols + kBCols; i += blockDim.x) sh.bad[i] = 0;
+  for (int i = tid; i < kACols + kBCols; i += blockDim.x) {
+    sh.bad[i] = 0;
+    if (i < kACols) sh.colmax[i] = kExpZero;
+  }
   if (warp == 1) tc::tmem_alloc(&sh.tmem_base, kTmemCols);
   tc::tc_fence_before();
   __syncthreads();
@@ -339,8 +343,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int E = badv ? kExpBad : exp_of_max(mx);
           sh.exps[es][c] = E;
           if (E == kExpBad) sh.bad[c] = 1;
-          // column exponents of the whole node, for the X V of the same form
-          if (J.col_exp && c < kACols && a0 + c < J.m && E > kExpZero) atomicMax(&J.col_exp[a0 + c], E);
+          // column exponents of the whole node, for the X V of the same form: a running
+          // maximum per CTA here, one global atomic per column at the end
+          if (c < kACols) sh.colmax[c] = max(sh.colmax[c], E);
         }
       }
       // every converter warp needs the exponents of all columns: arrive on the block's
@@ -494,6 +499,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
+  if (J.col_exp && Jt == 2 * I)  // one tile per A panel and split reports its columns
+    for (int c = tid; c < kACols && a0 + c < J.m; c += blockDim.x)
+      if (sh.colmax[c] > kExpZero) atomicMax(&J.col_exp[a0 + c], sh.colmax[c]);
   if (warp == 1) tc::tmem_dealloc(tbase, kTmemCols);
 }
 
