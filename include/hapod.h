@@ -299,6 +299,44 @@ hapod_status hapod_modes(int32_t precision, int64_t n, int64_t m, const void* X,
 hapod_status hapod_pod(int32_t precision, int64_t n, int64_t m, const void* X, int64_t ldx, double eps,
                        int64_t* N_host, double* sigma, void* Y, int64_t ldy, double* tail_host, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Input generation (stand-in for the PDE snapshot data of Sec. 4, which is not
+ * available): snapshots written directly into device memory, so that leaves and
+ * stream chunks (Sec. 3.4, reduced memory) need no host copy.
+ */
+#define HAPOD_SYNTH_MAX_PULSES 64
+typedef struct {
+  uint64_t seed;                                 /* Philox4x32-10 key of the snapshot times */
+  double nu;                                     /* diffusion coefficient */
+  double speed;                                  /* advection speed c */
+  double harmonic_amp[32];                       /* a_k of sin(k (x - c t)), k = 1..32 */
+  int32_t num_pulses;                            /* 0 .. HAPOD_SYNTH_MAX_PULSES */
+  double pulse_width;                            /* w (> 0 when num_pulses > 0) */
+  double pulse_centre[HAPOD_SYNTH_MAX_PULSES];   /* x_p at t = 0, in [0, 2 pi) */
+  double pulse_amp[HAPOD_SYNTH_MAX_PULSES];      /* A_p */
+} hapod_synth_params;
+
+/*
+ * hapod_synth_snapshots -- columns col0 .. col0 + ncols - 1 of the travelling-pulse
+ * trajectory on the periodic grid x_i = 2 pi i / n, i < n:
+ *   X[i, j] = sum_k a_k exp(-nu k^2 t) sin(k (x_i - c t))
+ *           + sum_p A_p exp(-d(x_i, x_p + c t)^2 / (2 w^2)),   t = t_{col0 + j},
+ * d the periodic distance, pulses beyond 9 w omitted (below 3e-18 A_p).  The time of
+ * global column g is the uniform t_g = (w0 2^21 + (w1 >> 11)) 2^-53 from the first
+ * two words (w0, w1) of Philox4x32-10 (Salmon et al., SC 2011) with key (seed mod
+ * 2^32, seed div 2^32) and counter (g mod 2^32, g div 2^32, 0, 0), so any column
+ * range is reproducible on its own.  The field is evaluated in FP32 (the Fourier
+ * coefficients, times and pulse positions in FP64); dtype 0 writes float, 1 writes
+ * double holding the same FP32 values.  X: device, n x ncols, column-major, leading
+ * dimension ldx >= n (elements).  t_out: device, ncols doubles receiving t_g, or
+ * NULL.  p: host, read during the call.  Asynchronous on `stream`; allocates a
+ * small per-column table (about 1 KB per column) from the stream-ordered default
+ * pool and frees it on the stream.  Errors: INVALID (n < 1 or n > 2^36, col0 < 0,
+ * ld, dtype, pulse count or width), OOM, CUDA.
+ */
+hapod_status hapod_synth_snapshots(const hapod_synth_params* p, int64_t n, int64_t col0, int64_t ncols,
+                                   int32_t dtype, void* X, int64_t ldx, double* t_out, void* stream);
+
 /*
  * hapod_gram_noalloc -- the FP64 Gram G = X^T X of hapod_gram (HAPOD_FP64 form)
  * for callers that must not allocate device memory while they run: for example

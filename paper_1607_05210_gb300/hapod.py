@@ -71,6 +71,16 @@ class hapod_node_info(ctypes.Structure):
                 ("status", ctypes.c_int32)]
 
 
+SYNTH_MAX_PULSES = 64
+
+
+class hapod_synth_params(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("nu", ctypes.c_double), ("speed", ctypes.c_double),
+                ("harmonic_amp", ctypes.c_double * 32), ("num_pulses", ctypes.c_int32),
+                ("pulse_width", ctypes.c_double), ("pulse_centre", ctypes.c_double * SYNTH_MAX_PULSES),
+                ("pulse_amp", ctypes.c_double * SYNTH_MAX_PULSES)]
+
+
 class HapodError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -98,6 +108,7 @@ def _load() -> ctypes.CDLL:
         "hapod_modes": ([i32, i64, i64, vp, i64, vp, i64, i64, vp, vp, i64, vp], i32),
         "hapod_pod": ([i32, i64, i64, vp, i64, d, pi64, vp, vp, i64, pd, vp], i32),
         "hapod_gram_noalloc": ([i64, i64, vp, i64, vp, vp], i32),
+        "hapod_synth_snapshots": ([ctypes.POINTER(hapod_synth_params), i64, i64, i64, i32, vp, i64, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -109,7 +120,8 @@ def _load() -> ctypes.CDLL:
 _lib = _load()
 EXPORTED = ("hapod_create", "hapod_push", "hapod_result", "hapod_node_stats", "hapod_profile", "hapod_last_error",
             "hapod_destroy", "hapod_trim_pool",
-            "hapod_gram", "hapod_eig", "hapod_truncate", "hapod_modes", "hapod_pod", "hapod_gram_noalloc")
+            "hapod_gram", "hapod_eig", "hapod_truncate", "hapod_modes", "hapod_pod", "hapod_gram_noalloc",
+            "hapod_synth_snapshots")
 
 
 def _stream(stream: Optional[torch.cuda.Stream]) -> int:
@@ -293,6 +305,41 @@ def hapod_pod(X: torch.Tensor, eps: float, precision: int = HAPOD_FP64, stream=N
                                ctypes.byref(tail), ctypes.c_void_p(_stream(stream))))
     k = N.value
     return k, sigma[:k], Y[:, :k], tail.value, st
+
+
+# ------------------------------------------------------------------ input generation
+def synth_params(seed: int, harmonic_amp, nu: float, speed: float, pulse_centre=(), pulse_amp=(),
+                 pulse_width: float = 0.01) -> hapod_synth_params:
+    p = hapod_synth_params()
+    p.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    p.nu, p.speed = float(nu), float(speed)
+    if len(harmonic_amp) != 32 or len(pulse_centre) != len(pulse_amp) or len(pulse_amp) > SYNTH_MAX_PULSES:
+        raise ValueError("32 harmonic amplitudes and at most 64 pulses (centre, amplitude) expected")
+    for k, a in enumerate(harmonic_amp):
+        p.harmonic_amp[k] = float(a)
+    p.num_pulses = len(pulse_amp)
+    p.pulse_width = float(pulse_width)
+    for q, (c, a) in enumerate(zip(pulse_centre, pulse_amp)):
+        p.pulse_centre[q] = float(c)
+        p.pulse_amp[q] = float(a)
+    return p
+
+
+def hapod_synth_snapshots(params: hapod_synth_params, n: int, col0: int, ncols: int, out: torch.Tensor,
+                          t_out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """Fill the n x ncols column-major CUDA tensor ``out`` (float32 or float64) with
+    columns col0 .. col0 + ncols - 1 of the travelling-pulse trajectory."""
+    nn, m, ld = _colmajor(out) if out.numel() else (n, ncols, n)
+    if nn != n or m != ncols or out.dtype not in (torch.float32, torch.float64):
+        raise ValueError("out must be an n x ncols float32/float64 column-major CUDA tensor")
+    if t_out is not None and (t_out.dtype != torch.float64 or t_out.numel() < ncols or not t_out.is_cuda):
+        raise ValueError("t_out must be a CUDA float64 tensor of ncols entries")
+    _check(_lib.hapod_synth_snapshots(ctypes.byref(params), int(n), int(col0), int(ncols),
+                                      0 if out.dtype == torch.float32 else 1,
+                                      ctypes.c_void_p(out.data_ptr() if out.numel() else 0), ld,
+                                      ctypes.c_void_p(t_out.data_ptr() if t_out is not None else 0),
+                                      ctypes.c_void_p(_stream(stream))))
+    return out
 
 
 def eps_star_to_global(eps_star: float, num_snapshots: int) -> float:

@@ -12,9 +12,14 @@ stand in for the paper's PDE snapshot data (Sec. 4), which is not available:
   on the periodic grid x_i = 2 pi i / n, a_k ~ N(0, k^-2), t_j ~ U[0, 1], nu = 1e-3,
   c = 1.  Expanded as X = B C with B = [sin(k x), cos(k x)] (n x 64) so that large
   matrices are produced by one matrix product on the device.
-* ``advection_pulses``: the advection-diffusion snapshots plus 64 travelling
-  Gaussian pulses sum_p A_p exp(-d(x, x_p + c t)^2 / (2 w^2)), w = 0.01, A_p = 1/p,
-  centres x_p ~ U[0, 2 pi), d the periodic distance (the precision workload).
+* ``pulse_workload`` / ``pulse_snapshots`` / ``advection_pulses``: the
+  advection-diffusion snapshots plus 64 travelling Gaussian pulses
+  sum_p A_p exp(-d(x, x_p + c t)^2 / (2 w^2)), w = 0.01, A_p = 1/p, centres
+  x_p ~ U[0, 2 pi), d the periodic distance (the precision workload), with snapshot
+  times from Philox4x32-10 (counter = global column index, key = seed) so that any
+  column range (a leaf, a stream chunk) is reproducible on its own; host twin of
+  the library's device generator ``hapod_synth_snapshots`` (FP64 arithmetic here,
+  FP32 there).
 * tree builders returning parent arrays (root has parent -1).
 """
 from __future__ import annotations
@@ -204,36 +209,84 @@ NUM_PULSES = 64
 PULSE_WIDTH = 0.01
 
 
-def pulse_params(seed: int):
-    """(centres x_p, amplitudes A_p) of the 64 travelling pulses: x_p ~ U[0, 2 pi) from
-    a stream of its own (seed + 1), A_p = 1/p (1/f decay)."""
-    rng = np.random.default_rng(seed + 1)
-    xp = rng.uniform(0.0, 2.0 * math.pi, NUM_PULSES)
-    amp = 1.0 / np.arange(1, NUM_PULSES + 1, dtype=np.float64)
-    return xp, amp
+# --------------------------------------------------- counter-based snapshot times
+PHILOX_M0, PHILOX_M1 = 0xD2511F53, 0xCD9E8D57
+PHILOX_W0, PHILOX_W1 = 0x9E3779B9, 0xBB67AE85
 
 
-def snapshot_times(num_cols: int, seed: int) -> np.ndarray:
-    """t_j of advection_diffusion_coeffs (the same stream, after the 32 amplitudes)."""
+def philox4x32_10(counter, key) -> np.ndarray:
+    """Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC 2011): ten rounds of
+    (c0, c1, c2, c3) <- (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0))
+    with the key bumped by the Weyl constants after each round.  ``counter``: 4 x N
+    unsigned 32-bit words, ``key``: two words; returns 4 x N words."""
+    c = [np.asarray(w, dtype=np.uint64) & 0xFFFFFFFF for w in counter]
+    k0, k1 = int(key[0]) & 0xFFFFFFFF, int(key[1]) & 0xFFFFFFFF
+    mask = np.uint64(0xFFFFFFFF)
+    for _ in range(10):
+        p0 = np.uint64(PHILOX_M0) * c[0]
+        p1 = np.uint64(PHILOX_M1) * c[2]
+        hi0, lo0 = p0 >> np.uint64(32), p0 & mask
+        hi1, lo1 = p1 >> np.uint64(32), p1 & mask
+        c = [hi1 ^ c[1] ^ np.uint64(k0), lo1, hi0 ^ c[3] ^ np.uint64(k1), lo0]
+        k0 = (k0 + PHILOX_W0) & 0xFFFFFFFF
+        k1 = (k1 + PHILOX_W1) & 0xFFFFFFFF
+    return np.stack([w.astype(np.uint32) for w in c])
+
+
+def philox_times(seed: int, col0: int, ncols: int) -> np.ndarray:
+    """t_g = (w0 2^21 + (w1 >> 11)) 2^-53 for global columns g = col0 .. col0 + ncols - 1,
+    (w0, w1) the first two words of Philox4x32-10 with counter (g mod 2^32, g div 2^32,
+    0, 0) and key (seed mod 2^32, seed div 2^32)."""
+    g = np.arange(col0, col0 + ncols, dtype=np.uint64)
+    zero = np.zeros_like(g)
+    w = philox4x32_10([g & np.uint64(0xFFFFFFFF), g >> np.uint64(32), zero, zero], (seed, seed >> 32))
+    bits = (w[0].astype(np.uint64) << np.uint64(21)) | (w[1].astype(np.uint64) >> np.uint64(11))
+    return bits.astype(np.float64) * 2.0 ** -53
+
+
+def pulse_workload(seed: int, num_pulses: int = NUM_PULSES, nu: float = 1e-3, speed: float = 1.0,
+                 width: float = PULSE_WIDTH) -> Dict:
+    """Parameters of the travelling-pulse trajectory: harmonic amplitudes a_k ~ N(0, k^-2)
+    from the seed's stream, pulse centres x_p ~ U[0, 2 pi) from stream seed + 1, pulse
+    amplitudes A_p = 1/p (1/f decay), width w, nu, c, and the Philox key (the seed)."""
     rng = np.random.default_rng(seed)
-    rng.standard_normal(NUM_HARMONICS)
-    return rng.uniform(0.0, 1.0, num_cols)
+    k = np.arange(1, NUM_HARMONICS + 1, dtype=np.float64)
+    a = rng.standard_normal(NUM_HARMONICS) / k
+    rng_p = np.random.default_rng(seed + 1)
+    xp = rng_p.uniform(0.0, 2.0 * math.pi, NUM_PULSES)[:num_pulses]
+    amp = 1.0 / np.arange(1, num_pulses + 1, dtype=np.float64)
+    return {"seed": int(seed), "harmonic_amp": a, "nu": float(nu), "speed": float(speed),
+            "pulse_centre": xp, "pulse_amp": amp, "pulse_width": float(width)}
 
 
-def add_pulses(X: np.ndarray, t: np.ndarray, seed: int, c: float = 1.0) -> np.ndarray:
-    """X[:, j] += sum_p A_p exp(-d(x_i, x_p + c t_j)^2 / (2 w^2)) on x_i = 2 pi i / n."""
-    n = X.shape[0]
-    x = 2.0 * math.pi * np.arange(n) / n
-    xp, amp = pulse_params(seed)
-    for p in range(NUM_PULSES):
-        d = (x[:, None] - xp[p] - c * t[None, :] + math.pi) % (2.0 * math.pi) - math.pi
-        X += amp[p] * np.exp(-d * d / (2.0 * PULSE_WIDTH ** 2))
-    return X
+def pulse_snapshots(n: int, col0: int, ncols: int, params: Dict, dtype=np.float32) -> np.ndarray:
+    """Host twin of the device generator: columns col0 .. col0 + ncols - 1 (n x ncols,
+    column-major), evaluated in FP64 and rounded once to ``dtype``."""
+    t = philox_times(params["seed"], col0, ncols)
+    k = np.arange(1, NUM_HARMONICS + 1, dtype=np.float64)
+    damp = params["harmonic_amp"][:, None] * np.exp(-params["nu"] * (k[:, None] ** 2) * t[None, :])
+    C = np.empty((2 * NUM_HARMONICS, ncols))
+    C[:NUM_HARMONICS] = damp * np.cos(k[:, None] * params["speed"] * t[None, :])
+    C[NUM_HARMONICS:] = -damp * np.sin(k[:, None] * params["speed"] * t[None, :])
+    X = fourier_basis(n) @ C
+    w = params["pulse_width"]
+    h = 2.0 * math.pi / n
+    R = int(math.ceil(9.0 * w / h)) + 1  # rows around the nearest grid point that can lie within 9 w
+    off = np.arange(-R, R + 1)
+    jj = np.broadcast_to(np.arange(ncols)[:, None], (ncols, off.size))
+    for c, a in zip(params["pulse_centre"], params["pulse_amp"]):
+        pos = np.mod(c + params["speed"] * t, 2.0 * math.pi)
+        rows = np.mod(np.rint(pos / h).astype(np.int64)[:, None] + off[None, :], n)  # ncols x (2R + 1)
+        d = np.abs(2.0 * math.pi * rows / n - pos[:, None])
+        d = np.minimum(d, 2.0 * math.pi - d)
+        v = np.where(d <= 9.0 * w, a * np.exp(-d * d / (2.0 * w * w)), 0.0)
+        if 2 * R + 1 <= n:  # rows of one column are distinct
+            X[rows, jj] += v
+        else:
+            np.add.at(X, (rows, jj), v)
+    return np.asfortranarray(X.astype(dtype))
 
 
 def advection_pulses(n: int, num_cols: int, seed: int, dtype=np.float64) -> np.ndarray:
-    """Host version of the precision workload's snapshots (n x num_cols)."""
-    X = fourier_basis(n) @ advection_diffusion_coeffs(num_cols, seed)
-    add_pulses(X, snapshot_times(num_cols, seed), seed)
-    return np.asfortranarray(X.astype(dtype))
-
+    """Columns 0 .. num_cols - 1 of the travelling-pulse trajectory of ``seed``."""
+    return pulse_snapshots(n, 0, num_cols, pulse_workload(seed), dtype)
