@@ -1,32 +1,42 @@
 #!/usr/bin/env python
-"""HAPOD throughput on one GB300: snapshot columns/s and algorithmic GB/s.
+"""HAPOD throughput on one GB300: snapshot columns/s and algorithmic GB/s at the
+stated error, mixed/batched form beside the FP64-accurate form.
 
-Workload (synthetic, seeded): n = 2^20 rows, 64 leaves x 256 snapshot columns of
-the advection-diffusion trajectory u(x, t) = sum_k a_k exp(-nu k^2 t) sin(k(x - c t))
-(32 harmonics, a_k ~ N(0, k^-2), nu = 1e-3, c = 1, t ~ U[0, 1]), balanced binary
-tree of edge depth 6 (L_T = 7), eps = 1e-5 relative (sum_s ||s - P s||^2 <=
-(1e-5 ||X||_F)^2), omega = 0.5.  The inputs (137 GB in FP64, 69 GB in FP32) are
-generated on the device before timing and are larger than L2, so no flush is
-needed between steps.
+Headline workload (precision form): n = 2^22 rows, 256 leaves x 128 FP32 snapshot
+columns (32,768 columns, 512 GiB) of the travelling-pulse trajectory -- the
+advection-diffusion field u = sum_k a_k exp(-nu k^2 t) sin(k(x - c t)) (32
+harmonics, a_k ~ N(0, k^-2), nu = 1e-3, c = 1) plus 64 Gaussian pulses of width 0.01
+with amplitudes 1/p moving at speed c, snapshot times from Philox4x32-10 -- on a
+balanced quaternary tree of edge depth 4 (L_T = 5), eps = 1e-4 relative, omega =
+0.5.  The snapshots are generated on the device by the library's generator
+(hapod_synth_snapshots) in waves of 16 leaves (one level-3 subtree, 32 GiB FP32):
+512 GiB never fit HBM at once.  The context processes each wave as it is pushed
+(max_pending_leaves = 16), so a wave's leaves, its four level-2 nodes and its
+level-3 node run before the next wave is generated; the root levels run with the
+last wave.  Timed region: the sum over waves of the CUDA-event interval around the
+wave's pushes (plus hapod_result after the last), so inputs are resident in HBM when
+each interval starts and generation is reported separately.  Every wave's leaves
+(2 GiB each) are larger than L2, so no flush is needed.
 
-A step is one full HAPOD through the C ABI: create, push every leaf, result,
-destroy.  The headline is the digit-slice FP64 form (FP64 data and results; Gram
-and X V from exact integer digit products on the tensor cores) at the workload's
-tolerance eps = 1e-5 rel; the FP64 ALU form runs at the same tolerance for
-comparison.  The mixed form (FP32 snapshots, TF32 tensor-core Gram) resolves
-singular values only down to its measured Gram error (noise eigenvalues summing
-to ~6e-8 of the trace), so it is run at eps = 1e-2 rel, and the FP64 ALU form is
-run at that tolerance too for a same-accuracy comparison; all appear under
-"forms".
+Forms: the mixed fixed-point form (HAPOD_MIXED_FX3: FP32 snapshots, Gram from exact
+8-bit digit products on the tensor cores with int64 sums, tensor-core X V, FP64
+eigensolve/tails, CholQR2 at the root) is the headline; the digit-slice FP64 form
+(HAPOD_FP64_OZAKI: the same values in FP64) runs at the same eps beside it.
 
-The end-to-end figure ("e2e") repeats the headline HAPOD from pinned host buffers
-right after the headline form: the 64 leaf uploads (137 GB) are queued on a copy
-stream and the context processes leaves in batches of 4 as they land, so the
-host-to-device link (~210 GB/s measured) bounds it; "h2d_gbs" is the upload rate
-seen during that step.
+Other workloads ("workloads"): the FP64 advection-diffusion workload at n = 2^20,
+64 leaves x 256 columns, eps = 1e-5 rel, on the balanced binary tree (L_T = 7) and
+on the two-level star, resident in HBM (137 GB), digit-slice and FP64 ALU forms.
 
---impl reference times the CPU FP64 oracle on the host cores on a bounded sample
-of the same workload (there is no other reference implementation of the method).
+End to end ("e2e"): the headline HAPOD through the public API from pinned host
+buffers.  Per wave the 16 generated leaves are first copied to pinned host memory
+(untimed); the timed interval then holds their host-to-device copies (a copy
+stream, each push waiting for its leaf) and the wave's processing.
+
+--impl reference and cpu_baseline time the CPU FP64 oracle (Householder QR +
+one-sided Jacobi per node) on a bounded sample: one leaf and one level-2 node of
+the headline tree at two reduced row counts; each node kind's time is fitted
+linearly in n and the whole tree (256 leaves + 85 inner nodes) is extrapolated to
+n = 2^22.
 """
 from __future__ import annotations
 
@@ -44,24 +54,31 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+UNIT = "columns/s"
+METRIC = "HAPOD snapshot columns/s at stated error (mixed/batched form vs FP64 form)"
+
+# precision workload: quaternary tree, device-generated travelling pulses
+C3 = {"name": "c3", "n": 1 << 22, "leaves": 256, "cols": 128, "arity": 4, "depth": 4, "eps_rel": 1e-4,
+      "omega": 0.5, "wave": 16, "seed": 1607052103}
+C3_WORKLOAD = ("travelling-pulse HAPOD (precision form), n=2^22 FP32 rows, 256 leaves x 128 snapshots "
+               "(32768 columns, 512 GiB generated on the device in waves of 16 leaves), quaternary tree L_T=5, "
+               "eps=1e-4 rel, omega=0.5")
+
+# FP64 advection-diffusion workload, resident
 N_ROWS = 1 << 20
 LEAVES = 64
 COLS = 256
 SEED = 1607052102
 EPS_REL = 1e-5
-MIXED_EPS_REL = 1e-2
 OMEGA = 0.5
 TREE_DEPTH = 6
-METRIC = "HAPOD snapshot columns/s at stated error (eps = 1e-5 rel, omega = 0.5)"
-UNIT = "columns/s"
-WORKLOAD = ("advection-diffusion HAPOD, n=2^20 rows, 64 leaves x 256 snapshots (16384 columns), "
-            "balanced binary tree L_T=7, eps=1e-5 rel, omega=0.5")
-ORACLE_SAMPLE_ROWS = N_ROWS // 16
+C2_WORKLOAD = ("advection-diffusion HAPOD, n=2^20 FP64 rows, 64 leaves x 256 snapshots (16384 columns), "
+               "eps=1e-5 rel, omega=0.5")
 
 
 def _peaks():
-    """(HBM GB/s, bf16 TFLOP/s sustained, source).  The tensor-core kernels run inside a
-    step of seconds, so the sustained bf16 figure is their denominator."""
+    """(HBM GB/s, bf16 TFLOP/s sustained, source).  The kernels run inside a step of
+    seconds, so the sustained bf16 figure is the tensor denominator."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             p = json.load(f)
@@ -118,7 +135,159 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# ----------------------------------------------------------------- inputs
+# ----------------------------------------------------------------- precision workload (device-generated)
+def c3_tree(wl=C3):
+    from paper_1607_05210_gb300 import synth
+
+    parent = synth.balanced_tree(wl["arity"], wl["depth"])
+    leaves = synth.leaves_of(parent)
+    cols = [0] * len(parent)
+    for a in leaves:
+        cols[a] = wl["cols"]
+    return parent, leaves, cols
+
+
+def c3_params(H, wl=C3):
+    from paper_1607_05210_gb300 import synth
+
+    return H.synth_params(**synth.pulse_workload(wl["seed"]))
+
+
+class Generator:
+    """Leaf i of the workload = global columns i * cols .. (i + 1) * cols - 1."""
+
+    def __init__(self, H, wl, dtype, device, nbuf):
+        import torch
+
+        self.H, self.wl, self.dtype = H, wl, dtype
+        self.params = c3_params(H, wl)
+        self.bufs = [torch.empty((wl["cols"], wl["n"]), dtype=dtype, device=device) for _ in range(nbuf)]
+
+    def gen(self, leaf_index, slot, stream):
+        wl = self.wl
+        self.H.hapod_synth_snapshots(self.params, wl["n"], leaf_index * wl["cols"], wl["cols"],
+                                     self.bufs[slot].t(), stream=stream)
+        return self.bufs[slot]
+
+
+def c3_fro2(H, wl, device, stream):
+    """||X||_F^2 of the whole workload (FP64 sum of the FP32 snapshots), untimed."""
+    import torch
+
+    g = Generator(H, wl, torch.float32, device, 1)
+    tot = 0.0
+    with torch.cuda.stream(stream):
+        for i in range(wl["leaves"]):
+            b = g.gen(i, 0, stream)
+            tot += float(torch.linalg.vector_norm(b, dtype=torch.float64) ** 2)
+    del g
+    return tot
+
+
+def run_waves(H, precision, wl, fro2, steps, warmup, stream, dist_ctx, host=None):
+    """The headline HAPOD: per wave, generate its leaves (untimed), then push them
+    (timed).  With ``host`` (pinned host buffers, one wave), the generated leaves are
+    first copied to the host (untimed) and the timed interval holds their uploads."""
+    import torch
+
+    parent, leaves, cols = c3_tree(wl)
+    dtype = H.DTYPE[precision]
+    device = torch.device("cuda", torch.cuda.current_device())
+    W = wl["wave"]
+    gen = Generator(H, wl, dtype, device, W)
+    eps = wl["eps_rel"] * math.sqrt(fro2)
+    copy_stream = torch.cuda.Stream(device) if host is not None else None
+    info = {}
+    launches = [0]
+    gen_ms = [0.0]
+
+    def step(profile, timed):
+        ctx = H.hapod_create(parent, cols, eps, wl["omega"], wl["n"], precision, stream=stream,
+                             max_pending_leaves=W, flags=H.HAPOD_FLAG_PROFILE if profile else 0)
+        ms = 0.0
+        d2h = 0
+        for w0 in range(0, len(leaves), W):
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                g0.record(stream)
+                for i in range(w0, min(len(leaves), w0 + W)):
+                    gen.gen(i, i - w0, stream)
+                g1.record(stream)
+            if host is not None:  # untimed: the wave's leaves to pinned host memory
+                with torch.cuda.stream(stream):
+                    for i in range(w0, min(len(leaves), w0 + W)):
+                        host[i - w0].copy_(gen.bufs[i - w0], non_blocking=True)
+                stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if host is not None:
+                copy_stream.wait_event(e0)
+                done = []
+                with torch.cuda.stream(copy_stream):
+                    for i in range(w0, min(len(leaves), w0 + W)):
+                        gen.bufs[i - w0].copy_(host[i - w0], non_blocking=True)
+                        ev = torch.cuda.Event()
+                        ev.record(copy_stream)
+                        done.append(ev)
+            for i in range(w0, min(len(leaves), w0 + W)):
+                if host is not None:
+                    stream.wait_event(done[i - w0])
+                H.hapod_push(ctx, leaves[i], gen.bufs[i - w0].t())
+            if w0 + W >= len(leaves):
+                s, U, st = H.hapod_result(ctx, device=device)
+                if host is not None:
+                    Uh = U.cpu()
+                    d2h = Uh.numel() * Uh.element_size() + s.numel() * 8
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            if timed:
+                gen_ms[0] += g0.elapsed_time(g1)
+        if profile:
+            prof = H.hapod_profile(ctx)
+            for k, v in prof.items():
+                d = info.setdefault(k, {"ms": 0.0, "launches": 0, "bytes": 0.0, "flops": 0.0})
+                for f in d:
+                    d[f] += v[f]
+            launches[0] += sum(v["launches"] for v in prof.values())
+            info["_nodes"] = [H.hapod_node_stats(ctx, a) for a in range(len(parent))]
+            info["_k"] = int(s.numel())
+            info["_status"] = int(st)
+            info["_sigma"] = s.numpy().tolist()
+        H.hapod_destroy(ctx)
+        return ms, d2h
+
+    for _ in range(warmup):
+        step(False, False)
+    dist_ctx.barrier()
+    tot, d2h = 0.0, 0
+    for _ in range(steps):
+        ms, d2h = step(True, True)
+        tot += ms
+    dist_ctx.barrier()
+    ms = dist_ctx.max(tot / steps)
+    es = 4 if dtype == torch.float32 else 8
+    alg_bytes = sum(es * wl["n"] * (2 * st_["m"] + max(0, st_["k"])) for st_ in info["_nodes"] if st_["m"] > 0)
+    per = {k: {f: v[f] / steps for f in v} for k, v in info.items() if not k.startswith("_")}
+    res = {"ms": ms, "alg_bytes": alg_bytes, "steps": per, "launches_per_step": launches[0] // steps,
+           "k": info["_k"], "status": info["_status"], "sigma": info["_sigma"], "nodes": info["_nodes"],
+           "gen_ms": gen_ms[0] / steps, "parent": parent, **_rank_summary(parent, info["_nodes"])}
+    if host is not None:
+        res["h2d_bytes"] = sum(h.numel() * h.element_size() for h in host) * (len(leaves) // W)
+        res["d2h_bytes"] = d2h
+    del gen
+    torch.cuda.empty_cache()
+    return res
+
+
+def _rank_summary(parent, nodes):
+    return {"max_inner_k": max([st_["k"] for a, st_ in enumerate(nodes) if st_["level"] > 1 and parent[a] >= 0]
+                               or [0]),
+            "max_intermediate_k": max([st_["k"] for a, st_ in enumerate(nodes) if parent[a] >= 0] or [0]),
+            "leaf_k": max(st_["k"] for st_ in nodes if st_["level"] == 1)}
+
+
+# ----------------------------------------------------------------- FP64 workload (resident)
 def make_inputs(dtype, device):
     import numpy as np
     import torch
@@ -139,10 +308,10 @@ def make_inputs(dtype, device):
     return bufs, fro2
 
 
-def tree():
+def tree(kind="binary"):
     from paper_1607_05210_gb300 import synth
 
-    parent = synth.balanced_tree(2, TREE_DEPTH)
+    parent = synth.balanced_tree(2, TREE_DEPTH) if kind == "binary" else synth.star_tree(LEAVES)
     leaves = synth.leaves_of(parent)
     cols = [0] * len(parent)
     for a in leaves:
@@ -150,9 +319,9 @@ def tree():
     return parent, leaves, cols
 
 
-# ----------------------------------------------------------------- our arm
 def run_form(H, precision, bufs, fro2, steps, warmup, stream, dist_ctx, eps_rel=EPS_REL, shape=None,
              omega=OMEGA, n_rows=N_ROWS):
+    """One HAPOD per step over resident leaves: create, push every leaf, result, destroy."""
     import torch
 
     parent, leaves, cols = shape if shape is not None else tree()
@@ -194,77 +363,18 @@ def run_form(H, precision, bufs, fro2, steps, warmup, stream, dist_ctx, eps_rel=
     dist_ctx.barrier()
     ms = ev0.elapsed_time(ev1) / steps
     ms = dist_ctx.max(ms)
-    # algorithmic bytes of the whole HAPOD (b n (2 m + k) per node)
-    es = 4 if precision == H.HAPOD_MIXED_TF32X3 else 8
+    es = 4 if H.DTYPE[precision] == torch.float32 else 8
     alg_bytes = sum(es * n_rows * (2 * st_["m"] + max(0, st_["k"])) for st_ in info["_nodes"] if st_["m"] > 0)
     per = {k: {f: v[f] / steps for f in v} for k, v in info.items() if not k.startswith("_")}
     return {"ms": ms, "alg_bytes": alg_bytes, "steps": per, "launches_per_step": launches[0] // steps,
-            "k": info["_k"], "status": info["_status"],
-            "max_inner_k": max([st_["k"] for a, st_ in enumerate(info["_nodes"])
-                                if st_["level"] > 1 and parent[a] >= 0] or [0]),
-            "max_intermediate_k": max([st_["k"] for a, st_ in enumerate(info["_nodes"]) if parent[a] >= 0] or [0]),
-            "leaf_k": max(st_["k"] for st_ in info["_nodes"] if st_["level"] == 1)}
+            "k": info["_k"], "status": info["_status"], **_rank_summary(parent, info["_nodes"])}
 
 
-E2E_PENDING = 4  # leaves per processing batch in the end-to-end run (max_pending_leaves)
-
-
-def run_e2e(H, precision, host_bufs, dev_bufs, fro2, steps, stream):
-    """Same HAPOD through the public API from pinned host buffers: H2D of every leaf and
-    D2H of the result (sigma, modes) inside the timed region.  The leaf copies are
-    queued up front on a copy stream; each push waits for its leaf's copy, and the
-    context processes leaves in batches of E2E_PENDING (max_pending_leaves, Sec. 3.4)
-    so that the copies of later leaves overlap the processing of earlier ones."""
-    import torch
-
-    parent, leaves, cols = tree()
-    eps = EPS_REL * math.sqrt(fro2)
-    h2d = sum(b.numel() * b.element_size() for b in host_bufs)
-    d2h = [0]
-    copy_stream = torch.cuda.Stream(dev_bufs[0].device)
-    cev = [torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
-
-    def step():
-        ctx = H.hapod_create(parent, cols, eps, OMEGA, N_ROWS, precision, stream=stream,
-                             max_pending_leaves=E2E_PENDING)
-        copy_stream.wait_stream(stream)
-        done = []
-        with torch.cuda.stream(copy_stream):
-            cev[0].record(copy_stream)
-            for i in range(len(leaves)):
-                dev_bufs[i].copy_(host_bufs[i], non_blocking=True)
-                ev = torch.cuda.Event()
-                ev.record(copy_stream)
-                done.append(ev)
-            cev[1].record(copy_stream)
-        for i, a in enumerate(leaves):
-            stream.wait_event(done[i])
-            H.hapod_push(ctx, a, dev_bufs[i].t())
-        s, U, st = H.hapod_result(ctx, device=dev_bufs[0].device)
-        Uh = U.cpu()
-        d2h[0] = Uh.numel() * Uh.element_size() + s.numel() * 8
-        H.hapod_destroy(ctx)
-
-    step()
-    torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(stream):
-        ev0.record(stream)
-        for _ in range(steps):
-            step()
-        ev1.record(stream)
-    torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1) / steps
-    copy_ms = cev[0].elapsed_time(cev[1])  # the last step's leaf uploads alone
-    return {"value": LEAVES * COLS / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h[0],
-            "ms_per_step": ms, "h2d_ms": copy_ms, "h2d_gbs": h2d / (copy_ms / 1e3) / 1e9}
-
-
+# ----------------------------------------------------------------- roofline
 # DRAM traffic of the dominant kernels, from one ncu capture per kernel
-# (dram__bytes_read.sum + dram__bytes_write.sum of a single launch), stored in
-# profiles/traffic.json with the SHA-256 of the kernel's source file at capture
-# time.  A kernel whose source changed since then reports traffic = null.
+# (dram__bytes_read.sum + dram__bytes_write.sum of a single launch, scaled to the
+# workload's launch where stated), stored with the SHA-256 of the kernel's source
+# file at capture time.  A kernel whose source changed since then reports null.
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
 
@@ -288,71 +398,105 @@ def kernel_traffic(kernel: str):
     return float(rec["bytes_per_launch"]), rec["note"]
 
 
-def f64_alu(precision, H):
-    """Steps that run on the FP64 FMA pipe: every FP64-ALU step, the X V of the digit-slice form."""
-    return precision in (H.HAPOD_FP64, H.HAPOD_FP64_OZAKI)
+GRAM_KERNEL = {2: "gram_oz_kernel", 4: "gram_fx3_kernel", 3: "gram_bf3_kernel", 1: "gram_tc_kernel",
+               0: "gram_f64_tiles"}
 
 
-def roofline(res, precision, H, hbm, bf16, dom=None):
+def roofline(res, precision, H, hbm, dom=None):
+    """Roofline of the dominant step on the method's algorithmic bytes: the Gram pass
+    reads b n m bytes per node (the library's step accounting); achieved = those bytes
+    over the step's CUDA-event time."""
     steps = res["steps"]
     if dom is None:
         dom = max((k for k in steps if steps[k]["launches"] > 0), key=lambda k: steps[k]["ms"])
     d = steps[dom]
-    if precision == H.HAPOD_FP64_OZAKI and dom == "gram":
-        # the method's bytes: one pass over the FP64 snapshots, b n m per node (the
-        # library's step accounting); the digit-pair tensor work (28 fp16 products per
-        # FP64 product of the upper triangle) is reported beside it
-        ach = d["bytes"] / (d["ms"] / 1e3) / 1e9
-        traffic, note = kernel_traffic("gram_oz_kernel")
-        return dom, {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                     "traffic": traffic, "traffic_note": note,
-                     "digit_tflops": 28.0 * d["flops"] / (d["ms"] / 1e3) / 1e12,
-                     "kernel": "gram_oz_kernel + oz_reduce_kernel (tcgen05 fp16 digit-pair MMAs); achieved = "
-                               "8 n m algorithmic bytes per node over the step's CUDA-event time; digit_tflops = "
-                               "28 fp16 pair products per FP64 product of the upper triangle over the same time"}
-    if f64_alu(precision, H) and dom in ("gram", "modes"):
+    if precision == H.HAPOD_FP64 and dom in ("gram", "modes"):
         ach = d["flops"] / (d["ms"] / 1e3) / 1e12
         return dom, {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
                      "kernel": f"{dom} (FP64 FMA pipe; peak = nominal GB300 FP64 rate)"}
     if dom in ("gram", "modes"):
         ach = d["bytes"] / (d["ms"] / 1e3) / 1e9
-        return dom, {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                     "traffic": None, "kernel": dom}
+        kern = GRAM_KERNEL.get(precision, dom) if dom == "gram" else dom
+        traffic, note = kernel_traffic(kern)
+        out = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": traffic,
+               "traffic_note": note, "kernel": kern,
+               "definition": f"achieved = b n m algorithmic bytes per node summed over the {dom} step's nodes, over "
+                             "that step's CUDA-event time (launches on the context stream)",
+               "launches_per_step": d["launches"], "bytes_per_step": d["bytes"], "ms_per_step": d["ms"]}
+        if precision == H.HAPOD_FP64_OZAKI and dom == "gram":
+            out["digit_tflops"] = 28.0 * d["flops"] / (d["ms"] / 1e3) / 1e12
+        return dom, out
     return dom, {"bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None,
                  "kernel": dom}
 
 
-# ----------------------------------------------------------------- oracle
-def oracle_sample():
-    """A 256-column leaf of the same trajectory type at n/16 rows, FP64, with the leaf
-    tolerance of the tree (Thm. cor:hapod_bound) computed from the sample's own RMS
-    snapshot norm."""
+def summarise(r, precision, H, eps_rel, total_cols, hbm, peak_src, world, dom=None):
+    d, roof = roofline(r, precision, H, hbm, dom)
+    roof["peak_source"] = peak_src if roof["bound"] in ("hbm", "tensor") else "nominal"
+    out = {"eps_rel": eps_rel, "value": total_cols / (r["ms"] / 1e3), "unit": UNIT, "ms_per_step": r["ms"],
+           "gb_per_s": r["alg_bytes"] / (r["ms"] / 1e3) / 1e9 * world,
+           "hbm_frac": r["alg_bytes"] / (r["ms"] / 1e3) / 1e9 / hbm,
+           "k_root": r["k"], "max_leaf_k": r["leaf_k"], "max_inner_k": r["max_inner_k"], "status": r["status"],
+           "launches_per_step": r["launches_per_step"],
+           "step_ms": {k: v["ms"] for k, v in r["steps"].items()}, "roofline": roof}
+    if "gen_ms" in r:
+        out["generation_ms_per_step"] = r["gen_ms"]
+    return out
+
+
+# ----------------------------------------------------------------- oracle (CPU baseline)
+ORACLE_ROWS = (4096, 8192)
+
+
+def time_oracle(reps: int = 1):
+    """Whole-tree oracle time of the headline workload, extrapolated: the oracle POD of
+    leaf 0 (128 columns) and of its level-2 parent (the four leaves' outputs) at two
+    reduced row counts, fitted as a + b n per node kind and summed over the tree's
+    256 leaves and 85 inner nodes at n = 2^22."""
+    import numpy as np
+
     import oracle
     from paper_1607_05210_gb300 import synth
 
-    X = synth.advection_diffusion(ORACLE_SAMPLE_ROWS, COLS, SEED)
-    parent, leaves, cols = tree()
-    eps_star = EPS_REL * math.sqrt(float((X * X).sum()) / COLS)
-    return X, oracle.tolerances(parent, cols, eps_star, OMEGA)[leaves[0]]
+    parent, leaves, cols = c3_tree()
+    S = sum(cols)
+    P = synth.pulse_workload(C3["seed"])
+    kids0 = [a for a in range(len(parent)) if parent[a] == parent[leaves[0]]]
+    t_leaf, t_inner, wall = [], [], 0.0
+    for n in ORACLE_ROWS:
+        data = {a: synth.pulse_snapshots(n, leaves.index(a) * C3["cols"], C3["cols"], P, np.float32).astype(np.float64)
+                for a in kids0}
+        fro2_est = sum(float(np.sum(x * x)) for x in data.values()) * (C3["leaves"] / len(kids0))
+        eps_nodes = oracle.tolerances(parent, cols, C3["eps_rel"] * math.sqrt(fro2_est) / math.sqrt(S), C3["omega"])
+        tl, ti = [], []
+        for _ in range(reps):
+            outs = []
+            t0 = time.perf_counter()
+            for a in kids0:
+                outs.append(oracle.pod(data[a], eps_nodes[a]).Y)
+            t1 = time.perf_counter()
+            oracle.pod(np.asfortranarray(np.concatenate(outs, axis=1)), eps_nodes[parent[kids0[0]]])
+            t2 = time.perf_counter()
+            tl.append((t1 - t0) / len(kids0))
+            ti.append(t2 - t1)
+            wall += t2 - t0
+        t_leaf.append(min(tl))
+        t_inner.append(min(ti))
+    n0, n1 = ORACLE_ROWS
+    N = C3["n"]
 
+    def extrap(t):
+        b = max(0.0, (t[1] - t[0]) / (n1 - n0))
+        return t[1] + b * (N - n1)
 
-def time_oracle(steps: int, warmup: int):
-    import oracle
-
-    X, eps_leaf = oracle_sample()
-    for _ in range(warmup):
-        oracle.pod(X, eps_leaf)
-    t = []
-    for _ in range(steps):
-        t0 = time.perf_counter()
-        oracle.pod(X, eps_leaf)
-        t.append(time.perf_counter() - t0)
-    sec = statistics.median(t)
-    # cols/s of a full-length leaf: the oracle's cost is linear in the rows (QR + n-length reflectors)
-    value = COLS / (sec * (N_ROWS / ORACLE_SAMPLE_ROWS))
+    inner = sum(1 for a in range(len(parent)) if cols[a] == 0)
+    total = len(leaves) * extrap(t_leaf) + inner * extrap(t_inner)
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return value, sec, cores
+    sample = (f"oracle POD of leaf 0 and of its level-2 parent at n = {n0} and {n1} rows ({wall:.1f} s of CPU time "
+              f"over {reps} repetition(s)); per node kind time fitted as a + b n and summed over {len(leaves)} "
+              f"leaves + {inner} inner nodes at n = 2^22: {total:.0f} s per HAPOD")
+    return S / total, total, wall, cores, sample
 
 
 # ----------------------------------------------------------------- distributed
@@ -392,6 +536,7 @@ class Dist:
             self.pg.destroy_process_group()
 
 
+# ----------------------------------------------------------------- sweeps (Sec. 4.2, 4.3)
 SWEEP_OMEGAS = (0.1, 0.25, 0.5, 0.75, 0.9, 0.95, 0.99, 0.999)
 SWEEP_PARTITIONS = ((10, 1000), (40, 250), (100, 100), (400, 25), (1000, 10))  # blocks x columns (10^4)
 SWEEP_DEPTHS = (2, 3, 4, 5)
@@ -426,7 +571,7 @@ def run_sweep(kind, H, device, dist_ctx):
         k_pod = direct_pod_rank(sig, EPS_REL * math.sqrt(fro2))
         for w in SWEEP_OMEGAS:
             r = run_form(H, prec, bufs, fro2, 2, 1, stream, dist_ctx, EPS_REL, omega=w)
-            print(json.dumps({"sweep": "omega", "omega": w, "workload": WORKLOAD.replace("omega=0.5", f"omega={w}"),
+            print(json.dumps({"sweep": "omega", "omega": w, "workload": C2_WORKLOAD.replace("omega=0.5", f"omega={w}"),
                               "value": LEAVES * COLS / (r["ms"] / 1e3), "unit": UNIT, "ms_per_step": r["ms"],
                               "k_root": r["k"], "direct_pod_k": k_pod, "additional_modes": r["k"] - k_pod,
                               "max_intermediate_k": r["max_intermediate_k"], "status": r["status"]}), flush=True)
@@ -455,28 +600,124 @@ def run_sweep(kind, H, device, dist_ctx):
                               "status": r["status"], "n": N_ROWS, "eps_rel": EPS_REL, "omega": OMEGA}), flush=True)
 
 
+# ----------------------------------------------------------------- profiling cases
+def profile_case(args, H, device):
+    """Small cases for ncu captures: three Gram calls (and X V where named) on one leaf."""
+    import torch
+
+    from paper_1607_05210_gb300 import synth
+
+    form = args.profile_form
+    if form in ("fx3-node", "oz-node"):
+        return profile_node(H, device, H.HAPOD_MIXED_FX3 if form == "fx3-node" else H.HAPOD_FP64_OZAKI)
+    if form in ("fx3", "bf3"):
+        prec = H.HAPOD_MIXED_FX3 if form == "fx3" else H.HAPOD_MIXED_BF16X3
+        X = H.colmajor_empty(C3["n"], C3["cols"], torch.float32, device)
+        H.hapod_synth_snapshots(c3_params(H), C3["n"], 0, C3["cols"], X)
+        V = torch.randn((90, C3["cols"]), dtype=torch.float64, device=device).t() / 16.0
+        for _ in range(3):
+            G = H.hapod_gram(X, prec)
+            Y = H.hapod_modes(X, V, 90, None, prec)
+        torch.cuda.synchronize()
+        return {"G00": float(G[0, 0]), "Y00": float(Y[0, 0])}
+    if form in ("fp64", "mixed"):
+        cols, dtype, prec = ((64, torch.float64, H.HAPOD_FP64) if form == "fp64"
+                             else (COLS, torch.float32, H.HAPOD_MIXED_TF32X3))
+        X = synth.advection_diffusion_device(N_ROWS, cols, SEED, dtype, device).t()
+        for _ in range(3):
+            G = H.hapod_gram(X, prec)
+        torch.cuda.synchronize()
+        return {"G00": float(G[0, 0])}
+    torch.manual_seed(SEED)
+    X = torch.randn((COLS, N_ROWS), dtype=torch.float64, device=device).t()
+    V = torch.randn((19, COLS), dtype=torch.float64, device=device).t() / 16.0
+    for _ in range(2):
+        G = H.hapod_gram(X, H.HAPOD_FP64_OZAKI)
+        Y = H.hapod_modes(X, V, 19, None, H.HAPOD_FP64_OZAKI)
+    torch.cuda.synchronize()
+    return {"G00": float(G[0, 0]), "Y00": float(Y[0, 0])}
+
+
+def profile_node(H, device, precision):
+    """One level-2 node of the headline workload and its four leaves: the leaves' PODs
+    (generated on the device, leaf tolerance of the tree) and the POD of the node on
+    their concatenated outputs, each step timed with CUDA events (2 repetitions)."""
+    import torch
+
+    wl = C3
+    parent, leaves, cols = c3_tree(wl)
+    dtype = H.DTYPE[precision]
+    params = c3_params(H, wl)
+    Xs = []
+    for i in range(4):
+        X = H.colmajor_empty(wl["n"], wl["cols"], dtype, device)
+        H.hapod_synth_snapshots(params, wl["n"], i * wl["cols"], wl["cols"], X)
+        Xs.append(X)
+    fro2_cols = sum(float(torch.linalg.vector_norm(X, dtype=torch.float64) ** 2) for X in Xs) / (4 * wl["cols"])
+    eps_star = wl["eps_rel"] * math.sqrt(fro2_cols)
+    eps_leaf = math.sqrt(wl["cols"] / (wl["depth"]) * (1 - wl["omega"] ** 2)) * eps_star
+    eps_l2 = math.sqrt(4 * wl["cols"] / (wl["depth"]) * (1 - wl["omega"] ** 2)) * eps_star
+    out = {}
+
+    def timed(name, f):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = f()
+        e1.record()
+        torch.cuda.synchronize()
+        out.setdefault(name, []).append(round(e0.elapsed_time(e1), 3))
+        return r
+
+    for rep in range(2):
+        Ys = []
+        for i, X in enumerate(Xs):
+            timed("leaf_gram", lambda: H.hapod_gram(X, precision))
+            N, s, Y, tail, st = timed("leaf_pod", lambda: H.hapod_pod(X, eps_leaf, precision))
+            Ys.append(Y)
+        Xin = H.colmajor_empty(wl["n"], sum(Y.shape[1] for Y in Ys), dtype, device)
+        off = 0
+        for Y in Ys:
+            Xin[:, off:off + Y.shape[1]].copy_(Y)
+            off += Y.shape[1]
+        G = timed("node_gram", lambda: H.hapod_gram(Xin, precision))
+        lam, V, sw, st = timed("node_eig", lambda: H.hapod_eig(G, precision))
+        N, tail = H.hapod_truncate(lam, eps_l2)
+        timed("node_modes", lambda: H.hapod_modes(Xin, V, N, None, precision))
+        Nn, s, Y, tail, st = timed("node_pod", lambda: H.hapod_pod(Xin, eps_l2, precision))
+        out["node_m"] = Xin.shape[1]
+        out["node_k"] = Nn
+        out["node_sweeps"] = sw
+        out["leaf_k"] = [Y.shape[1] for Y in Ys]
+        del Xin, Ys
+    return out
+
+
+# ----------------------------------------------------------------- main
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--forms", default="mixed,fp64,oz",
-                    help="comma list of forms: 'oz' (digit-slice FP64, the headline when present), "
-                         "'fp64' (FP64 ALU), 'mixed' (FP32 snapshots at eps = 1e-2)")
+    ap.add_argument("--workloads", default="c2",
+                    help="comma list of extra workloads beside the headline: 'c2' (FP64 advection-diffusion, "
+                         "binary tree and star, resident), 'none'")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64-form", action="store_true", help="skip the digit-slice FP64 form of the headline")
     ap.add_argument("--profile-leaf", action="store_true",
-                    help="run two digit-slice Gram + X V calls on one 2^20 x 256 FP64 leaf (k = 19) and exit: "
-                         "the small case for ncu captures of oz_split / gram_oz / modes_oz")
-    ap.add_argument("--profile-form", choices=["oz", "fp64", "mixed"], default="oz",
-                    help="with --profile-leaf: 'fp64' runs three FP64 Gram calls on a 2^20 x 64 "
-                         "advection-diffusion leaf (gram_f64_tiles), 'mixed' three mixed-form Gram calls on a "
-                         "2^20 x 256 FP32 one (gram_tc_kernel)")
+                    help="run the small per-leaf case named by --profile-form and exit (for ncu captures)")
+    ap.add_argument("--profile-form", choices=["oz", "fp64", "mixed", "fx3", "bf3", "fx3-node", "oz-node"],
+                    default="fx3",
+                    help="with --profile-leaf: 'fx3'/'bf3' three Gram + X V calls on one 2^22 x 128 FP32 leaf of "
+                         "the headline workload; 'oz' two digit-slice Gram + X V calls on a 2^20 x 256 FP64 leaf; "
+                         "'fp64' three FP64 Gram calls on 2^20 x 64; 'mixed' three TF32 Gram calls on 2^20 x 256; "
+                         "'fx3-node' / 'oz-node' the PODs of four headline leaves and of their level-2 parent, "
+                         "each step timed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep", choices=["omega", "trees"],
-                    help="print one JSON line per configuration and exit: 'omega' runs the benchmark "
-                         "workload for omega in 0.1 .. 0.999 (Sec. 4.3); 'trees' runs 10^4 advection-diffusion "
-                         "columns in 10 x 1000 .. 1000 x 10 blocks on balanced trees of edge depth 2..5 (Sec. 4.2)")
+                    help="print one JSON line per configuration and exit: 'omega' runs the FP64 workload for "
+                         "omega in 0.1 .. 0.999 (Sec. 4.3); 'trees' runs 10^4 advection-diffusion columns in "
+                         "10 x 1000 .. 1000 x 10 blocks on balanced trees of edge depth 2..5 (Sec. 4.2)")
     args = ap.parse_args()
     os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
     dist_ctx = Dist()
@@ -485,13 +726,18 @@ def main():
         if dist_ctx.rank != 0:
             dist_ctx.close()
             return
-        value, sec, cores = time_oracle(args.steps, args.warmup)
-        sample = (f"oracle POD (Householder QR + one-sided Jacobi, FP64) of one 256-column leaf at n/16 = "
-                  f"{ORACLE_SAMPLE_ROWS} rows per step, {sec:.2f} s; columns/s scaled to full-length leaves")
+        vals = []
+        for _ in range(args.warmup):
+            time_oracle()
+        sample = cores = None
+        for _ in range(args.steps):
+            v, total, wall, cores, sample = time_oracle()
+            vals.append(v)
+        value = statistics.median(vals)
         print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": C3["leaves"] * C3["cols"] / value * 1e3,
                           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                          "data": "synthetic", "config": {"workload": WORKLOAD, "form": "cpu oracle"},
+                          "data": "synthetic", "config": {"workload": C3_WORKLOAD, "form": "cpu oracle"},
                           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                                            "sample": sample},
                           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
@@ -504,137 +750,88 @@ def main():
     device = torch.device("cuda", dist_ctx.local)
     from paper_1607_05210_gb300 import hapod as H
 
-    if args.profile_leaf and args.profile_form != "oz":
-        from paper_1607_05210_gb300 import synth
-
-        cols, dtype, prec = ((64, torch.float64, H.HAPOD_FP64) if args.profile_form == "fp64"
-                             else (COLS, torch.float32, H.HAPOD_MIXED_TF32X3))
-        X = synth.advection_diffusion_device(N_ROWS, cols, SEED, dtype, device).t()  # column-major n x cols
-        for _ in range(3):
-            G = H.hapod_gram(X, prec)
-        torch.cuda.synchronize()
-        print(json.dumps({"profile_leaf": True, "form": args.profile_form, "G00": float(G[0, 0])}))
-        dist_ctx.close()
-        return
     if args.profile_leaf:
-        torch.manual_seed(SEED)
-        X = torch.randn((COLS, N_ROWS), dtype=torch.float64, device=device).t()  # column-major n x m
-        V = torch.randn((19, COLS), dtype=torch.float64, device=device).t() / 16.0
-        for _ in range(2):
-            G = H.hapod_gram(X, H.HAPOD_FP64_OZAKI)
-            Y = H.hapod_modes(X, V, 19, None, H.HAPOD_FP64_OZAKI)
-        torch.cuda.synchronize()
-        print(json.dumps({"profile_leaf": True, "G00": float(G[0, 0]), "Y00": float(Y[0, 0])}))
+        print(json.dumps({"profile_leaf": True, "form": args.profile_form, **profile_case(args, H, device)}))
         dist_ctx.close()
         return
-
     if args.sweep:
         if dist_ctx.rank == 0:
             run_sweep(args.sweep, H, device, dist_ctx)
         dist_ctx.close()
         return
 
-    hbm, bf16, peak_src = _peaks()
+    hbm, _, peak_src = _peaks()
     stream = torch.cuda.Stream(device)
-    total_cols = LEAVES * COLS * dist_ctx.world
-
-    def summarise(r, precision, eps_rel, dom=None):
-        d, roof = roofline(r, precision, H, hbm, bf16, dom)
-        roof["peak_source"] = peak_src if roof["bound"] in ("hbm", "tensor") else "nominal"
-        return {"eps_rel": eps_rel, "value": total_cols / (r["ms"] / 1e3), "unit": UNIT, "ms_per_step": r["ms"],
-                "gb_per_s": r["alg_bytes"] / (r["ms"] / 1e3) / 1e9 * dist_ctx.world,
-                "k_root": r["k"], "max_leaf_k": r["leaf_k"], "max_inner_k": r["max_inner_k"],
-                "step_ms": {k: v["ms"] for k, v in r["steps"].items()}, "roofline": roof}
-
+    world = dist_ctx.world
+    total_c3 = C3["leaves"] * C3["cols"] * world
     forms = {}
-    # pinned host buffers for the end-to-end leg, allocated before any device work
+
+    # pinned host buffers for one wave (end-to-end leg), before device work
     host = None
     if not args.no_e2e:
         try:
-            host = [torch.empty((COLS, N_ROWS), dtype=torch.float64, pin_memory=True) for _ in range(LEAVES)]
+            host = [torch.empty((C3["cols"], C3["n"]), dtype=torch.float32, pin_memory=True)
+                    for _ in range(C3["wave"])]
         except (RuntimeError, MemoryError) as ex:
             host = str(ex)[:120]
-    # mixed form at the tolerance its precision floor supports
-    if "mixed" in args.forms:
-        bufs, fro2 = make_inputs(torch.float32, device)
-        try:
-            rm = run_form(H, H.HAPOD_MIXED_TF32X3, bufs, fro2, args.steps, args.warmup, stream, dist_ctx,
-                          MIXED_EPS_REL)
-            forms[f"mixed@{MIXED_EPS_REL:g}"] = summarise(rm, H.HAPOD_MIXED_TF32X3, MIXED_EPS_REL, "gram")
-            forms[f"mixed@{MIXED_EPS_REL:g}"]["launches_per_step"] = rm["launches_per_step"]
-        except H.HapodError as e:
-            forms[f"mixed@{MIXED_EPS_REL:g}"] = {"unavailable": str(e)}
+
+    fro2 = c3_fro2(H, C3, device, stream)
+    sampler = ClockSampler(dist_ctx.local)
+    head = run_waves(H, H.HAPOD_MIXED_FX3, C3, fro2, args.steps, args.warmup, stream, dist_ctx)
+    clocks = sampler.stop()
+    head_key = f"mixed_fx3@{C3['eps_rel']:g}"
+    forms[head_key] = summarise(head, H.HAPOD_MIXED_FX3, H, C3["eps_rel"], total_c3, hbm, peak_src, world, "gram")
+    e2e = None
+    if not args.no_e2e:
+        if isinstance(host, list):
+            r = run_waves(H, H.HAPOD_MIXED_FX3, C3, fro2, args.steps, 1, stream, dist_ctx, host=host)
+            e2e = {"value": total_c3 / (r["ms"] / 1e3), "unit": UNIT, "h2d_bytes_per_step": r["h2d_bytes"],
+                   "d2h_bytes_per_step": r["d2h_bytes"], "ms_per_step": r["ms"], "form": head_key,
+                   "steps": args.steps, "note": "per wave: uploads of the 16 leaves from pinned host memory on a copy "
+                                               "stream, each push waiting for its leaf, then the wave's processing; "
+                                               "the root's modes and sigma read back"}
+        else:
+            e2e = {"value": None, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                   "note": f"pinned host buffers unavailable: {host}"}
+        host = None
+    if not args.no_fp64_form:
+        r64 = run_waves(H, H.HAPOD_FP64_OZAKI, C3, fro2, args.steps, 1, stream, dist_ctx)
+        k64 = f"fp64_ozaki@{C3['eps_rel']:g}"
+        forms[k64] = summarise(r64, H.HAPOD_FP64_OZAKI, H, C3["eps_rel"], total_c3, hbm, peak_src, world, "gram")
+        forms[head_key]["speedup_vs_fp64_form_same_eps"] = r64["ms"] / head["ms"]
+        s1, s2 = head["sigma"], r64["sigma"]
+        k = min(len(s1), len(s2))
+        forms[head_key]["vs_fp64_form"] = {
+            "k_root": [len(s1), len(s2)],
+            "max_rel_sigma_diff_above_1e-5": max([abs(s1[j] - s2[j]) / s2[j] for j in range(k)
+                                                  if s2[j] >= 1e-5 * s2[0]] or [0.0])}
+
+    workloads = {}
+    if "c2" in args.workloads:
+        bufs, fro2_c2 = make_inputs(torch.float64, device)
+        total_c2 = LEAVES * COLS * world
+        for kind in ("binary", "star"):
+            shape = tree(kind)
+            r = run_form(H, H.HAPOD_FP64_OZAKI, bufs, fro2_c2, max(1, min(args.steps, 3)), 1, stream, dist_ctx,
+                         EPS_REL, shape=shape)
+            workloads[f"c2_{kind}/fp64_ozaki@{EPS_REL:g}"] = summarise(r, H.HAPOD_FP64_OZAKI, H, EPS_REL, total_c2,
+                                                                      hbm, peak_src, world)
+        r = run_form(H, H.HAPOD_FP64, bufs, fro2_c2, 1, 1, stream, dist_ctx, EPS_REL, shape=tree("binary"))
+        workloads[f"c2_binary/fp64@{EPS_REL:g}"] = summarise(r, H.HAPOD_FP64, H, EPS_REL, total_c2, hbm, peak_src,
+                                                            world)
+        workloads["c2_workload"] = C2_WORKLOAD + "; binary = balanced binary tree L_T=7, star = two-level (L_T=2)"
         del bufs
         torch.cuda.empty_cache()
-    # FP64 snapshots: the digit-slice form (headline) and the FP64 ALU form at the
-    # workload tolerance, then the FP64 ALU form at the mixed tolerance
-    bufs, fro2 = make_inputs(torch.float64, device)
-    head = head_prec = clocks = None
-    if "oz" in args.forms:
-        sampler = ClockSampler(dist_ctx.local)
-        head = run_form(H, H.HAPOD_FP64_OZAKI, bufs, fro2, args.steps, args.warmup, stream, dist_ctx, EPS_REL)
-        clocks = sampler.stop()
-        head_prec = H.HAPOD_FP64_OZAKI
-        forms[f"fp64_ozaki@{EPS_REL:g}"] = summarise(head, H.HAPOD_FP64_OZAKI, EPS_REL)
-    e2e = None
 
-    steps_e2e = args.steps
-
-    def measure_e2e(prec, key):
-        # right after the headline form, with the pool's cached blocks returned first
-        if not isinstance(host, list):
-            return {"value": None, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
-                    "note": f"pinned host buffers unavailable: {host}"}
-        H.hapod_trim_pool(stream)
-        for h_, b in zip(host, bufs):
-            h_.copy_(b)
-        # the link alone: one upload of every leaf with nothing else running
-        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with torch.cuda.stream(stream):
-            c0.record(stream)
-            for h_, b in zip(host, bufs):
-                b.copy_(h_, non_blocking=True)
-            c1.record(stream)
-        torch.cuda.synchronize()
-        idle_gbs = sum(h_.numel() * 8 for h_ in host) / (c0.elapsed_time(c1) / 1e3) / 1e9
-        r = run_e2e(H, prec, host, bufs, fro2, steps_e2e, stream)
-        r["form"] = key
-        r["max_pending_leaves"] = E2E_PENDING
-        r["h2d_gbs_alone"] = idle_gbs
-        return r
-
-    if not args.no_e2e and head is not None:
-        e2e = measure_e2e(head_prec, f"fp64_ozaki@{EPS_REL:g}")
-    if "fp64" in args.forms or head is None:
-        sampler = ClockSampler(dist_ctx.local)
-        alu = run_form(H, H.HAPOD_FP64, bufs, fro2, args.steps, args.warmup, stream, dist_ctx, EPS_REL)
-        alu_clocks = sampler.stop()
-        forms[f"fp64@{EPS_REL:g}"] = summarise(alu, H.HAPOD_FP64, EPS_REL)
-        if head is None:
-            head, head_prec, clocks = alu, H.HAPOD_FP64, alu_clocks
-            if not args.no_e2e:
-                e2e = measure_e2e(head_prec, f"fp64@{EPS_REL:g}")
-        else:
-            forms[f"fp64_ozaki@{EPS_REL:g}"]["speedup_vs_fp64_alu"] = alu["ms"] / head["ms"]
-    head_key = f"fp64_ozaki@{EPS_REL:g}" if head_prec == H.HAPOD_FP64_OZAKI else f"fp64@{EPS_REL:g}"
-    if "mixed" in args.forms:
-        r2 = run_form(H, H.HAPOD_FP64, bufs, fro2, max(1, min(args.steps, 2)), 1, stream, dist_ctx, MIXED_EPS_REL)
-        forms[f"fp64@{MIXED_EPS_REL:g}"] = summarise(r2, H.HAPOD_FP64, MIXED_EPS_REL)
-        mk = f"mixed@{MIXED_EPS_REL:g}"
-        if "value" in forms.get(mk, {}):
-            forms[mk]["speedup_vs_fp64_same_eps"] = forms[mk]["value"] / forms[f"fp64@{MIXED_EPS_REL:g}"]["value"]
-    del bufs
-    host = None
-    torch.cuda.empty_cache()
-
-    value = total_cols / (head["ms"] / 1e3)
     hs = forms[head_key]
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist_ctx.world, "steps": args.steps,
+        "metric": METRIC, "value": hs["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "form": head_key.split("@")[0], "parallelism": f"replicas x{dist_ctx.world}",
-                   "l2": "inputs larger than L2 (no flush needed)"},
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": C3_WORKLOAD, "form": "mixed_fx3", "parallelism": f"replicas x{world}",
+                   "l2": "every leaf (2 GiB) larger than L2; no flush needed",
+                   "timed": "sum over waves of the push-to-processed interval (generation between waves untimed, "
+                            "reported as generation_ms_per_step)", "seed": C3["seed"]},
         "gb_per_s": hs["gb_per_s"],
         "roofline": hs["roofline"],
         "gpu_launches": head["launches_per_step"] * args.steps,
@@ -644,11 +841,11 @@ def main():
                    "status": head["status"]},
         "step_ms": hs["step_ms"],
         "forms": forms,
+        "workloads": workloads,
     }
-    if dist_ctx.rank == 0 and dist_ctx.world == 1 and not args.no_cpu_baseline:
-        v, sec, cores = time_oracle(1, 0)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": f"one 256-column leaf at n/16 rows ({sec:.2f} s), scaled to full leaves"}
+    if dist_ctx.rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, total, wall, cores, sample = time_oracle()
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
     if dist_ctx.rank == 0:
         print(json.dumps(line))
     dist_ctx.close()

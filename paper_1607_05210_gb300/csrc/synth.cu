@@ -90,8 +90,7 @@ __global__ void __launch_bounds__(kRowsPerBlock) synth_field_kernel(hapod_synth_
                                                                     const ColumnInfo* __restrict__ info,
                                                                     T* __restrict__ X, int64_t ldx) {
   __shared__ float s_coef[kColChunk][2 * kHarmonics];
-  __shared__ int s_cnt[kColChunk];
-  __shared__ int s_list[kColChunk][HAPOD_SYNTH_MAX_PULSES];
+  __shared__ unsigned long long s_mask[kColChunk];  // pulses that reach the block's rows
   const int64_t r0 = (int64_t)blockIdx.x * kRowsPerBlock;
   const int64_t i = r0 + threadIdx.x;
   const bool live = i < n;
@@ -111,6 +110,7 @@ __global__ void __launch_bounds__(kRowsPerBlock) synth_field_kernel(hapod_synth_
   const double two_pi = 6.283185307179586476925286766559;
   const float h = (float)(two_pi / (double)n);
   const float inv2w2 = (float)(1.0 / (2.0 * p.pulse_width * p.pulse_width));
+  const float cut = (float)(9.0 * p.pulse_width);
   // rows within 9 w of a pulse centre, plus one for the offset
   const int64_t reach = (int64_t)ceil(9.0 * p.pulse_width / (two_pi / (double)n)) + 1;
   const int64_t r1 = min(n, r0 + kRowsPerBlock) - 1;  // last row of the block
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(kRowsPerBlock) synth_field_kernel(hapod_synth_
     __syncthreads();  // previous chunk done with the shared lists
     for (int e = threadIdx.x; e < nc * 2 * kHarmonics; e += blockDim.x)
       s_coef[e / (2 * kHarmonics)][e % (2 * kHarmonics)] = info[j0 + e / (2 * kHarmonics)].coef[e % (2 * kHarmonics)];
-    if (threadIdx.x < kColChunk) s_cnt[threadIdx.x] = 0;
+    if (threadIdx.x < kColChunk) s_mask[threadIdx.x] = 0ull;
     __syncthreads();
     // periodic row distance from each pulse row to the block's row interval [r0, r1]
     for (int e = threadIdx.x; e < nc * p.num_pulses; e += blockDim.x) {
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(kRowsPerBlock) synth_field_kernel(hapod_synth_
       int64_t d = 0;
       if (pr < r0) d = min(r0 - pr, pr + n - r1);
       else if (pr > r1) d = min(pr - r1, r0 + n - pr);
-      if (d <= reach) s_list[jj][atomicAdd(&s_cnt[jj], 1)] = q;
+      if (d <= reach) atomicOr(&s_mask[jj], 1ull << q);
     }
     __syncthreads();
     if (!live) continue;
@@ -136,14 +136,15 @@ __global__ void __launch_bounds__(kRowsPerBlock) synth_field_kernel(hapod_synth_
       float u = 0.f;
 #pragma unroll
       for (int k = 0; k < kHarmonics; ++k) u = fmaf(s_coef[jj][k], sv[k], fmaf(s_coef[jj][kHarmonics + k], cv[k], u));
-      const int cnt = s_cnt[jj];
-      for (int e = 0; e < cnt; ++e) {
-        const int q = s_list[jj][e];
+      // pulses in ascending order, so that every column range gives the same bits
+      for (unsigned long long mask = s_mask[jj]; mask; mask &= mask - 1ull) {
+        const int q = __ffsll((long long)mask) - 1;
         int64_t dr = i - info[j0 + jj].prow[q];  // periodic representative
         if (dr > n / 2) dr -= n;
         else if (dr < -(n / 2)) dr += n;
         if (dr > reach || dr < -reach) continue;
         const float d = fmaf((float)dr, h, info[j0 + jj].poff[q]);
+        if (fabsf(d) > cut) continue;
         u = fmaf((float)p.pulse_amp[q], expf(-d * d * inv2w2), u);
       }
       X[(size_t)(j0 + jj) * (size_t)ldx + (size_t)i] = (T)u;

@@ -76,7 +76,7 @@ def test_roofline_fields_for_the_digit_slice_gram():
 
     res = {"steps": {"gram": {"ms": 100.0, "launches": 64, "bytes": 1e9, "flops": 2e12},
                      "modes": {"ms": 50.0, "launches": 7, "bytes": 1e9, "flops": 1e11}}}
-    dom, roof = bench.roofline(res, H.HAPOD_FP64_OZAKI, H, 6786.2, 1725.3)
+    dom, roof = bench.roofline(res, H.HAPOD_FP64_OZAKI, H, 6786.2)
     assert dom == "gram" and roof["bound"] == "hbm" and roof["unit"] == "GB/s"
     assert roof["achieved"] == pytest.approx(1e9 / 0.1 / 1e9)
     assert roof["frac"] == pytest.approx(roof["achieved"] / 6786.2)
@@ -105,8 +105,26 @@ def test_mixed_gram_roofline_is_hbm_bound():
 
     res = {"steps": {"gram": {"ms": 100.0, "launches": 64, "bytes": 1e9, "flops": 2e12},
                      "modes": {"ms": 50.0, "launches": 7, "bytes": 1e9, "flops": 1e11}}}
-    dom, roof = bench.roofline(res, H.HAPOD_MIXED_TF32X3, H, 6786.2, 1725.3, "gram")
-    assert roof["bound"] == "hbm" and roof["achieved"] == pytest.approx(1e9 / 0.1 / 1e9)
+    for prec in (H.HAPOD_MIXED_TF32X3, H.HAPOD_MIXED_FX3, H.HAPOD_MIXED_BF16X3):
+        dom, roof = bench.roofline(res, prec, H, 6786.2, "gram")
+        assert roof["bound"] == "hbm" and roof["achieved"] == pytest.approx(1e9 / 0.1 / 1e9)
+        assert roof["frac"] == pytest.approx(10.0 / 6786.2)
+    assert bench.roofline(res, H.HAPOD_MIXED_FX3, H, 6786.2, "gram")[1]["kernel"] == "gram_fx3_kernel"
+
+
+def test_headline_tree_and_workload():
+    """The precision workload's tree: balanced quaternary of edge depth 4 (L_T = 5),
+    256 leaves x 128 columns, waves of 16 leaves = whole level-3 subtrees."""
+    parent, leaves, cols = bench.c3_tree()
+    assert len(leaves) == 256 and sum(cols) == 32768 and len(parent) == 341
+    levels = oracle.tree_levels(parent)
+    assert max(levels) == 5
+    W = bench.C3["wave"]
+    for w0 in range(0, 256, W):
+        anc = set()
+        for a in leaves[w0:w0 + W]:
+            anc.add(parent[parent[a]])
+        assert len(anc) == 1  # one level-3 node per wave
 
 
 def test_rank_within_accepts_only_ranks_of_nearby_tolerances():
