@@ -64,6 +64,14 @@ C3_WORKLOAD = ("travelling-pulse HAPOD (precision form), n=2^22 FP32 rows, 256 l
                "(32768 columns, 512 GiB generated on the device in waves of 16 leaves), quaternary tree L_T=5, "
                "eps=1e-4 rel, omega=0.5")
 
+# streamed incremental workload: 64 chunks of 64 columns, never all resident, on a
+# left-deep chain of four depth-4 binary subtrees (Sec. 3.2, skinny tree)
+C5 = {"name": "c5", "n": 1 << 23, "leaves": 64, "cols": 64, "subtrees": 4, "depth": 4, "eps_rel": 1e-4,
+      "omega": 0.5, "wave": 8, "seed": 1607052105}
+C5_WORKLOAD = ("streamed incremental HAPOD, n=2^23 FP32 rows, 4096 snapshots generated on the device in chunks of 64 "
+               "(2 GiB each, 8 chunks resident at a time), left-deep chain of 4 binary subtrees of depth 4 (L_T=8), "
+               "eps=1e-4 rel, omega=0.5")
+
 # FP64 advection-diffusion workload, resident
 N_ROWS = 1 << 20
 LEAVES = 64
@@ -137,10 +145,21 @@ class ClockSampler:
 
 # ----------------------------------------------------------------- precision workload (device-generated)
 def c3_tree(wl=C3):
+    """(parent, leaves in push order, cols): leaf i of the push order holds global
+    columns i * cols .. (i + 1) * cols - 1 of the trajectory."""
     from paper_1607_05210_gb300 import synth
 
-    parent = synth.balanced_tree(wl["arity"], wl["depth"])
-    leaves = synth.leaves_of(parent)
+    if wl["name"] == "c5":
+        parent = synth.chain_of_subtrees(wl["subtrees"], wl["depth"])
+        leaves = synth.leaves_of(parent)
+        # stream order: subtree 1 (deepest in the chain) first, then 2, 3, 4, so that each
+        # chain node can run as soon as its subtree has arrived
+        per = len(leaves) // wl["subtrees"]
+        blocks = [leaves[i:i + per] for i in range(0, len(leaves), per)]
+        leaves = [a for b in reversed(blocks) for a in b]
+    else:
+        parent = synth.balanced_tree(wl["arity"], wl["depth"])
+        leaves = synth.leaves_of(parent)
     cols = [0] * len(parent)
     for a in leaves:
         cols[a] = wl["cols"]
@@ -699,9 +718,10 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workloads", default="c2",
-                    help="comma list of extra workloads beside the headline: 'c2' (FP64 advection-diffusion, "
-                         "binary tree and star, resident), 'none'")
+    ap.add_argument("--workloads", default="c5,c2",
+                    help="comma list of extra workloads beside the headline: 'c5' (streamed incremental chain, "
+                         "device-generated chunks), 'c2' (FP64 advection-diffusion, binary tree and star, "
+                         "resident), 'none'")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true", help="skip the digit-slice FP64 form of the headline")
     ap.add_argument("--profile-leaf", action="store_true",
@@ -807,6 +827,18 @@ def main():
                                                   if s2[j] >= 1e-5 * s2[0]] or [0.0])}
 
     workloads = {}
+    if "c5" in args.workloads:
+        fro2_c5 = c3_fro2(H, C5, device, stream)
+        total_c5 = C5["leaves"] * C5["cols"] * world
+        st5 = max(1, min(args.steps, 2))
+        r5 = run_waves(H, H.HAPOD_MIXED_FX3, C5, fro2_c5, st5, 1, stream, dist_ctx)
+        r5b = run_waves(H, H.HAPOD_FP64_OZAKI, C5, fro2_c5, st5, 1, stream, dist_ctx)
+        k1 = f"c5/mixed_fx3@{C5['eps_rel']:g}"
+        workloads[k1] = summarise(r5, H.HAPOD_MIXED_FX3, H, C5["eps_rel"], total_c5, hbm, peak_src, world, "gram")
+        workloads[f"c5/fp64_ozaki@{C5['eps_rel']:g}"] = summarise(r5b, H.HAPOD_FP64_OZAKI, H, C5["eps_rel"], total_c5,
+                                                                 hbm, peak_src, world, "gram")
+        workloads[k1]["speedup_vs_fp64_form_same_eps"] = r5b["ms"] / r5["ms"]
+        workloads["c5_workload"] = C5_WORKLOAD
     if "c2" in args.workloads:
         bufs, fro2_c2 = make_inputs(torch.float64, device)
         total_c2 = LEAVES * COLS * world

@@ -662,9 +662,13 @@ bool step_modes_fx(Env& env, std::vector<Work*>& ws) {
     const int mode_tiles = (k + MT - 1) / MT;
     uint16_t* vdig = (uint16_t*)env.alloc(fx_vdig_bytes(w->m, k), "alloc V digits");
     int32_t* fexp = (int32_t*)env.alloc(sizeof(int32_t) * mode_tiles * MT, "alloc mode exponents");
+    float2* xscale = (float2*)env.alloc(fx_xscale_bytes(w->m), "alloc column scales");
+    float* yscale = (float*)env.alloc(sizeof(float) * mode_tiles * MT, "alloc mode scales");
     bufs.push_back(vdig);
     bufs.push_back(fexp);
-    ok = vdig && fexp;
+    bufs.push_back(xscale);
+    bufs.push_back(yscale);
+    ok = vdig && fexp && xscale && yscale;
     if (!ok) break;
     FxVSplitJob& V = vj[i];
     memset(&V, 0, sizeof(V));
@@ -673,6 +677,9 @@ bool step_modes_fx(Env& env, std::vector<Work*>& ws) {
     V.exps = w->exps;
     V.vdig = vdig;
     V.fexp = fexp;
+    V.xscale = xscale;
+    V.scale = w->scale;
+    V.yscale = yscale;
     V.m = (int32_t)w->m;
     V.k = k;
     V.kpad = mode_tiles * MT;
@@ -682,6 +689,8 @@ bool step_modes_fx(Env& env, std::vector<Work*>& ws) {
     M.X = static_cast<const float*>(w->X);
     M.ldx = w->ldx;
     M.exps = w->exps;
+    M.xscale = xscale;
+    M.yscale = yscale;
     M.vdig = vdig;
     M.fexp = fexp;
     M.scale = w->scale;
@@ -813,13 +822,16 @@ bool step_eig(Env& env, int precision, std::vector<Work*>& ws, NodeResult* res_d
     J.m = (int32_t)w->m;
     max_m = std::max(max_m, (int)w->m);
   }
-  EigJob* jobs_d = env.upload(jobs, "upload eig jobs");
-  if (!jobs_d) return false;
+  EigJob* jobs_d = (EigJob*)env.alloc(sizeof(EigJob) * jobs.size(), "alloc eig jobs");
+  EigSync* sync_d = (EigSync*)env.alloc(sizeof(EigSync) * jobs.size(), "alloc eig barriers");
+  bool ok = jobs_d && sync_d;
   cudaEvent_t t0 = env.tic();
-  bool ok = env.cuda(launch_eig(eig_mode(precision), jobs_d, (int)jobs.size(), max_m, kMaxSweeps, env.s),
-                     "eigensolver launch");
+  ok = ok && env.cuda(launch_eig(eig_mode(precision), jobs.data(), jobs_d, (int)jobs.size(), max_m, kMaxSweeps,
+                                 sync_d, env.err_dev, env.s),
+                      "eigensolver launch");
   env.toc(t0, 1, 1, 0.0, 0.0);
   env.release(jobs_d);
+  env.release(sync_d);
   return ok;
 }
 

@@ -106,6 +106,9 @@ struct FxVSplitJob {
   const int32_t* exps;
   uint16_t* vdig;
   int32_t* fexp;
+  float2* xscale;  // per column j (padded to whole stages): s1 s2 = 2^(30 - E_j)
+  const double* scale;  // k or null: scale of mode c
+  float* yscale;        // kpad: FP32 scale of mode c (1 without a scale)
   int32_t m;
   int32_t k;
   int32_t kpad;  // k rounded up to whole mode tiles
@@ -117,9 +120,11 @@ struct FxModesJob {
   const float* X;
   int64_t ldx;
   const int32_t* exps;
+  const float2* xscale;
   const uint16_t* vdig;
   const int32_t* fexp;
   const double* scale;  // k or null
+  const float* yscale;  // kpad: FP32 scale of mode c
   float* Y;
   int64_t ldy;
   int64_t n;
@@ -131,6 +136,7 @@ struct FxModesJob {
 };
 int fx_modes_tile();
 size_t fx_vdig_bytes(int64_t m, int64_t k);
+size_t fx_xscale_bytes(int64_t m);
 cudaError_t launch_fx_colexp(const float* X, int64_t ldx, int64_t n, int64_t m, int* exps, cudaStream_t s);
 cudaError_t launch_modes_fx(const FxVSplitJob* vjobs_dev, int njobs, int max_kpad, const FxModesJob* jobs_dev,
                             const CUtensorMap* maps_dev, int64_t total_items, int* err_flag, cudaStream_t s);
@@ -273,6 +279,13 @@ cudaError_t launch_modes_oz(const OzModesJob* jobs_dev, const CUtensorMap* maps_
                             int* err_flag, cudaStream_t s);
 
 // ---------------------------------------------------------------- eig (K2)
+// Node barrier state of the multi-CTA eigensolver (zeroed before each launch).
+struct EigSync {
+  unsigned count;   // CTAs arrived at the current barrier
+  unsigned gen;     // barrier generation
+  int abort;        // a wait of this node ran out
+  int rot_sweep;    // last sweep (1-based) in which a pair was rotated
+};
 struct EigJob {
   const double* G;     // m x m FP64 input (not modified)
   void* A;             // m x m FP64 work: pivoted Cholesky factor L
@@ -284,15 +297,19 @@ struct EigJob {
   double eps2;         // the node's eps^2 (caps the factorisation's stopping residual)
   double floor_rel;    // relative level of the Gram's error: the factorisation stops there at the latest
   int32_t m;
+  int32_t cta0;        // first CTA of this job in its launch (set by launch_eig)
+  int32_t ncta;        // CTAs of this job (set by launch_eig)
   int32_t pad;
+  EigSync* sync;       // node barrier (set by launch_eig)
 };
 // Rotation precision: FP64 (V in FP64) or FP32 (V in FP32).
 constexpr int kEigF64 = 0;
 constexpr int kEigF32 = 1;
-// One CTA per job; max_m sizes the dynamic shared memory (eig_smem_bytes).
-cudaError_t launch_eig(int mode, const EigJob* jobs_dev, int njobs, int max_m, int max_sweeps, cudaStream_t s);
-int eig_threads();
-size_t eig_smem_bytes(int m);
+// Cooperative launches over the jobs, several CTAs per job.  jobs_host is completed
+// (cta0, ncta, sync) and copied to jobs_dev (njobs entries); sync_dev: njobs entries.
+// err: the bounded-wait flag block (err[1] = debug wait budget) or null.
+cudaError_t launch_eig(int mode, EigJob* jobs_host, EigJob* jobs_dev, int njobs, int max_m, int max_sweeps,
+                       EigSync* sync_dev, const int* err, cudaStream_t s);
 constexpr int kEigMaxM = 13000;  // dynamic shared memory bound of the eigensolver
 
 // ---------------------------------------------------------------- truncation (K3)

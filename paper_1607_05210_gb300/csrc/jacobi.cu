@@ -1,33 +1,39 @@
 // K2: eigen-decomposition of a node's Gramian G (Sec. 2, Remark
-// def:method_of_snapshots: lambda_k, psi_k of G give the POD), one CTA per node.
+// def:method_of_snapshots: lambda_k, psi_k of G give the POD) for every node of a
+// batch in one cooperative launch, each node spread over several CTAs.
 //
-// 1. Rank-revealing factorisation (FP64): diagonally pivoted Cholesky
-//    G = L L^T + S, choosing at step k the largest remaining diagonal of the Schur
-//    complement S and stopping once trace(S) (the sum of its diagonal, S being PSD)
-//    is below min(tol * trace(G), 1e-2 eps^2) (tol * trace(G) without an eps),
-//    tol = m 2^-53 (FP64 rotations) or 1e-7 (FP32 rotations), but not below the
-//    form's Gram error level floor_rel * trace(G) (the remaining pivots would factor
-//    rounding noise).  trace(S) is
-//    returned as `resid` and added to every tail of the truncation, so the dropped
-//    part is accounted for exactly: no eigenvalue of G exceeds that of L L^T by more
-//    than ||S|| <= trace(S).
-// 2. One-sided Jacobi (Hestenes) on the r columns of L in precision T: plane
-//    rotations from the right make the columns mutually orthogonal, L J = W.  Then
-//    L L^T = W W^T, so the eigenvectors of L L^T are u_j = w_j / ||w_j|| (no
-//    rotation matrix has to be accumulated); the eigenvalues are taken as FP64
-//    Rayleigh quotients u_j^T G u_j with the original G.  Pairs follow the round-robin ("circle") ordering, one warp per
-//    pair, all pairs of a step concurrently; a pair is rotated while
-//    |w_p . w_q| > tol ||w_p|| ||w_q||, tol = m * unit roundoff of T.
-// For the exponentially decaying spectra of snapshot data r is a few tens, so the
-// eigensolve costs O(m r^2) per sweep instead of the O(m^3) of a Jacobi sweep on G.
-// Output: lambda descending (clamped >= 0, zero beyond r), V (T, m x m) with
-// column j = w_j / ||w_j|| for j < r and zero otherwise, perm = sorted order.
+// 1. Rank-revealing factorisation: diagonally pivoted Cholesky G = L L^T + S in FP64, stopping once trace(S) is
+//    below min(tol trace(G), 1e-2 eps^2), tol = m 2^-53 (FP64 rotations) or 1e-7 (FP32
+//    rotations), but not below the form's Gram error level floor_rel trace(G) (the
+//    remaining pivots would factor rounding noise).  trace(S) (S is PSD) is returned
+//    as `resid` and added to every tail of the truncation, so the dropped part is
+//    accounted for exactly: no eigenvalue of G exceeds that of L L^T by more than
+//    ||S|| <= trace(S);
+// 2. one-sided Jacobi (Hestenes) on the r columns of L in precision T: plane rotations
+//    from the right make the columns mutually orthogonal, L J = W, so L L^T = W W^T and
+//    the eigenvectors are u_j = w_j / ||w_j|| (no rotation matrix is accumulated);
+//    pairs in the round-robin ("circle") order, rotated while
+//    |w_p . w_q| > m u ||w_p|| ||w_q||, u the unit roundoff of T;
+// 3. lambda_j = u_j^T G u_j in FP64 (Rayleigh quotients against the original G: second
+//    order in the eigenvector error), sorted descending, clamped >= 0, zero beyond r.
+// GB300 executes FP64 at about two fused multiply-adds per clock and SM, so one CTA
+// per node leaves the rest of the GPU idle while an O(m r^2) sweep runs.  Here the
+// CTAs of a node split every step: the rows of each Cholesky column, the pairs of
+// each Jacobi round (one warp per pair), the columns of the Rayleigh quotients.  The
+// CTAs of one node meet at a node barrier (global counter and generation word,
+// bounded spin) after each Cholesky step and each Jacobi round; a cooperative launch
+// keeps every CTA resident, and nodes never wait on one another.  A barrier that
+// runs out of its budget raises the node's abort word and error status
+// HAPOD_ERR_TIMEOUT; every CTA of the node then leaves.
+#include <algorithm>
+
 #include "hapod_internal.cuh"
+#include "tc_common.cuh"
 
 namespace hapod {
 namespace {
 
-constexpr int kThreads = 512;
+constexpr int kThreads = 128;
 constexpr int kWarps = kThreads / 32;
 
 template <typename T>
@@ -52,7 +58,6 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-// Pair k of round t in the circle method on mp (even) players.
 __device__ __forceinline__ void rr_pair(int t, int k, int mp, int& p, int& q) {
   const int r = mp - 1;
   if (k == 0) {
@@ -64,9 +69,56 @@ __device__ __forceinline__ void rr_pair(int t, int k, int mp, int& p, int& q) {
   }
 }
 
-// Block-wide argmax of d[i] over unchosen i (ties: lowest index) and the block sum
-// of the positive d[i]; every thread receives the results.
-__device__ void argmax_block(const double* d, const unsigned char* chosen, int m, int& p, double& dmax, double& dsum,
+// Node barrier of the CTAs of one job.  Returns false once the job aborted (a wait
+// ran out here or elsewhere).
+struct NodeBarrier {
+  EigSync* s;
+  unsigned ncta;
+  unsigned gen;  // generation this CTA waits to leave
+  tc::WaitBudget wb;
+
+  __device__ bool sync() {
+    __syncthreads();
+    __shared__ int ok_sh;
+    if (threadIdx.x == 0) {
+      int ok = 1;
+      volatile unsigned* vgen = &s->gen;
+      volatile int* vabort = &s->abort;
+      __threadfence();
+      const unsigned arrived = atomicAdd(&s->count, 1u) + 1u;
+      if (arrived == ncta) {
+        atomicExch(&s->count, 0u);
+        __threadfence();
+        atomicExch(&s->gen, gen + 1u);
+      } else {
+        const long long t0 = clock64();
+        while (*vgen == gen) {
+          if (*vabort) {
+            ok = 0;
+            break;
+          }
+          if (clock64() - t0 > wb.cycles) {
+            atomicExch(&s->abort, 1);
+            ok = 0;
+            break;
+          }
+        }
+      }
+      __threadfence();
+      if (*vabort) ok = 0;
+      gen += 1u;
+      ok_sh = ok;
+    }
+    __syncthreads();
+    const bool ok = ok_sh != 0;
+    __syncthreads();
+    return ok;
+  }
+};
+
+// Block-wide argmax of d[i] over unchosen i (ties: lowest index) and sum of the
+// positive d[i]; every thread of the CTA receives the results.
+__device__ void argmax_block(const double* d, const int32_t* chosen, int m, int& p, double& dmax, double& dsum,
                              double* red_v, int* red_i, double* red_s) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   double best = -1.0, sum = 0.0;
@@ -99,7 +151,7 @@ __device__ void argmax_block(const double* d, const unsigned char* chosen, int m
   if (tid == 0) {
     double b = -1.0, s = 0.0;
     int i = -1;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+    for (int w = 0; w < kWarps; ++w) {
       s += red_s[w];
       if (red_v[w] > b || (red_v[w] == b && red_i[w] >= 0 && (i < 0 || red_i[w] < i))) {
         b = red_v[w];
@@ -117,218 +169,259 @@ __device__ void argmax_block(const double* d, const unsigned char* chosen, int m
   __syncthreads();
 }
 
-// One-sided Jacobi sweeps on the r columns (length m) of W in precision U until no
-// pair needs a rotation (|w_p . w_q| <= m u ||w_p|| ||w_q||, u the unit roundoff of U)
-// or max_sweeps sweeps were made.  Block-wide; returns the sweeps made.
-template <typename U>
-__device__ int jacobi_sweeps(U* W, int m, int r, int max_sweeps, bool& converged, int* flag_sh) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int rp = r + (r & 1), npairs = rp / 2;
-  const U rtol = (U)m * Unit<U>::eps();
-  int sweeps = 0;
-  converged = (r <= 1);
-  while (!converged && sweeps < max_sweeps) {
-    ++sweeps;
-    if (tid == 0) *flag_sh = 0;
-    __syncthreads();
-    int rotated = 0;
-    for (int t = 0; t < rp - 1; ++t) {
-      for (int k = warp; k < npairs; k += kWarps) {
-        int p, q;
-        rr_pair(t, k, rp, p, q);
-        if (p >= r || q >= r) continue;
-        U* wp = W + (size_t)p * m;
-        U* wq = W + (size_t)q * m;
-        U al = 0, be = 0, ga = 0;
-        for (int i = lane; i < m; i += 32) {
-          const U x = wp[i], y = wq[i];
-          al = fma(x, x, al);
-          be = fma(y, y, be);
-          ga = fma(x, y, ga);
-        }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        ga = warp_sum(ga);
-        if (ga == U(0) || !(fabs(ga) > rtol * sqrt(al * be))) continue;
-        rotated = 1;
-        const U zeta = (be - al) / (U(2) * ga);
-        // smaller root of t^2 + 2 zeta t - 1 = 0; 1/(2 zeta) once zeta^2 would overflow
-        const U tt = fabs(zeta) > U(1e15) ? U(0.5) / zeta
-                                           : (zeta >= U(0) ? U(1) : U(-1)) / (fabs(zeta) + sqrt(U(1) + zeta * zeta));
-        const U c = U(1) / sqrt(U(1) + tt * tt);
-        const U s = c * tt;
-        for (int i = lane; i < m; i += 32) {
-          const U x = wp[i], y = wq[i];
-          wp[i] = c * x - s * y;
-          wq[i] = s * x + c * y;
-        }
-      }
-      __syncthreads();
-    }
-    if (rotated && lane == 0) *flag_sh = 1;
-    __syncthreads();
-    converged = (*flag_sh == 0);
-    __syncthreads();
+__device__ __forceinline__ int find_job(const EigJob* jobs, int njobs, int cta) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].cta0 <= cta) lo = mid; else hi = mid - 1;
   }
-  return sweeps;
+  return lo;
 }
 
-// T: precision of the rotations and of the eigenvectors.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) chol_jacobi_kernel(const EigJob* __restrict__ jobs, int max_sweeps) {
-  typedef T V_t;
-  const EigJob J = jobs[blockIdx.x];
+__global__ void __launch_bounds__(kThreads) eig_coop_kernel(const EigJob* __restrict__ jobs, int njobs,
+                                                            int max_sweeps, const int* err) {
+  const int jb = find_job(jobs, njobs, blockIdx.x);
+  const EigJob J = jobs[jb];
+  const int c = blockIdx.x - J.cta0;  // this CTA within the job
+  const int P = J.ncta;
   const int m = J.m;
-  if (m <= 0) return;
+  if (m <= 0 || c >= P) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const double* __restrict__ G = J.G;
   double* L = static_cast<double*>(J.A);  // m x m FP64 (first r columns used)
   T* W = static_cast<T*>(J.V);           // m x m in T: rotated columns, then eigenvectors
+  double* d = J.lam_tmp;                  // Schur complement diagonal during the factorisation
+  int32_t* chosen = J.perm;               // pivot flags during the factorisation
   NodeResult* res = J.result;
-  extern __shared__ double shm[];
-  double* d = shm;                                                         // m
-  double* rowp = shm + m;                                                  // m (row p of L)
-  unsigned char* chosen = reinterpret_cast<unsigned char*>(shm + 2 * m);  // m
+  extern __shared__ double rowp[];        // row p of L
   __shared__ double red_v[kWarps], red_s[kWarps];
   __shared__ int red_i[kWarps];
   __shared__ int flag_sh;
+  NodeBarrier bar{J.sync, (unsigned)P, 0u, tc::wait_budget(err)};
+  // rows of this CTA for row-parallel steps
+  const int chunk = (m + P - 1) / P;
+  const int i0 = c * chunk, i1 = min(m, i0 + chunk);
 
   // ---------------- pivoted Cholesky (FP64)
   if (tid == 0) flag_sh = 0;
   __syncthreads();
-  for (int i = tid; i < m; i += blockDim.x) {
-    const double gi = G[(size_t)i * m + i];
-    if (!isfinite(gi)) flag_sh = 1;  // NaN/Inf in a column of X reaches its diagonal entry
-    d[i] = gi;
+  for (int i = i0 + tid; i < i1; i += blockDim.x) {
+    d[i] = G[(size_t)i * m + i];
     chosen[i] = 0;
   }
-  __syncthreads();
-  int p0;
-  double dmax0, trace;
-  argmax_block(d, chosen, m, p0, dmax0, trace, red_v, red_i, red_s);
-  const bool finite = flag_sh == 0 && isfinite(trace) && isfinite(dmax0);
-  __syncthreads();
-  if (!finite && tid == 0) res->status = HAPOD_ERR_NONFINITE;
-  const double tol = (sizeof(V_t) == sizeof(double)) ? (double)m * 1.1102230246251565e-16 : 1e-7;
-  const double tr_pos = trace > 0.0 ? trace : 0.0;
-  const double stop_round = tol * tr_pos;
-  double stop = J.eps2 > 0.0 ? fmin(stop_round, 1e-2 * J.eps2) : stop_round;
-  // below the Gram's own error level the remaining pivots would factor rounding noise
-  if (J.floor_rel > 0.0) stop = fmax(stop, J.floor_rel * tr_pos);
-  int r = 0;
-  double resid = finite && trace > 0.0 ? trace : 0.0;
-  if (finite && trace > 0.0) {
-    for (int k = 0; k < m; ++k) {
-      int p;
-      double dmax, dsum;
-      argmax_block(d, chosen, m, p, dmax, dsum, red_v, red_i, red_s);
-      resid = dsum;
-      if (p < 0 || !(dmax > 0.0) || dsum <= stop) break;
-      for (int j = tid; j < k; j += blockDim.x) rowp[j] = L[(size_t)j * m + p];  // row p of L
-      __syncthreads();
-      const double piv = sqrt(dmax);
-      const double inv = 1.0 / piv;
-      for (int i = tid; i < m; i += blockDim.x) {
-        double v;
-        if (i == p) {
-          v = piv;
-        } else if (chosen[i]) {
-          v = 0.0;
-        } else {
-          double s = G[(size_t)p * m + i];
-          for (int j = 0; j < k; ++j) s -= L[(size_t)j * m + i] * rowp[j];
-          v = s * inv;
-          d[i] -= v * v;
+  // every CTA checks the whole diagonal for non-finite values (NaN/Inf in a column of
+  // X reaches its diagonal entry) and forms the same trace
+  for (int i = tid; i < m; i += blockDim.x)
+    if (!isfinite(G[(size_t)i * m + i])) flag_sh = 1;
+  if (!bar.sync()) goto timeout;
+  {
+    int p0;
+    double dmax0, trace;
+    argmax_block(d, chosen, m, p0, dmax0, trace, red_v, red_i, red_s);
+    const bool finite = flag_sh == 0 && isfinite(trace) && isfinite(dmax0);
+    if (!finite && c == 0 && tid == 0) res->status = HAPOD_ERR_NONFINITE;
+    const double tol = (sizeof(T) == sizeof(double)) ? (double)m * 1.1102230246251565e-16 : 1e-7;
+    const double tr_pos = trace > 0.0 ? trace : 0.0;
+    const double stop_round = tol * tr_pos;
+    double stop = J.eps2 > 0.0 ? fmin(stop_round, 1e-2 * J.eps2) : stop_round;
+    if (J.floor_rel > 0.0) stop = fmax(stop, J.floor_rel * tr_pos);
+    int r = 0;
+    double resid = finite && trace > 0.0 ? trace : 0.0;
+    if (finite && trace > 0.0) {
+      for (int k = 0; k < m; ++k) {
+        int p;
+        double dmax, dsum;
+        argmax_block(d, chosen, m, p, dmax, dsum, red_v, red_i, red_s);
+        resid = dsum;
+        if (p < 0 || !(dmax > 0.0) || dsum <= stop) break;
+        for (int j = tid; j < k; j += blockDim.x) rowp[j] = L[(size_t)j * m + p];
+        __syncthreads();
+        const double piv = sqrt(dmax);
+        const double inv = 1.0 / piv;
+        for (int i = i0 + tid; i < i1; i += blockDim.x) {
+          double v;
+          if (i == p) {
+            v = piv;
+          } else if (chosen[i]) {
+            v = 0.0;
+          } else {
+            double s = G[(size_t)p * m + i];
+            for (int j = 0; j < k; ++j) s -= L[(size_t)j * m + i] * rowp[j];
+            v = s * inv;
+            d[i] -= v * v;
+          }
+          L[(size_t)k * m + i] = v;
         }
-        L[(size_t)k * m + i] = v;
+        if (p >= i0 && p < i1 && tid == 0) {
+          chosen[p] = 1;
+          d[p] = 0.0;
+        }
+        r = k + 1;
+        resid = 0.0;
+        if (!bar.sync()) goto timeout;
       }
-      __syncthreads();
-      if (tid == 0) {
-        chosen[p] = 1;
-        d[p] = 0.0;
-      }
-      __syncthreads();
-      r = k + 1;
-      resid = 0.0;
     }
-  }
 
-  // ---------------- one-sided Jacobi on the r columns (precision T)
-  for (size_t e = tid; e < (size_t)r * m; e += blockDim.x) W[e] = (T)L[e];
-  __syncthreads();
-  bool converged = false;
-  const int sweeps = jacobi_sweeps<T>(W, m, r, max_sweeps, converged, &flag_sh);
-  V_t* U = W;
-  for (size_t e = (size_t)r * m + tid; e < (size_t)m * m; e += blockDim.x) U[e] = V_t(0);
-  __syncthreads();
-
-  // ---------------- normalised eigenvectors u_j = w_j / ||w_j||, then FP64 Rayleigh
-  // quotients lambda_j = u_j^T G u_j against the original G (second order in the
-  // eigenvector error, so the rounding of L and of the rotations enters squared)
-  for (int j = warp; j < m; j += kWarps) {
-    double s = 0.0;
-    if (j < r) {
-      const V_t* wj = U + (size_t)j * m;
-      for (int i = lane; i < m; i += 32) s += (double)wj[i] * (double)wj[i];
-      s = warp_sum(s);
-    }
-    if (j < r && s > 0.0) {
-      const double inv = 1.0 / sqrt(s);
-      V_t* wj = U + (size_t)j * m;
-      for (int i = lane; i < m; i += 32) wj[i] = (V_t)((double)wj[i] * inv);
-    }
-  }
-  __syncthreads();
-  for (int j = warp; j < m; j += kWarps) {
-    double acc = 0.0;
-    if (j < r) {
-      const V_t* uj = U + (size_t)j * m;
-      for (int i = lane; i < m; i += 32) {
-        double gi = 0.0;  // (G u_j)_i; G symmetric, column-major
-        for (int l = 0; l < m; ++l) gi = fma(G[(size_t)l * m + i], (double)uj[l], gi);
-        acc = fma((double)uj[i], gi, acc);
+    // ---------------- one-sided Jacobi on the r columns (precision T)
+    for (int j = 0; j < r; ++j)
+      for (int i = i0 + tid; i < i1; i += blockDim.x) W[(size_t)j * m + i] = (T)L[(size_t)j * m + i];
+    if (!bar.sync()) goto timeout;
+    const int rp = r + (r & 1), npairs = rp / 2;
+    const int nw = P * kWarps, wg = c * kWarps + warp;
+    const T rtol = (T)m * Unit<T>::eps();
+    int sweeps = 0;
+    bool converged = (r <= 1);
+    volatile int* rot_sweep = &J.sync->rot_sweep;
+    while (!converged && sweeps < max_sweeps) {
+      ++sweeps;
+      for (int t = 0; t < rp - 1; ++t) {
+        for (int k = wg; k < npairs; k += nw) {
+          int p, q;
+          rr_pair(t, k, rp, p, q);
+          if (p >= r || q >= r) continue;
+          T* wp = W + (size_t)p * m;
+          T* wq = W + (size_t)q * m;
+          T al = 0, be = 0, ga = 0;
+          for (int i = lane; i < m; i += 32) {
+            const T x = wp[i], y = wq[i];
+            al = fma(x, x, al);
+            be = fma(y, y, be);
+            ga = fma(x, y, ga);
+          }
+          al = warp_sum(al);
+          be = warp_sum(be);
+          ga = warp_sum(ga);
+          if (ga == T(0) || !(fabs(ga) > rtol * sqrt(al * be))) continue;
+          if (lane == 0 && *rot_sweep < sweeps) atomicMax(&J.sync->rot_sweep, sweeps);
+          const T zeta = (be - al) / (T(2) * ga);
+          const T tt = fabs(zeta) > T(1e15) ? T(0.5) / zeta
+                                             : (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+          const T cs = T(1) / sqrt(T(1) + tt * tt);
+          const T sn = cs * tt;
+          for (int i = lane; i < m; i += 32) {
+            const T x = wp[i], y = wq[i];
+            wp[i] = cs * x - sn * y;
+            wq[i] = sn * x + cs * y;
+          }
+        }
+        if (!bar.sync()) goto timeout;
       }
-      acc = warp_sum(acc);
+      converged = *rot_sweep < sweeps;  // no rotation in this sweep
     }
-    if (lane == 0) J.lam_tmp[j] = acc;
-  }
-  __syncthreads();
-  for (int j = tid; j < m; j += blockDim.x) {
-    const double lj = J.lam_tmp[j];
-    int rank = 0;
-    for (int i = 0; i < m; ++i) {
-      const double li = J.lam_tmp[i];
-      rank += (li > lj) || (li == lj && i < j);
+
+    // ---------------- u_j = w_j / ||w_j|| and FP64 Rayleigh quotients against G
+    for (int j = wg; j < m; j += nw) {
+      T* wj = W + (size_t)j * m;
+      double acc = 0.0;
+      if (j < r) {
+        double s = 0.0;
+        for (int i = lane; i < m; i += 32) s += (double)wj[i] * (double)wj[i];
+        s = warp_sum(s);
+        if (s > 0.0) {
+          const double inv = 1.0 / sqrt(s);
+          for (int i = lane; i < m; i += 32) wj[i] = (T)((double)wj[i] * inv);
+        }
+        __syncwarp();
+        for (int i = lane; i < m; i += 32) {
+          double gi = 0.0;  // (G u_j)_i; G symmetric, column-major
+          for (int l = 0; l < m; ++l) gi = fma(G[(size_t)l * m + i], (double)wj[l], gi);
+          acc = fma((double)wj[i], gi, acc);
+        }
+        acc = warp_sum(acc);
+      } else {
+        for (int i = lane; i < m; i += 32) wj[i] = T(0);
+      }
+      if (lane == 0) d[j] = acc;  // d now holds the unsorted eigenvalues
     }
-    J.lambda[rank] = lj > 0.0 ? lj : 0.0;
-    J.perm[rank] = j;
+    if (!bar.sync()) goto timeout;
+    for (int j = i0 + tid; j < i1; j += blockDim.x) {
+      const double lj = d[j];
+      int rank = 0;
+      for (int i = 0; i < m; ++i) {
+        const double li = d[i];
+        rank += (li > lj) || (li == lj && i < j);
+      }
+      J.lambda[rank] = lj > 0.0 ? lj : 0.0;
+      chosen[rank] = j;  // perm: sorted position -> column of V
+    }
+    if (c == 0 && tid == 0) {
+      res->sweeps = sweeps;
+      res->trace = trace;
+      res->rank = r;
+      res->resid = resid;
+      if (!converged && res->status == HAPOD_OK) res->status = HAPOD_WARN_NOCONVERGE;
+    }
+    return;
   }
-  if (tid == 0) {
-    res->sweeps = sweeps;
-    res->trace = trace;
-    res->rank = r;
-    res->resid = resid;
-    if (!converged && res->status == HAPOD_OK) res->status = HAPOD_WARN_NOCONVERGE;
-  }
+timeout:
+  if (c == 0 && tid == 0) res->status = HAPOD_ERR_TIMEOUT;
 }
 
 }  // namespace
 
-int eig_threads() { return kThreads; }
+size_t eig_smem_bytes(int m) { return (size_t)std::max(m, 1) * sizeof(double); }
 
-size_t eig_smem_bytes(int m) { return (size_t)m * (2 * sizeof(double) + 1) + 16; }
-
-cudaError_t launch_eig(int mode, const EigJob* jobs_dev, int njobs, int max_m, int max_sweeps, cudaStream_t s) {
+// Per-job CTA counts: one warp per Jacobi pair (m / 8 CTAs of 4 warps, at most 128),
+// scaled down to what the GPU keeps resident; jobs beyond that go to further launches.
+cudaError_t launch_eig(int mode, EigJob* jobs_host, EigJob* jobs_dev, int njobs, int max_m, int max_sweeps,
+                       EigSync* sync_dev, const int* err, cudaStream_t s) {
   if (njobs <= 0) return cudaSuccess;
+  const void* fn = mode == kEigF32 ? (const void*)eig_coop_kernel<float> : (const void*)eig_coop_kernel<double>;
   const size_t smem = eig_smem_bytes(max_m);
-  const void* fn =
-      mode == kEigF32 ? (const void*)chol_jacobi_kernel<float> : (const void*)chol_jacobi_kernel<double>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  void* args[] = {(void*)&jobs_dev, (void*)&max_sweeps};
-  return cudaLaunchKernel(fn, dim3(njobs), dim3(kThreads), args, smem, s);
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem);
+  if (e != cudaSuccess) return e;
+  const int cap = std::max(1, sms * per_sm);
+  e = cudaMemsetAsync(sync_dev, 0, sizeof(EigSync) * (size_t)njobs, s);
+  if (e != cudaSuccess) return e;
+  int j0 = 0;
+  while (j0 < njobs) {
+    // the jobs of this launch: at most `cap` CTAs, at least one per job
+    int j1 = j0;
+    int64_t want = 0;
+    while (j1 < njobs && want + 1 <= cap && j1 - j0 < cap) {
+      want += std::max(1, std::min(128, (jobs_host[j1].m + 7) / 8));
+      ++j1;
+    }
+    const double scale = want > cap ? (double)cap / (double)want : 1.0;
+    int total = 0;
+    for (int j = j0; j < j1; ++j) {
+      EigJob& J = jobs_host[j];
+      const int w = std::max(1, std::min(128, (J.m + 7) / 8));
+      J.ncta = std::max(1, (int)(w * scale));
+      J.cta0 = total;
+      J.sync = sync_dev + j;
+      total += J.ncta;
+    }
+    while (total > cap) {  // rounding up to one CTA per job can overshoot
+      for (int j = j0; j < j1 && total > cap; ++j)
+        if (jobs_host[j].ncta > 1) {
+          jobs_host[j].ncta--;
+          total--;
+        }
+      int t = 0;
+      for (int j = j0; j < j1; ++j) {
+        jobs_host[j].cta0 = t;
+        t += jobs_host[j].ncta;
+      }
+    }
+    e = cudaMemcpyAsync(jobs_dev + j0, jobs_host + j0, sizeof(EigJob) * (size_t)(j1 - j0), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    const EigJob* jd = jobs_dev + j0;
+    int nj = j1 - j0;
+    void* args[] = {(void*)&jd, (void*)&nj, (void*)&max_sweeps, (void*)&err};
+    e = cudaLaunchCooperativeKernel(fn, dim3(total), dim3(kThreads), args, smem, s);
+    if (e != cudaSuccess) return e;
+    j0 = j1;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace hapod

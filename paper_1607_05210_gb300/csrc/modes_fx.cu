@@ -4,27 +4,30 @@
 // digit operands) with exact accumulation.
 //
 // With E_j the exponent of column j's largest |x| (2^(E_j-1) <= max < 2^E_j, recorded
-// by the Gram kernel) and F_c that of max_j 2^E_j |V_jc|, every x_rj is the 32-bit
-// integer A_rj = rint(x_rj 2^(31-E_j)) and every V_jc the 32-bit integer
-// B_jc = rint(V_jc 2^(E_j+31-F_c)), each written as four balanced base-256 digits, so
-//   Y_rc = sum_j x_rj V_jc = 2^(F_c-62) sum_j A_rj B_jc   (the column scales cancel),
+// by the Gram kernel) and F_c that of max_j 2^E_j |V_jc|, every x_rj is the integer
+// A_rj = rint(x_rj 2^(30-E_j)) (|A| <= 2^30) and every V_jc the integer
+// B_jc = rint(V_jc 2^(E_j+31-F_c)) (|B| < 2^31), each written as four base-256 digits,
+// so that
+//   Y_rc = sum_j x_rj V_jc = 2^(F_c-61) sum_j A_rj B_jc   (the column scales cancel),
 // sum_j A_rj B_jc = sum_{t,u} 2^(8(8-t-u)) L_{t+u} with L_s the level sums of digit
-// products.  Levels 2..5 (ten digit pairs) are kept; over a chunk of 64 columns every
-// L_s <= 64 * 4 * 2^14 = 2^22 is an exact integer in the FP32 accumulator; the chunks
-// are added exactly into int64 sums (unit 2^(F_c-38)) and rounded once to FP32 at the
-// end.  The error of an entry is at most 2^(-30) sum_j 2^(E_j+F_c-E_j) per column
-// pair: about m 2^-30 max|x| max|V|, against the 2^-24 m max|x| max|V| of an FP32
-// dot product.  Columns holding Inf or NaN give NaN columns of Y.
+// products.  The digits of A are the bytes of A + 0x80808080 less 128 (in [-128, 127];
+// the sum reproduces A exactly because |A| <= 2^30), those of B balanced (rounded to
+// nearest at each step, |b| <= 128).  Levels 2..5 (ten digit pairs) are kept; over a
+// chunk of 256 columns every L_s <= 4 * 256 * 2^14 = 2^24 is an exact integer in the
+// FP32 accumulator; the chunks are added exactly into int64 sums (unit 2^(F_c-37)) and
+// rounded once to FP32 at the end.  Columns holding Inf or NaN give NaN columns of Y.
 //
-// Work item = (node, 128-row tile, 64-mode tile).  One CTA per item, 14 warps:
+// Persistent: one CTA per SM walks the items (node, 128-row tile, 64-mode tile), the
+// mode tiles of a row tile adjacent so that the second read of X comes from L2; the
+// stage ring and the two accumulator sets run on across items.  18 warps:
 //   warp 0        loader: TMA box of X (128 rows x 16 columns FP32) and a bulk copy
-//                 of the 16-column chunk of V digits (8 KB), 4 stages deep
+//                 of the 16-column chunk of V digits (8 KB), 6 stages deep
 //   warp 1        TMEM owner and single-thread MMA issuer: per 16 columns four MMAs,
 //                 X digit t against the V digits 1 .. 5 - t (N = 64 (5 - t)) into
 //                 the level accumulators L_{t+1} .. L_5; two accumulator sets
-//                 (2 x 256 TMEM columns) alternate between 64-column chunks
-//   warps 2..5    converters: X -> four digit planes (K-major core matrices)
-//   warps 6..13   output: int64 sums of 32 entries per thread, then Y
+//                 (2 x 256 TMEM columns) alternate between chunks
+//   warps 2..9    converters: X -> four digit planes (K-major core matrices)
+//   warps 10..17  output: int64 sums of 32 entries per thread, then Y
 // Every mbarrier wait is bounded: a timeout raises the error flag, the CTA drains
 // its copies and MMAs and frees TMEM.
 #include <cuda_fp16.h>
@@ -41,15 +44,15 @@ constexpr int kDigits = 4;
 constexpr int kRowsT = 128;                          // rows of X per item (M)
 constexpr int kModesT = 64;                          // modes per item
 constexpr int kK = 16;                               // columns of X per stage (one MMA K)
-constexpr int kChunkStages = 4;                      // 64 columns between exact flushes
+constexpr int kChunkStages = 16;                     // 256 columns between exact flushes
 constexpr int kStX = kRowsT * kK * 4;                // FP32 staging of X, 8 KB
 constexpr int kPlaneX = kRowsT * kK * 2;             // one digit plane of X, 4 KB
 constexpr int kPlaneV = kModesT * kK * 2;            // one digit plane of V, 2 KB
 constexpr int kOpX = kDigits * kPlaneX;              // 16 KB
 constexpr int kOpV = kDigits * kPlaneV;              // 8 KB
-constexpr int kStages = 4;
+constexpr int kStages = 6;
 constexpr int kSmemBytes = kStages * (kStX + kOpX + kOpV) + 1024;
-constexpr int kConvWarps = 4;
+constexpr int kConvWarps = 8;
 constexpr int kFirstConvWarp = 2;
 constexpr int kFirstOutWarp = kFirstConvWarp + kConvWarps;
 constexpr int kOutWarps = 8;
@@ -60,6 +63,7 @@ constexpr uint32_t kSetCols = 256;                   // L2 | L3 | L4 | L5 of 64 
 constexpr uint32_t kTmemCols = 512;
 constexpr int kExpZero = kFxExpZero;
 constexpr int kExpBad = kFxExpBad;
+static_assert(kSmemBytes <= 227 * 1024, "shared memory");
 
 struct Bars {
   uint64_t full[kStages];    // loader: X (TMA) and V digits (bulk), transaction bytes
@@ -71,22 +75,6 @@ struct Bars {
   uint64_t mma_done;
 };
 
-__device__ __forceinline__ void digits4(float a, float (&d)[4]) {
-  const float C = 12582912.0f;  // 1.5 2^23: (y + C) - C = rint(y) for |y| < 2^22
-  d[0] = __fadd_rn(__fmaf_rn(a, 1.0f / 16777216.0f, C), -C);
-  const float r1 = __fmaf_rn(d[0], -16777216.0f, a);
-  d[1] = __fadd_rn(__fmaf_rn(r1, 1.0f / 65536.0f, C), -C);
-  const float r2 = __fmaf_rn(d[1], -65536.0f, r1);
-  d[2] = __fadd_rn(__fmaf_rn(r2, 1.0f / 256.0f, C), -C);
-  const float r3 = __fmaf_rn(d[2], -256.0f, r2);
-  d[3] = __fadd_rn(__fadd_rn(r3, C), -C);
-}
-
-__device__ __forceinline__ uint32_t h2bits(float lo, float hi) {
-  const __half2 v = __floats2half2_rn(lo, hi);
-  return *reinterpret_cast<const uint32_t*>(&v);
-}
-
 __device__ __forceinline__ int find_job(const FxModesJob* jobs, int njobs, int64_t item) {
   int lo = 0, hi = njobs - 1;
   while (lo < hi) {
@@ -96,9 +84,35 @@ __device__ __forceinline__ int find_job(const FxModesJob* jobs, int njobs, int64
   return lo;
 }
 
+// Item `it` of the launch: job, first row, mode tile, stages (16 columns each).
+struct Item {
+  int jb;
+  int row0;
+  int mt;
+  int nst;
+};
+__device__ __forceinline__ Item item_of(const FxModesJob* jobs, int njobs, int64_t it) {
+  Item r;
+  r.jb = find_job(jobs, njobs, it);
+  const FxModesJob& J = jobs[r.jb];
+  const int64_t local = it - J.item_base;
+  r.row0 = (int)((local / J.mode_tiles) * kRowsT);
+  r.mt = (int)(local % J.mode_tiles);
+  r.nst = (J.m + kK - 1) / kK;
+  return r;
+}
+
+// fp16 pair (lo, hi) = (byte b of u0 - 128, byte b of u1 - 128): the bytes are placed
+// in the mantissas of 1024 (0x6400), and 1152 is subtracted, exactly.
+__device__ __forceinline__ uint32_t digit_pair(uint32_t u0, uint32_t u1, uint32_t sel) {
+  const uint32_t w = (__byte_perm(u0, u1, sel) & 0x00FF00FFu) | 0x64006400u;
+  const __half2 h = __hsub2(*reinterpret_cast<const __half2*>(&w), __floats2half2_rn(1152.f, 1152.f));
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
     modes_fx_kernel(const FxModesJob* __restrict__ jobs, const CUtensorMap* __restrict__ maps, int njobs,
-                    int* err) {
+                    int64_t total_items, int* err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ Bars bars;
@@ -106,14 +120,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ volatile int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const tc::WaitBudget wb = tc::wait_budget(err);
-
-  const int jb = find_job(jobs, njobs, blockIdx.x);
-  const FxModesJob& J = jobs[jb];
-  const int64_t local = blockIdx.x - J.item_base;
-  const int row0 = (int)((local % J.row_tiles) * kRowsT);
-  const int mt = (int)(local / J.row_tiles);
-  const int nst = (J.m + kK - 1) / kK;
-  const int nchunk = (nst + kChunkStages - 1) / kChunkStages;
   auto st_x = [&](int s) -> uint8_t* { return smem + (size_t)s * kStX; };
   auto op_x = [&](int s) -> uint8_t* { return smem + (size_t)kStages * kStX + (size_t)s * (kOpX + kOpV); };
   auto op_v = [&](int s) -> uint8_t* { return op_x(s) + kOpX; };
@@ -141,26 +147,38 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp == 0) {
     // ------------------------------------------------------------ loader
-    if (lane == 0 && nst > 0) {
-      const CUtensorMap* map = maps + jb;
-      tc::tensormap_acquire(map);
-      const uint8_t* vsrc = reinterpret_cast<const uint8_t*>(J.vdig) + (size_t)mt * nst * kOpV;
-      int issued = 0;
-      for (int k = 0; k < nst; ++k) {
-        const int s = k % kStages;
-        // the slot's X staging and its operand area must both be free
-        if (k >= kStages && (!tc::mbar_wait(&bars.xfree[s], ((k / kStages) - 1) & 1, &abort_flag, err, wb) ||
-                             !tc::mbar_wait(&bars.ofree[s], ((k / kStages) - 1) & 1, &abort_flag, err, wb)))
-          break;
-        tc::mbar_expect_tx(&bars.full[s], (uint32_t)(kStX + kOpV));
-        tc::tma_load_2d(st_x(s), map, row0, k * kK, &bars.full[s]);
-        tc::bulk_load(op_v(s), vsrc + (size_t)k * kOpV, (uint32_t)kOpV, &bars.full[s]);
-        issued = k + 1;
+    if (lane == 0) {
+      int64_t g = 0;  // stages issued by this CTA
+      int cur_jb = -1;
+      bool ok = true;
+      for (int64_t it = blockIdx.x; it < total_items && ok; it += gridDim.x) {
+        const Item I = item_of(jobs, njobs, it);
+        const FxModesJob& J = jobs[I.jb];
+        const CUtensorMap* map = maps + I.jb;
+        if (I.jb != cur_jb) {
+          tc::tensormap_acquire(map);
+          cur_jb = I.jb;
+        }
+        const uint8_t* vsrc = reinterpret_cast<const uint8_t*>(J.vdig) + (size_t)I.mt * I.nst * kOpV;
+        for (int k = 0; k < I.nst; ++k, ++g) {
+          const int s = (int)(g % kStages);
+          const uint32_t use = (uint32_t)(g / kStages);
+          // the slot's X staging and its operand area must both be free
+          if (g >= kStages && (!tc::mbar_wait(&bars.xfree[s], (use - 1) & 1, &abort_flag, err, wb) ||
+                               !tc::mbar_wait(&bars.ofree[s], (use - 1) & 1, &abort_flag, err, wb))) {
+            ok = false;
+            break;
+          }
+          tc::mbar_expect_tx(&bars.full[s], (uint32_t)(kStX + kOpV));
+          tc::tma_load_2d(st_x(s), map, I.row0, k * kK, &bars.full[s]);
+          tc::bulk_load(op_v(s), vsrc + (size_t)k * kOpV, (uint32_t)kOpV, &bars.full[s]);
+        }
       }
-      if (abort_flag) {
-        for (int k = max(0, issued - kStages); k < issued; ++k) {
+      if (abort_flag) {  // wait (bounded) for the copies still in flight
+        for (int64_t k = (g > kStages ? g - kStages : 0); k < g; ++k) {
           const long long t0 = clock64();
-          while (!tc::mbar_try(&bars.full[k % kStages], (k / kStages) & 1) && clock64() - t0 < tc::kWaitBudget) {
+          while (!tc::mbar_try(&bars.full[k % kStages], (uint32_t)(k / kStages) & 1) &&
+                 clock64() - t0 < tc::kWaitBudget) {
           }
         }
       }
@@ -171,26 +189,39 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t idn[kDigits];
 #pragma unroll
       for (int t = 0; t < kDigits; ++t) idn[t] = tc::idesc_f16_f32_major(128, (uint32_t)(kModesT * (kDigits - t)), 0, 0);
-      for (int k = 0; k < nst; ++k) {
-        const int s = k % kStages;
-        const int ch = k / kChunkStages;
-        const bool first = (k % kChunkStages) == 0;
-        const bool last = (k % kChunkStages) == kChunkStages - 1 || k == nst - 1;
-        const int set = ch & 1;
-        if (first && ch >= 2 && !tc::mbar_wait(&bars.acc_empty[set], ((ch >> 1) - 1) & 1, &abort_flag, err, wb))
-          break;
-        if (!tc::mbar_wait(&bars.ofull[s], (k / kStages) & 1, &abort_flag, err, wb) ||
-            !tc::mbar_wait(&bars.full[s], (k / kStages) & 1, &abort_flag, err, wb))  // the V digits landed
-          break;
-        tc::tc_fence_after();
-        const uint32_t px = tc::smem_u32(op_x(s)), pv = tc::smem_u32(op_v(s));
-        const uint32_t d = tbase + (uint32_t)set * kSetCols;
+      int64_t g = 0, ch = 0;
+      bool ok = true;
+      for (int64_t it = blockIdx.x; it < total_items && ok; it += gridDim.x) {
+        const Item I = item_of(jobs, njobs, it);
+        for (int k = 0; k < I.nst; ++k, ++g) {
+          const int s = (int)(g % kStages);
+          const uint32_t use = (uint32_t)(g / kStages);
+          const bool first = (k % kChunkStages) == 0;
+          const bool last = (k % kChunkStages) == kChunkStages - 1 || k == I.nst - 1;
+          const int set = (int)(ch & 1);
+          if (first && ch >= 2 &&
+              !tc::mbar_wait(&bars.acc_empty[set], (uint32_t)((ch >> 1) - 1) & 1, &abort_flag, err, wb)) {
+            ok = false;
+            break;
+          }
+          if (!tc::mbar_wait(&bars.ofull[s], use & 1, &abort_flag, err, wb) ||
+              !tc::mbar_wait(&bars.full[s], use & 1, &abort_flag, err, wb)) {  // the V digits landed
+            ok = false;
+            break;
+          }
+          tc::tc_fence_after();
+          const uint32_t px = tc::smem_u32(op_x(s)), pv = tc::smem_u32(op_v(s));
+          const uint32_t d = tbase + (uint32_t)set * kSetCols;
 #pragma unroll
-        for (int t = 0; t < kDigits; ++t)
-          tc::umma_f16(d + (uint32_t)(kModesT * t), tc::ns_desc(px + (uint32_t)t * kPlaneX, kLbo, kSbo),
-                       tc::ns_desc(pv, kLbo, kSbo), idn[t], (first && t == 0) ? 0u : 1u);
-        tc::umma_commit(&bars.ofree[s]);
-        if (last) tc::umma_commit(&bars.acc_full[set]);
+          for (int t = 0; t < kDigits; ++t)
+            tc::umma_f16(d + (uint32_t)(kModesT * t), tc::ns_desc(px + (uint32_t)t * kPlaneX, kLbo, kSbo),
+                         tc::ns_desc(pv, kLbo, kSbo), idn[t], (first && t == 0) ? 0u : 1u);
+          tc::umma_commit(&bars.ofree[s]);
+          if (last) {
+            tc::umma_commit(&bars.acc_full[set]);
+            ++ch;
+          }
+        }
       }
       tc::umma_commit(&bars.mma_done);
       const long long t0 = clock64();
@@ -199,46 +230,50 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp < kFirstOutWarp) {
     // ------------------------------------------------------------ converters
-    // thread ct takes row r = ct for both column octets g of a stage (a warp: 32
-    // consecutive rows, so every staging load reads 128 contiguous bytes); the 16-byte
-    // digit stores of 8 consecutive rows fill one core matrix (128 contiguous bytes)
-    const int r = tid - kFirstConvWarp * 32;  // 0..127
-    for (int k = 0; k < nst; ++k) {
-      const int s = k % kStages;
-      if (!tc::mbar_wait_warp(&bars.full[s], (k / kStages) & 1, &abort_flag, err, wb)) break;
-      const float* xs = reinterpret_cast<const float*>(st_x(s));
-      uint32_t w[2][kDigits][4];
-#pragma unroll
-      for (int g = 0; g < 2; ++g) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int cl = 8 * g + 2 * i;  // column within the stage
-          const int c0 = k * kK + cl;     // column of X
-          const int e0 = c0 < J.m ? J.exps[c0] : kExpZero;
-          const int e1 = c0 + 1 < J.m ? J.exps[c0 + 1] : kExpZero;
-          const float x0 = xs[cl * kRowsT + r], x1 = xs[(cl + 1) * kRowsT + r];
-          const bool v0 = e0 > kExpZero && e0 < kExpBad, v1 = e1 > kExpZero && e1 < kExpBad;
-          float da[kDigits], db[kDigits];
-          digits4(v0 ? ldexpf(x0, 31 - e0) : 0.f, da);
-          digits4(v1 ? ldexpf(x1, 31 - e1) : 0.f, db);
-#pragma unroll
-          for (int t = 0; t < kDigits; ++t) w[g][t][i] = h2bits(da[t], db[t]);
+    // thread (r, g): row r of the tile, column octet g of the stage (a warp: 32
+    // consecutive rows, every staging load 128 contiguous bytes); its 16-byte digit
+    // stores fill core-matrix rows
+    const int ct = tid - kFirstConvWarp * 32;  // 0..255
+    const int r = ct & (kRowsT - 1), g8 = ct >> 7;
+    const uint32_t off = (uint32_t)(r >> 3) * kSbo + (uint32_t)g8 * kLbo + (uint32_t)(r & 7) * 16;
+    int64_t g = 0;
+    bool ok = true;
+    for (int64_t it = blockIdx.x; it < total_items && ok; it += gridDim.x) {
+      const Item I = item_of(jobs, njobs, it);
+      const float2* __restrict__ xsc = jobs[I.jb].xscale;
+      for (int k = 0; k < I.nst; ++k, ++g) {
+        const int s = (int)(g % kStages);
+        const uint32_t use = (uint32_t)(g / kStages);
+        if (!tc::mbar_wait_warp(&bars.full[s], use & 1, &abort_flag, err, wb)) {
+          ok = false;
+          break;
         }
-      }
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&bars.xfree[s]);  // this warp's staging reads are done
-      if (k >= kStages && !tc::mbar_wait_warp(&bars.ofree[s], ((k / kStages) - 1) & 1, &abort_flag, err, wb)) break;
+        const float* xs = reinterpret_cast<const float*>(st_x(s));
+        uint32_t b[8];
 #pragma unroll
-      for (int g = 0; g < 2; ++g) {
-        const uint32_t off = (uint32_t)(r >> 3) * kSbo + (uint32_t)g * kLbo + (uint32_t)(r & 7) * 16;
+        for (int i = 0; i < 8; ++i) {
+          const int cl = 8 * g8 + i;
+          const float2 sc = xsc[k * kK + cl];  // zero beyond m and for zero or non-finite columns
+          b[i] = (uint32_t)__float2int_rn((xs[cl * kRowsT + r] * sc.x) * sc.y) + 0x80808080u;
+        }
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&bars.xfree[s]);  // this warp's staging reads are done
+        if (g >= kStages && !tc::mbar_wait_warp(&bars.ofree[s], (use - 1) & 1, &abort_flag, err, wb)) {
+          ok = false;
+          break;
+        }
 #pragma unroll
-        for (int t = 0; t < kDigits; ++t)
+        for (int t = 0; t < kDigits; ++t) {
+          const uint32_t bs = 3u - (uint32_t)t;  // digit t = byte 3 - t
+          const uint32_t sel = bs | (bs << 4) | ((bs + 4u) << 8) | ((bs + 4u) << 12);
           *reinterpret_cast<uint4*>(op_x(s) + t * kPlaneX + off) =
-              make_uint4(w[g][t][0], w[g][t][1], w[g][t][2], w[g][t][3]);
+              make_uint4(digit_pair(b[0], b[1], sel), digit_pair(b[2], b[3], sel), digit_pair(b[4], b[5], sel),
+                         digit_pair(b[6], b[7], sel));
+        }
+        tc::fence_async_smem();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&bars.ofull[s]);
       }
-      tc::fence_async_smem();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&bars.ofull[s]);
     }
   } else {
     // ------------------------------------------------------------ output
@@ -246,44 +281,54 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int q = warp & 3;               // TMEM lane quarter = rows 32 q .. 32 q + 31
     const int h = ow >> 2;                // modes 32 h .. 32 h + 31 of the tile
     const uint32_t lanes = (uint32_t)(32 * q) << 16;
-    long long acc[32];
-#pragma unroll
-    for (int c = 0; c < 32; ++c) acc[c] = 0;
+    int64_t ch = 0;
     bool ok = true;
-    for (int ch = 0; ch < nchunk && ok; ++ch) {
-      const int set = ch & 1;
-      ok = tc::mbar_wait_warp(&bars.acc_full[set], (ch >> 1) & 1, &abort_flag, err, wb);
-      if (!ok) break;
-      tc::tc_fence_after();
+    for (int64_t it = blockIdx.x; it < total_items && ok; it += gridDim.x) {
+      const Item I = item_of(jobs, njobs, it);
+      const FxModesJob& J = jobs[I.jb];
+      const int nchunk = (I.nst + kChunkStages - 1) / kChunkStages;
+      long long acc[32];
 #pragma unroll
-      for (int g8 = 0; g8 < 4; ++g8) {
-        const uint32_t col = (uint32_t)set * kSetCols + (uint32_t)(32 * h + 8 * g8);
-        uint32_t l2[8], l3[8], l4[8], l5[8];
-        tc::tmem_ld8_raw(tbase + lanes + col, l2);
-        tc::tmem_ld8_raw(tbase + lanes + col + kModesT, l3);
-        tc::tmem_ld8_raw(tbase + lanes + col + 2 * kModesT, l4);
-        tc::tmem_ld8_raw(tbase + lanes + col + 3 * kModesT, l5);
-        tc::tmem_wait_ld();
-        tc::reg_barrier8(l2);
-        tc::reg_barrier8(l3);
-        tc::reg_barrier8(l4);
-        tc::reg_barrier8(l5);
+      for (int c = 0; c < 32; ++c) acc[c] = 0;
+      for (int c = 0; c < nchunk; ++c, ++ch) {
+        const int set = (int)(ch & 1);
+        if (!tc::mbar_wait_warp(&bars.acc_full[set], (uint32_t)(ch >> 1) & 1, &abort_flag, err, wb)) {
+          ok = false;
+          break;
+        }
+        tc::tc_fence_after();
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
-          acc[8 * g8 + i] += (long long)__float2int_rn(__uint_as_float(l2[i])) * 16777216LL +
-                             (long long)__float2int_rn(__uint_as_float(l3[i])) * 65536LL +
-                             (long long)__float2int_rn(__uint_as_float(l4[i])) * 256LL +
-                             (long long)__float2int_rn(__uint_as_float(l5[i]));
+        for (int g8 = 0; g8 < 4; ++g8) {
+          const uint32_t col = (uint32_t)set * kSetCols + (uint32_t)(32 * h + 8 * g8);
+          uint32_t l2[8], l3[8], l4[8], l5[8];
+          tc::tmem_ld8_raw(tbase + lanes + col, l2);
+          tc::tmem_ld8_raw(tbase + lanes + col + kModesT, l3);
+          tc::tmem_ld8_raw(tbase + lanes + col + 2 * kModesT, l4);
+          tc::tmem_ld8_raw(tbase + lanes + col + 3 * kModesT, l5);
+          tc::tmem_wait_ld();
+          tc::reg_barrier8(l2);
+          tc::reg_barrier8(l3);
+          tc::reg_barrier8(l4);
+          tc::reg_barrier8(l5);
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            acc[8 * g8 + i] += (long long)__float2int_rn(__uint_as_float(l2[i])) * 16777216LL +
+                               (long long)__float2int_rn(__uint_as_float(l3[i])) * 65536LL +
+                               (long long)__float2int_rn(__uint_as_float(l4[i])) * 256LL +
+                               (long long)__float2int_rn(__uint_as_float(l5[i]));
+        }
+        tc::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&bars.acc_empty[set]);
       }
-      tc::tc_fence_before();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&bars.acc_empty[set]);
-    }
-    if (__all_sync(0xffffffffu, ok && !abort_flag)) {
-      const int64_t row = row0 + 32 * q + lane;
+      if (!ok || abort_flag) break;
+      // y = acc 2^(F_c - 37) scale_c in FP32 arithmetic (GB300 runs FP64 at 1/64 of the
+      // FP32 rate): one rounding of the int64 sum, an exact power-of-two scaling
+      // (ldexpf rounds only in the subnormal range) and the FP32 scale
+      const int64_t row = I.row0 + 32 * q + lane;
 #pragma unroll
       for (int c = 0; c < 32; ++c) {
-        const int col = mt * kModesT + 32 * h + c;
+        const int col = I.mt * kModesT + 32 * h + c;
         if (col >= J.k || row >= J.n) continue;
         const int F = J.fexp[col];
         float y;
@@ -292,7 +337,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         else if (F <= kExpZero)
           y = 0.f;
         else
-          y = (float)(ldexp((double)acc[c], F - 38) * (J.scale ? J.scale[col] : 1.0));
+          y = ldexpf(__ll2float_rn(acc[c]), F - 37) * J.yscale[col];
         J.Y[(size_t)col * J.ldy + row] = y;
       }
     }
@@ -347,7 +392,26 @@ __global__ void __launch_bounds__(256) modes_fx_vsplit(const FxVSplitJob* __rest
   }
   __syncthreads();
   const int F = s_max[0];
-  if (tid == 0) J.fexp[c] = F;
+  if (tid == 0) {
+    J.fexp[c] = F;
+    J.yscale[c] = c < J.k && J.scale ? (float)J.scale[c] : 1.0f;
+  }
+  // the block of mode 0 also writes the X scale pairs s1 s2 = 2^(30 - E_j) of the
+  // converters (zero for zero or non-finite columns and for the padding up to whole
+  // 16-column stages)
+  if (c == 0) {
+    const int npad = (J.m + kK - 1) / kK * kK;
+    for (int j = tid; j < npad; j += blockDim.x) {
+      float s1 = 0.f, s2 = 0.f;
+      const int E = j < J.m ? J.exps[j] : kExpZero;
+      if (E > kExpZero && E < kExpBad) {
+        const int e = 30 - E, e1 = max(-126, min(127, e));
+        s1 = ldexpf(1.0f, e1);
+        s2 = ldexpf(1.0f, e - e1);
+      }
+      J.xscale[j] = make_float2(s1, s2);
+    }
+  }
   // digits, column by column of V (the contraction index j), zero beyond m and k
   const int mt = c / kModesT, cc = c % kModesT;
   const int nst = (J.m + kK - 1) / kK;
@@ -419,6 +483,7 @@ __global__ void __launch_bounds__(256) fx_colexp(const float* __restrict__ X, in
 }  // namespace
 
 int fx_modes_tile() { return kModesT; }
+size_t fx_xscale_bytes(int64_t m) { return (size_t)((m + kK - 1) / kK * kK) * sizeof(float2); }
 size_t fx_vdig_bytes(int64_t m, int64_t k) {
   const int64_t nst = (m + kK - 1) / kK, mtiles = (k + kModesT - 1) / kModesT;
   return (size_t)(mtiles * nst) * kOpV;
@@ -441,7 +506,14 @@ cudaError_t launch_modes_fx(const FxVSplitJob* vjobs_dev, int njobs, int max_kpa
   modes_fx_vsplit<<<dim3((unsigned)max_kpad, (unsigned)njobs), 256, 0, s>>>(vjobs_dev, njobs);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  modes_fx_kernel<<<(unsigned)total_items, kThreads, kSmemBytes, s>>>(jobs_dev, maps_dev, njobs, err_flag);
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
+  }
+  const int64_t grid = total_items < sms ? total_items : sms;
+  modes_fx_kernel<<<(unsigned)grid, kThreads, kSmemBytes, s>>>(jobs_dev, maps_dev, njobs, total_items, err_flag);
   return cudaGetLastError();
 }
 
