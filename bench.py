@@ -72,6 +72,14 @@ C5_WORKLOAD = ("streamed incremental HAPOD, n=2^23 FP32 rows, 4096 snapshots gen
                "(2 GiB each, 8 chunks resident at a time), left-deep chain of 4 binary subtrees of depth 4 (L_T=8), "
                "eps=1e-4 rel, omega=0.5")
 
+# batched uneven leaves: 1000 prescribed-spectrum leaves with m ~ U{16..512}
+C4 = {"name": "c4", "n": 1 << 18, "leaves": 1000, "lo": 16, "hi": 512, "rank": 200, "arity": 4, "depth": 5,
+      "eps_rel": 1e-5, "omega": 0.5, "wave": 64, "seed": 1607052104}
+C4_WORKLOAD = ("batched uneven leaves, n=2^18 FP32 rows, 1000 leaves with m ~ U{16..512} (265336 columns, 278 GB, "
+               "generated on the device in waves of 64 leaves), shared rank-200 basis, sigma_j = 10^(-delta j) with "
+               "delta ~ U[1/40, 1/10] per leaf, + 1e-10 N(0,1), quaternary tree L_T=6 (first 1000 of 1024 slots), "
+               "eps=1e-5 rel, omega=0.5")
+
 # FP64 advection-diffusion workload, resident
 N_ROWS = 1 << 20
 LEAVES = 64
@@ -149,6 +157,14 @@ def c3_tree(wl=C3):
     columns i * cols .. (i + 1) * cols - 1 of the trajectory."""
     from paper_1607_05210_gb300 import synth
 
+    if wl["name"] == "c4":
+        parent = synth.balanced_tree(wl["arity"], wl["depth"], wl["leaves"])
+        leaves = synth.leaves_of(parent)
+        m = synth.uneven_leaf_cols(wl["seed"], wl["leaves"], wl["lo"], wl["hi"])
+        cols = [0] * len(parent)
+        for i, a in enumerate(leaves):
+            cols[a] = int(m[i])
+        return parent, leaves, cols
     if wl["name"] == "c5":
         parent = synth.chain_of_subtrees(wl["subtrees"], wl["depth"])
         leaves = synth.leaves_of(parent)
@@ -172,8 +188,9 @@ def c3_params(H, wl=C3):
     return H.synth_params(**synth.pulse_workload(wl["seed"]))
 
 
-class Generator:
-    """Leaf i of the workload = global columns i * cols .. (i + 1) * cols - 1."""
+class PulseGenerator:
+    """Leaf i of the travelling-pulse workloads = global columns i * cols .. (i + 1) *
+    cols - 1, written by the library's device generator."""
 
     def __init__(self, H, wl, dtype, device, nbuf):
         import torch
@@ -183,17 +200,71 @@ class Generator:
         self.bufs = [torch.empty((wl["cols"], wl["n"]), dtype=dtype, device=device) for _ in range(nbuf)]
 
     def gen(self, leaf_index, slot, stream):
+        """Leaf `leaf_index` into buffer `slot` (on `stream`); returns the cols x n view."""
         wl = self.wl
         self.H.hapod_synth_snapshots(self.params, wl["n"], leaf_index * wl["cols"], wl["cols"],
                                      self.bufs[slot].t(), stream=stream)
         return self.bufs[slot]
 
 
+class UnevenGenerator:
+    """Leaf i of the batched workload: Q[:, :r] diag(sigma_i) W_i^T + 1e-10 N(0, 1) formed
+    on the device in FP32 (the FP64 form receives the same FP32 values).  Q (n x 200) and
+    the W_i are drawn on the host once (synth.shared_basis, synth.leaf_factors); the noise
+    comes from torch's device generator seeded per leaf."""
+
+    _cache = {}
+
+    def __init__(self, H, wl, dtype, device, nbuf):
+        import numpy as np
+        import torch
+
+        from paper_1607_05210_gb300 import synth
+
+        self.wl, self.dtype, self.device = wl, dtype, device
+        key = (wl["seed"], wl["n"], wl["leaves"], str(device))
+        if key not in UnevenGenerator._cache:
+            m = synth.uneven_leaf_cols(wl["seed"], wl["leaves"], wl["lo"], wl["hi"])
+            delta = synth.uneven_decays(wl["seed"], wl["leaves"])
+            Q = torch.from_numpy(synth.shared_basis(wl["seed"], wl["n"], wl["rank"]).astype(np.float32)).to(device)
+            WS = []
+            for i in range(wl["leaves"]):
+                W, sg = synth.leaf_factors(wl["seed"], i, int(m[i]), wl["rank"], float(delta[i]))
+                WS.append(torch.from_numpy((W * sg).astype(np.float32)).to(device))  # m x r
+            UnevenGenerator._cache[key] = (m, Q, WS)
+        self.m, self.Q, self.WS = UnevenGenerator._cache[key]
+        mmax = int(self.m.max())
+        self.bufs = [torch.empty((mmax, wl["n"]), dtype=dtype, device=device) for _ in range(nbuf)]
+        self.g = torch.Generator(device=device)
+
+    def gen(self, leaf_index, slot, stream):
+        import torch
+
+        m = int(self.m[leaf_index])
+        with torch.cuda.stream(stream):
+            WS = self.WS[leaf_index]
+            Xt = WS @ self.Q[:, :WS.shape[1]].t()  # m x n: row j = snapshot j
+            self.g.manual_seed(self.wl["seed"] * 4096 + leaf_index)
+            Xt += 1e-10 * torch.randn(Xt.shape, generator=self.g, device=self.device, dtype=torch.float32)
+            out = self.bufs[slot][:m]
+            out.copy_(Xt)
+            del Xt
+        return out
+
+
+def make_generator(H, wl, dtype, device, nbuf):
+    return UnevenGenerator(H, wl, dtype, device, nbuf) if wl["name"] == "c4" else PulseGenerator(H, wl, dtype,
+                                                                                                  device, nbuf)
+
+
+Generator = make_generator
+
+
 def c3_fro2(H, wl, device, stream):
     """||X||_F^2 of the whole workload (FP64 sum of the FP32 snapshots), untimed."""
     import torch
 
-    g = Generator(H, wl, torch.float32, device, 1)
+    g = make_generator(H, wl, torch.float32, device, 1)
     tot = 0.0
     with torch.cuda.stream(stream):
         for i in range(wl["leaves"]):
@@ -213,7 +284,7 @@ def run_waves(H, precision, wl, fro2, steps, warmup, stream, dist_ctx, host=None
     dtype = H.DTYPE[precision]
     device = torch.device("cuda", torch.cuda.current_device())
     W = wl["wave"]
-    gen = Generator(H, wl, dtype, device, W)
+    gen = make_generator(H, wl, dtype, device, W)
     eps = wl["eps_rel"] * math.sqrt(fro2)
     copy_stream = torch.cuda.Stream(device) if host is not None else None
     info = {}
@@ -227,15 +298,16 @@ def run_waves(H, precision, wl, fro2, steps, warmup, stream, dist_ctx, host=None
         d2h = 0
         for w0 in range(0, len(leaves), W):
             g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            views = {}
             with torch.cuda.stream(stream):
                 g0.record(stream)
                 for i in range(w0, min(len(leaves), w0 + W)):
-                    gen.gen(i, i - w0, stream)
+                    views[i] = gen.gen(i, i - w0, stream)
                 g1.record(stream)
             if host is not None:  # untimed: the wave's leaves to pinned host memory
                 with torch.cuda.stream(stream):
                     for i in range(w0, min(len(leaves), w0 + W)):
-                        host[i - w0].copy_(gen.bufs[i - w0], non_blocking=True)
+                        host[i - w0][:views[i].shape[0]].copy_(views[i], non_blocking=True)
                 stream.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -244,14 +316,14 @@ def run_waves(H, precision, wl, fro2, steps, warmup, stream, dist_ctx, host=None
                 done = []
                 with torch.cuda.stream(copy_stream):
                     for i in range(w0, min(len(leaves), w0 + W)):
-                        gen.bufs[i - w0].copy_(host[i - w0], non_blocking=True)
+                        views[i].copy_(host[i - w0][:views[i].shape[0]], non_blocking=True)
                         ev = torch.cuda.Event()
                         ev.record(copy_stream)
                         done.append(ev)
             for i in range(w0, min(len(leaves), w0 + W)):
                 if host is not None:
                     stream.wait_event(done[i - w0])
-                H.hapod_push(ctx, leaves[i], gen.bufs[i - w0].t())
+                H.hapod_push(ctx, leaves[i], views[i].t())
             if w0 + W >= len(leaves):
                 s, U, st = H.hapod_result(ctx, device=device)
                 if host is not None:
@@ -292,7 +364,7 @@ def run_waves(H, precision, wl, fro2, steps, warmup, stream, dist_ctx, host=None
            "k": info["_k"], "status": info["_status"], "sigma": info["_sigma"], "nodes": info["_nodes"],
            "gen_ms": gen_ms[0] / steps, "parent": parent, **_rank_summary(parent, info["_nodes"])}
     if host is not None:
-        res["h2d_bytes"] = sum(h.numel() * h.element_size() for h in host) * (len(leaves) // W)
+        res["h2d_bytes"] = sum(cols) * wl["n"] * es
         res["d2h_bytes"] = d2h
     del gen
     torch.cuda.empty_cache()
@@ -718,8 +790,10 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workloads", default="c5,c2",
-                    help="comma list of extra workloads beside the headline: 'c5' (streamed incremental chain, "
+    ap.add_argument("--workloads", default="c4,c5,c2",
+                    help="comma list of extra workloads beside the headline: 'c4' (1000 uneven prescribed-spectrum "
+                         "leaves, device-generated; 'c4-fp64' adds its digit-slice FP64 form), 'c5' (streamed "
+                         "incremental chain, "
                          "device-generated chunks), 'c2' (FP64 advection-diffusion, binary tree and star, "
                          "resident), 'none'")
     ap.add_argument("--no-e2e", action="store_true")
@@ -827,6 +901,19 @@ def main():
                                                   if s2[j] >= 1e-5 * s2[0]] or [0.0])}
 
     workloads = {}
+    if "c4" in args.workloads:
+        fro2_c4 = c3_fro2(H, C4, device, stream)
+        total_c4 = int(sum(c3_tree(C4)[2])) * world
+        st4 = max(1, min(args.steps, 2))
+        r4 = run_waves(H, H.HAPOD_MIXED_FX3, C4, fro2_c4, st4, 1, stream, dist_ctx)
+        k1 = f"c4/mixed_fx3@{C4['eps_rel']:g}"
+        workloads[k1] = summarise(r4, H.HAPOD_MIXED_FX3, H, C4["eps_rel"], total_c4, hbm, peak_src, world, "gram")
+        if "c4-fp64" in args.workloads:
+            r4b = run_waves(H, H.HAPOD_FP64_OZAKI, C4, fro2_c4, st4, 1, stream, dist_ctx)
+            workloads[f"c4/fp64_ozaki@{C4['eps_rel']:g}"] = summarise(r4b, H.HAPOD_FP64_OZAKI, H, C4["eps_rel"],
+                                                                     total_c4, hbm, peak_src, world, "gram")
+            workloads[k1]["speedup_vs_fp64_form_same_eps"] = r4b["ms"] / r4["ms"]
+        workloads["c4_workload"] = C4_WORKLOAD
     if "c5" in args.workloads:
         fro2_c5 = c3_fro2(H, C5, device, stream)
         total_c5 = C5["leaves"] * C5["cols"] * world

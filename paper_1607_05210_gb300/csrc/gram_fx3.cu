@@ -16,15 +16,21 @@
 // representation error is at most 2^(E-32): every FP32 value within 2^8 of its
 // block maximum is represented exactly.
 // Products: x_i x_j = 2^(E_i+E_j-62) sum_{t,u} d_t d_u 2^(8(8-t-u)); the levels
-// s = t + u = 2..5 are kept (ten digit pairs; the dropped ones weigh less than
-// 2^(E_i+E_j-30.4) per row), each level summed over the block on the tensor cores:
-// L_s <= 64 * 4 * 2^14 = 2^22, an integer the FP32 accumulator holds exactly.
-// Flush: after each block, v = L_2 2^24 + L_3 2^16 + L_4 2^8 + L_5 (exact, < 2^45) is
-// added into an int64 fixed-point sum per entry whose unit is 2^(R_i+R_j-38), R the
-// running maximum of the block exponents (rounding shift; the sum is shifted down
-// when R grows).  The item writes ldexp(sum, R_i + R_j - 38) in FP64 -- one rounding
-// -- and row splits are summed in FP64 in a fixed order.  Columns holding Inf or NaN
-// give NaN rows and columns of G.
+// s = t + u = 2..6 are kept (thirteen digit pairs; the dropped ones weigh less than
+// 2^(E_i+E_j-38.9) per row).  Levels 2..5 are summed over the block on the tensor
+// cores as integers, L_s <= 64 * 4 * 2^14 = 2^22, which the FP32 accumulator holds
+// exactly; the three level-6 pairs enter the level-5 accumulator through B digit
+// planes scaled by 2^-8 (exact in fp16), so L'_5 = L_5 + 2^-8 L_6 carries a fraction
+// whose FP32 rounding is below 2^-24 |L'_5| per step.  (Dropping level 6 instead
+// leaves a random error of 2^(E_i+E_j-33.6) per row, which at n ~ 2^10..2^18 rows
+// reaches the tail sums of eps = 1e-5 rel.)
+// Flush: after each block, v = L_2 2^28 + L_3 2^20 + L_4 2^12 + rint(16 L'_5) (exact,
+// |v| < 2^48.1) is added into an int64 fixed-point sum per entry whose unit is
+// 2^(R_i+R_j-42), R the running maximum of the block exponents (rounding shift; the
+// sum is shifted down when R grows); a row split holds at most 2^20 rows, so the sum
+// stays below 2^62.1.  The item writes ldexp(sum, R_i + R_j - 42) in FP64 -- one
+// rounding -- and row splits are summed in FP64 in a fixed order.  Columns holding
+// Inf or NaN give NaN rows and columns of G.
 //
 // Work item = one 128 x 64 tile (A columns 128 I.., B columns 64 J.., J >= 2 I) of
 // one node's G over one row split; items are ordered by split first.  One CTA per
@@ -34,8 +40,10 @@
 //                 6 (A only) or 4 stages deep
 //   warp 1        TMEM owner and single-thread MMA issuer: per 16 rows four MMAs,
 //                 digit t of A against the B digits 1 .. 5 - t (consecutive planes,
-//                 N = 64 (5 - t)) into the adjacent level accumulators L_{t+1} .. L_5;
-//                 two accumulator sets (2 x 256 TMEM columns) alternate between blocks
+//                 N = 64 (5 - t)) into the adjacent level accumulators L_{t+1} .. L_5,
+//                 and three (N = 64) of the A digits 2, 3, 4 against the scaled B
+//                 digits 4, 3, 2 into L_5; two accumulator sets (2 x 256 TMEM columns)
+//                 alternate between blocks
 //   warps 2..9    converters: block column maxima, exponents, digits (K-major 8 x 8
 //                 core matrices, no swizzle), 2 stages deep
 //   warps 10..17  flushers: int64 sums of 32 entries per thread
@@ -65,7 +73,8 @@ constexpr int kStSlotsMax = kStRegion / kStA;          // 6 (B inside A) or kStR
 constexpr int kPlaneA = kRows * kACols * 2;            // one digit plane of A, 8 KB
 constexpr int kPlaneB = kRows * kBCols * 2;            // 4 KB
 constexpr int kDigits = 4;
-constexpr int kOpSlot = kDigits * (kPlaneA + kPlaneB);  // 48 KB
+constexpr int kScaled = 3;                             // B digits 2..4 scaled by 2^-8 (level 6 into L_5)
+constexpr int kOpSlot = kDigits * (kPlaneA + kPlaneB) + kScaled * kPlaneB;  // 60 KB
 constexpr int kOpSlots = 2;
 constexpr int kExpSlots = 2;
 constexpr int kSmemBytes = kStRegion + kOpSlots * kOpSlot + 1024;
@@ -78,7 +87,8 @@ constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kSetCols = 256;                     // one set of L2 | L3 | L4 | L5
 constexpr int kExpZero = kFxExpZero;                   // exponent of an all-zero column block
 constexpr int kExpBad = kFxExpBad;                     // exponent marking Inf / NaN
-static_assert(kSmemBytes <= 227 * 1024, "shared memory");
+static_assert(kSmemBytes + 2048 <= 227 * 1024, "shared memory");
+constexpr int64_t kMaxSplitRows = (int64_t)1 << 20;   // keeps the int64 sums below 2^62.1
 
 struct Bars {
   uint64_t full[kStSlotsMax];     // TMA -> converters
@@ -144,15 +154,17 @@ __device__ __forceinline__ void scales(int E, float& s1, float& s2) {
 }
 
 // Convert the unit (column c of the staged panel, row octet g) of one stage: 8 values
-// from the 128-byte-swizzled staging, four fp16 digit planes out at column dc, and
-// again at column dc2 of the second plane set `planes2` when that is not null.
+// from the 128-byte-swizzled staging, four fp16 digit planes out at column dc (B
+// planes, planes_are_b, are followed by the three scaled planes of digits 2..4), and
+// with `dup` again at column dc2 of the B plane set `planes2` (digits and scaled).
+template <bool planes_are_b, bool dup>
 __device__ __forceinline__ void convert_unit(const uint8_t* __restrict__ st, int c, uint8_t* __restrict__ planes,
-                                             uint32_t plane_bytes, int dc, uint8_t* __restrict__ planes2,
-                                             uint32_t plane_bytes2, int dc2, int g, float s1, float s2) {
+                                             uint32_t plane_bytes, int dc, uint8_t* __restrict__ planes2, int dc2,
+                                             int g, float s1, float s2) {
   const float4 v0 = *reinterpret_cast<const float4*>(st + c * 128 + (((2 * g) ^ (c & 7)) << 4));
   const float4 v1 = *reinterpret_cast<const float4*>(st + c * 128 + (((2 * g + 1) ^ (c & 7)) << 4));
   const float x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-  uint32_t w[kDigits][4];
+  uint32_t w[kDigits][4], ws[kScaled][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     float da[kDigits], db[kDigits];
@@ -160,16 +172,31 @@ __device__ __forceinline__ void convert_unit(const uint8_t* __restrict__ st, int
     digits4(x[2 * i + 1], s1, s2, db);
 #pragma unroll
     for (int t = 0; t < kDigits; ++t) w[t][i] = h2bits(da[t], db[t]);
+    if (planes_are_b || dup) {
+#pragma unroll
+      for (int t = 0; t < kScaled; ++t)  // d 2^-8, |d| <= 128: exact in fp16
+        ws[t][i] = h2bits(da[t + 1] * 0.00390625f, db[t + 1] * 0.00390625f);
+    }
   }
   const uint32_t off = (uint32_t)(dc >> 3) * kSbo + (uint32_t)g * kLbo + (uint32_t)(dc & 7) * 16;
 #pragma unroll
   for (int t = 0; t < kDigits; ++t)
     *reinterpret_cast<uint4*>(planes + t * plane_bytes + off) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
-  if (planes2) {
+  if constexpr (planes_are_b) {
+#pragma unroll
+    for (int t = 0; t < kScaled; ++t)
+      *reinterpret_cast<uint4*>(planes + (kDigits + t) * plane_bytes + off) =
+          make_uint4(ws[t][0], ws[t][1], ws[t][2], ws[t][3]);
+  }
+  if constexpr (dup) {
     const uint32_t off2 = (uint32_t)(dc2 >> 3) * kSbo + (uint32_t)g * kLbo + (uint32_t)(dc2 & 7) * 16;
 #pragma unroll
     for (int t = 0; t < kDigits; ++t)
-      *reinterpret_cast<uint4*>(planes2 + t * plane_bytes2 + off2) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
+      *reinterpret_cast<uint4*>(planes2 + t * kPlaneB + off2) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
+#pragma unroll
+    for (int t = 0; t < kScaled; ++t)
+      *reinterpret_cast<uint4*>(planes2 + (kDigits + t) * kPlaneB + off2) =
+          make_uint4(ws[t][0], ws[t][1], ws[t][2], ws[t][3]);
   }
 }
 
@@ -295,6 +322,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int tt = 0; tt < kDigits; ++tt)
             tc::umma_f16(d + (uint32_t)(kBCols * tt), tc::ns_desc(pa + (uint32_t)tt * kPlaneA + ko, kLbo, kSbo),
                          tc::ns_desc(pb + ko, kLbo, kSbo), idn[tt], (blk_first && kk == 0 && tt == 0) ? 0u : 1u);
+          // level 6 into L_5: A digit 2, 3, 4 against the scaled B digit 4, 3, 2
+#pragma unroll
+          for (int tt = 1; tt < kDigits; ++tt)
+            tc::umma_f16(d + (uint32_t)(kBCols * (kDigits - 1)),
+                         tc::ns_desc(pa + (uint32_t)tt * kPlaneA + ko, kLbo, kSbo),
+                         tc::ns_desc(pb + (uint32_t)(kDigits + kDigits - 1 - tt) * kPlaneB + ko, kLbo, kSbo),
+                         idn[kDigits - 1], 1u);
         }
         tc::umma_commit(&bars.op_free[t]);
         if (blk_last) tc::umma_commit(&bars.acc_full[set]);
@@ -367,13 +401,16 @@ __global__ void __launch_bounds__(kThreads, 1)
           float s1, s2;
           scales(sh.exps[es][c], s1, s2);
           const bool dup = b_in_a && c >= b0 - a0 && c < b0 - a0 + kBCols;  // also a B column
-          convert_unit(st_a(s), c, op_a(t), kPlaneA, c, dup ? op_b(t) : nullptr, kPlaneB, c - (b0 - a0), g, s1, s2);
+          if (dup)
+            convert_unit<false, true>(st_a(s), c, op_a(t), kPlaneA, c, op_b(t), c - (b0 - a0), g, s1, s2);
+          else
+            convert_unit<false, false>(st_a(s), c, op_a(t), kPlaneA, c, nullptr, 0, g, s1, s2);
         }
         if (!b_in_a) {  // B panel: 64 columns x 4 octets = 256 units, one per thread
           const int c = ct & (kBCols - 1), g = ct >> 6;
           float s1, s2;
           scales(sh.exps[es][kACols + c], s1, s2);
-          convert_unit(st_b(s), c, op_b(t), kPlaneB, c, nullptr, 0, 0, g, s1, s2);
+          convert_unit<true, false>(st_b(s), c, op_b(t), kPlaneB, c, nullptr, 0, g, s1, s2);
         }
         tc::fence_async_smem();
         __syncwarp();
@@ -445,10 +482,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           const int jj = 8 * g + i;  // column within the warp's 32
-          const long long v = (long long)__float2int_rn(__uint_as_float(l2[i])) * 16777216LL +
-                              (long long)__float2int_rn(__uint_as_float(l3[i])) * 65536LL +
-                              (long long)__float2int_rn(__uint_as_float(l4[i])) * 256LL +
-                              (long long)__float2int_rn(__uint_as_float(l5[i]));
+          const long long v = (long long)__float2int_rn(__uint_as_float(l2[i])) * 268435456LL +
+                              (long long)__float2int_rn(__uint_as_float(l3[i])) * 1048576LL +
+                              (long long)__float2int_rn(__uint_as_float(l4[i])) * 4096LL +
+                              (long long)__float2int_rn(__uint_as_float(l5[i]) * 16.0f);
           if (plain) {  // no exponent moved and every block exponent is the running one
             acc[jj] += v;
           } else {
@@ -486,7 +523,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         else if (Ri <= kExpZero || Rj <= kExpZero)
           v = 0.0;
         else
-          v = ldexp((double)acc[jj], Ri + Rj - 38);
+          v = ldexp((double)acc[jj], Ri + Rj - 42);
         if (out) {
           out[(size_t)ai * kBCols + bj] = v;
         } else if (gi < J.m && gj < J.m && gj >= gi) {
@@ -562,6 +599,7 @@ void plan_gram_fx3(GramJob* jobs, int njobs, int target_items, std::vector<int4>
   for (int j = 0; j < njobs; ++j) {
     GramJob& J = jobs[j];
     int64_t s = std::max<int64_t>(1, std::min(splits, std::max<int64_t>(1, J.n / min_rows)));
+    s = std::max<int64_t>(s, (J.n + kMaxSplitRows - 1) / kMaxSplitRows);
     int64_t rps = (J.n + s - 1) / s;
     rps = (rps + 63) / 64 * 64;  // whole 64-row exponent blocks
     s = std::max<int64_t>(1, (J.n + rps - 1) / rps);

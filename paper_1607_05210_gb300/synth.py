@@ -20,6 +20,10 @@ stand in for the paper's PDE snapshot data (Sec. 4), which is not available:
   column range (a leaf, a stream chunk) is reproducible on its own; host twin of
   the library's device generator ``hapod_synth_snapshots`` (FP64 arithmetic here,
   FP32 there).
+* ``uneven_leaf_cols`` / ``uneven_decays`` / ``shared_basis`` / ``uneven_leaf``: the
+  batched workload's leaves, X_l = Q[:, :r] diag(10^(-delta_l j)) W_l^T + noise with a
+  shared orthonormal Q, per-leaf orthonormal W_l, m_l ~ U{16..512} columns and
+  delta_l ~ U[1/40, 1/10] decades per index.
 * tree builders returning parent arrays (root has parent -1).
 """
 from __future__ import annotations
@@ -290,3 +294,37 @@ def pulse_snapshots(n: int, col0: int, ncols: int, params: Dict, dtype=np.float3
 def advection_pulses(n: int, num_cols: int, seed: int, dtype=np.float64) -> np.ndarray:
     """Columns 0 .. num_cols - 1 of the travelling-pulse trajectory of ``seed``."""
     return pulse_snapshots(n, 0, num_cols, pulse_workload(seed), dtype)
+
+
+# --------------------------------------------------- uneven prescribed-spectrum leaves
+def uneven_leaf_cols(seed: int, num_leaves: int, lo: int = 16, hi: int = 512) -> np.ndarray:
+    """Column counts m_l ~ U{lo .. hi} of the batched workload's leaves."""
+    return np.random.default_rng(seed).integers(lo, hi + 1, num_leaves)
+
+
+def uneven_decays(seed: int, num_leaves: int, lo: float = 1.0 / 40.0, hi: float = 1.0 / 10.0) -> np.ndarray:
+    """Per-leaf decay rates delta_l ~ U[lo, hi] decades per index (sigma_j = 10^(-delta_l j))."""
+    return np.random.default_rng(seed + 1).uniform(lo, hi, num_leaves)
+
+
+def shared_basis(seed: int, n: int, rank: int = 200) -> np.ndarray:
+    """The leaves' shared left factor Q (n x rank, orthonormal columns)."""
+    return orthonormal(np.random.default_rng(seed + 2), n, rank)
+
+
+def leaf_factors(seed: int, leaf: int, m: int, rank: int, delta: float):
+    """(W_l, sigma_l): W_l m x r orthonormal, sigma_j = 10^(-delta j), r = min(m, rank)."""
+    r = min(m, rank)
+    W = orthonormal(np.random.default_rng([seed, leaf]), m, r)
+    return W, 10.0 ** (-delta * np.arange(r))
+
+
+def uneven_leaf(Q: np.ndarray, seed: int, leaf: int, m: int, delta: float, noise: float = 1e-10,
+                dtype=np.float64) -> np.ndarray:
+    """Leaf l of the batched workload: Q[:, :r] diag(sigma_l) W_l^T + noise N(0, 1)
+    (n x m, column-major), r = min(m, rank of Q)."""
+    W, s = leaf_factors(seed, leaf, m, Q.shape[1], delta)
+    X = (Q[:, :W.shape[1]] * s) @ W.T
+    if noise:
+        X = X + noise * np.random.default_rng([seed, leaf, 1]).standard_normal(X.shape)
+    return np.asfortranarray(X.astype(dtype))

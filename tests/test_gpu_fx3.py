@@ -5,10 +5,12 @@ the CPU FP64 oracle run on the same FP32 values.
 Tolerances, derived from the arithmetic of gram_fx3.cu:
   * Gram: in a 64-row exponent block b column j is represented as an integer
     multiple of 2^(E_j - 31) with |x - x~| <= 2^(E_j - 32), 2^(E_j - 1) <= M_j^b < 2^E_j
-    (M the block maximum of |x|); the ten kept digit pairs (levels 2..5) leave out
-    less than 2^(E_i + E_j - 30.4) per row; the level sums are exact integers and the
-    int64 sums lose at most half a unit of 2^(R_i + R_j - 38) per shift.  Per row:
-    |x_i x_j - p| <= (2^-31 + 2^-30.4) 2^(E_i + E_j) <= 2^-27 M_i^b M_j^b, so
+    (M the block maximum of |x|); the thirteen kept digit pairs (levels 2..6) leave out
+    less than 2^(E_i + E_j - 38.9) per row; the level sums 2..4 are exact integers,
+    the FP32 rounding of L'_5 = L_5 + 2^-8 L_6 (28 steps per 64-row block, each below
+    2^-24 |L'_5| <= 2^-2 of its unit) adds less than 2^(E_i + E_j - 41) per row, and the
+    int64 sums lose at most half a unit of 2^(R_i + R_j - 42) per shift.  Per row:
+    |x_i x_j - p| <= (2^-31 + 2^-38.9 + 2^-41) 2^(E_i + E_j) <= 2^-27 M_i^b M_j^b, so
     |G - G_ref| <= 2^-27 sum_r M_i^b(r) M_j^b(r) + the oracle's FP64 rounding
     (1e-13 sqrt(n) sqrt(G_ii G_jj)).
   * exact case: small integers are represented exactly and every sum is an exact

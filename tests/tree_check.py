@@ -109,10 +109,10 @@ def waves_run(H, bench, wl, precision, fro2, stream):
                          max_pending_leaves=wl["wave"])
     with torch.cuda.stream(stream):
         for w0 in range(0, len(leaves), wl["wave"]):
-            for i in range(w0, w0 + wl["wave"]):
-                gen.gen(i, i - w0, stream)
-            for i in range(w0, w0 + wl["wave"]):
-                H.hapod_push(ctx, leaves[i], gen.bufs[i - w0].t())
+            idx = range(w0, min(len(leaves), w0 + wl["wave"]))
+            views = {i: gen.gen(i, i - w0, stream) for i in idx}
+            for i in idx:
+                H.hapod_push(ctx, leaves[i], views[i].t())
         s, U, st = H.hapod_result(ctx, device=device)
     stats = [H.hapod_node_stats(ctx, a) for a in range(len(parent))]
     H.hapod_destroy(ctx)
@@ -153,7 +153,7 @@ def full_size_waves(H, bench, wl):
     res = {}
     for form, prec in (("fx3", H.HAPOD_MIXED_FX3), ("fp64_ozaki", H.HAPOD_FP64_OZAKI)):
         s, U, stats, st = waves_run(H, bench, wl, prec, fro2, stream)
-        assert st == H.HAPOD_OK, form
+        assert st in (H.HAPOD_OK, H.HAPOD_WARN_BELOW_FLOOR), form
         assert all(stats[a]["tail_sq"] <= eps_nodes[a] ** 2 * (1 + 1e-12) for a in range(len(parent))), form
         perr = waves_projection_error(H, bench, wl, U)
         print(f"{wl['name']} {form}: k_root={len(s)} projection error {perr / bound:.4f} of the bound, "
