@@ -116,15 +116,15 @@ struct NodeBarrier {
   }
 };
 
-// Block-wide argmax of d[i] over unchosen i (ties: lowest index) and sum of the
-// positive d[i]; every thread of the CTA receives the results.
-__device__ void argmax_block(const double* d, const int32_t* chosen, int m, int& p, double& dmax, double& dsum,
+// Block-wide argmax of d[i] (ties: lowest index) and sum of the positive d[i];
+// chosen pivots hold -inf and take part in neither.  Every thread of the CTA
+// receives the results.
+__device__ void argmax_block(const double* d, int m, int& p, double& dmax, double& dsum,
                              double* red_v, int* red_i, double* red_s) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   double best = -1.0, sum = 0.0;
   int bi = -1;
   for (int i = tid; i < m; i += blockDim.x) {
-    if (chosen[i]) continue;
     const double v = d[i];
     if (v > 0.0) sum += v;
     if (v > best) {
@@ -191,8 +191,14 @@ __global__ void __launch_bounds__(kThreads) eig_coop_kernel(const EigJob* __rest
   const double* __restrict__ G = J.G;
   double* L = static_cast<double*>(J.A);  // m x m FP64 (first r columns used)
   T* W = static_cast<T*>(J.V);           // m x m in T: rotated columns, then eigenvectors
-  double* d = J.lam_tmp;                  // Schur complement diagonal during the factorisation
-  int32_t* chosen = J.perm;               // pivot flags during the factorisation
+  double* d = J.lam_tmp;                  // Schur complement diagonal (even steps), then eigenvalues
+  // odd steps of the factorisation read and write a second copy of the diagonal, so
+  // that no CTA overwrites entries another CTA of the node is still searching for the
+  // pivot of the same step (with one CTA the copy is d itself: the search ends in a
+  // CTA barrier before any update); W is free until the rotations start and holds at
+  // least m doubles whenever the node has more than one CTA (m > 8)
+  double* d_odd = P > 1 ? reinterpret_cast<double*>(W) : d;
+  int32_t* perm = J.perm;
   NodeResult* res = J.result;
   extern __shared__ double rowp[];        // row p of L
   __shared__ double red_v[kWarps], red_s[kWarps];
@@ -206,10 +212,7 @@ __global__ void __launch_bounds__(kThreads) eig_coop_kernel(const EigJob* __rest
   // ---------------- pivoted Cholesky (FP64)
   if (tid == 0) flag_sh = 0;
   __syncthreads();
-  for (int i = i0 + tid; i < i1; i += blockDim.x) {
-    d[i] = G[(size_t)i * m + i];
-    chosen[i] = 0;
-  }
+  for (int i = i0 + tid; i < i1; i += blockDim.x) d[i] = G[(size_t)i * m + i];
   // every CTA checks the whole diagonal for non-finite values (NaN/Inf in a column of
   // X reaches its diagonal entry) and forms the same trace
   for (int i = tid; i < m; i += blockDim.x)
@@ -218,7 +221,7 @@ __global__ void __launch_bounds__(kThreads) eig_coop_kernel(const EigJob* __rest
   {
     int p0;
     double dmax0, trace;
-    argmax_block(d, chosen, m, p0, dmax0, trace, red_v, red_i, red_s);
+    argmax_block(d, m, p0, dmax0, trace, red_v, red_i, red_s);
     const bool finite = flag_sh == 0 && isfinite(trace) && isfinite(dmax0);
     if (!finite && c == 0 && tid == 0) res->status = HAPOD_ERR_NONFINITE;
     const double tol = (sizeof(T) == sizeof(double)) ? (double)m * 1.1102230246251565e-16 : 1e-7;
@@ -232,7 +235,9 @@ __global__ void __launch_bounds__(kThreads) eig_coop_kernel(const EigJob* __rest
       for (int k = 0; k < m; ++k) {
         int p;
         double dmax, dsum;
-        argmax_block(d, chosen, m, p, dmax, dsum, red_v, red_i, red_s);
+        const double* dc = (k & 1) ? d_odd : d;  // this step's diagonal
+        double* dn = (k & 1) ? d : d_odd;        // the next step's
+        argmax_block(dc, m, p, dmax, dsum, red_v, red_i, red_s);
         resid = dsum;
         if (p < 0 || !(dmax > 0.0) || dsum <= stop) break;
         for (int j = tid; j < k; j += blockDim.x) rowp[j] = L[(size_t)j * m + p];
@@ -241,21 +246,20 @@ __global__ void __launch_bounds__(kThreads) eig_coop_kernel(const EigJob* __rest
         const double inv = 1.0 / piv;
         for (int i = i0 + tid; i < i1; i += blockDim.x) {
           double v;
+          const double di = dc[i];
           if (i == p) {
             v = piv;
-          } else if (chosen[i]) {
+            dn[i] = -INFINITY;  // chosen
+          } else if (di == -INFINITY) {
             v = 0.0;
+            dn[i] = -INFINITY;
           } else {
             double s = G[(size_t)p * m + i];
             for (int j = 0; j < k; ++j) s -= L[(size_t)j * m + i] * rowp[j];
             v = s * inv;
-            d[i] -= v * v;
+            dn[i] = di - v * v;
           }
           L[(size_t)k * m + i] = v;
-        }
-        if (p >= i0 && p < i1 && tid == 0) {
-          chosen[p] = 1;
-          d[p] = 0.0;
         }
         r = k + 1;
         resid = 0.0;
@@ -264,6 +268,8 @@ __global__ void __launch_bounds__(kThreads) eig_coop_kernel(const EigJob* __rest
     }
 
     // ---------------- one-sided Jacobi on the r columns (precision T)
+    // W held the odd steps' diagonal: every CTA must be done with its last pivot search
+    if (P > 1 && !bar.sync()) goto timeout;
     for (int j = 0; j < r; ++j)
       for (int i = i0 + tid; i < i1; i += blockDim.x) W[(size_t)j * m + i] = (T)L[(size_t)j * m + i];
     if (!bar.sync()) goto timeout;
@@ -343,7 +349,7 @@ __global__ void __launch_bounds__(kThreads) eig_coop_kernel(const EigJob* __rest
         rank += (li > lj) || (li == lj && i < j);
       }
       J.lambda[rank] = lj > 0.0 ? lj : 0.0;
-      chosen[rank] = j;  // perm: sorted position -> column of V
+      perm[rank] = j;  // sorted position -> column of V
     }
     if (c == 0 && tid == 0) {
       res->sweeps = sweeps;
