@@ -17,9 +17,9 @@
 // FP32 accumulator; the chunks are added exactly into int64 sums (unit 2^(F_c-37)) and
 // rounded once to FP32 at the end.  Columns holding Inf or NaN give NaN columns of Y.
 //
-// Persistent: one CTA per SM walks the items (node, 128-row tile, 64-mode tile), the
-// mode tiles of a row tile adjacent so that the second read of X comes from L2; the
-// stage ring and the two accumulator sets run on across items.  18 warps:
+// Persistent: one CTA per SM walks a contiguous range of the items (node, 128-row
+// tile, 64-mode tile), the mode tiles of a row tile adjacent so that the second read of
+// X comes from L2; the stage ring and the two accumulator sets run on across items.  18 warps:
 //   warp 0        loader: TMA box of X (128 rows x 16 columns FP32) and a bulk copy
 //                 of the 16-column chunk of V digits (8 KB), 6 stages deep
 //   warp 1        TMEM owner and single-thread MMA issuer: per 16 columns four MMAs,
@@ -102,6 +102,14 @@ __device__ __forceinline__ Item item_of(const FxModesJob* jobs, int njobs, int64
   return r;
 }
 
+// FP32 value of an int64 in FP32 arithmetic only (a 64-bit conversion would run on
+// the FP64 unit): |a| split into 32-bit halves, at most two roundings.
+__device__ __forceinline__ float i64_to_f32(long long a) {
+  const unsigned long long u = a < 0 ? 0ull - (unsigned long long)a : (unsigned long long)a;
+  const float f = fmaf(__uint2float_rn((unsigned)(u >> 32)), 4294967296.0f, __uint2float_rn((unsigned)u));
+  return a < 0 ? -f : f;
+}
+
 // fp16 pair (lo, hi) = (byte b of u0 - 128, byte b of u1 - 128): the bytes are placed
 // in the mantissas of 1024 (0x6400), and 1152 is subtracted, exactly.
 __device__ __forceinline__ uint32_t digit_pair(uint32_t u0, uint32_t u1, uint32_t sel) {
@@ -120,6 +128,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ volatile int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const tc::WaitBudget wb = tc::wait_budget(err);
+  // a contiguous range of items per CTA: the mode tiles of a row tile follow each
+  // other, so the second read of the tile's X comes from L2
+  const int64_t per_cta = (total_items + gridDim.x - 1) / gridDim.x;
+  const int64_t it_begin = (int64_t)blockIdx.x * per_cta;
+  const int64_t it_end = it_begin + per_cta < total_items ? it_begin + per_cta : total_items;
   auto st_x = [&](int s) -> uint8_t* { return smem + (size_t)s * kStX; };
   auto op_x = [&](int s) -> uint8_t* { return smem + (size_t)kStages * kStX + (size_t)s * (kOpX + kOpV); };
   auto op_v = [&](int s) -> uint8_t* { return op_x(s) + kOpX; };
@@ -151,7 +164,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       int64_t g = 0;  // stages issued by this CTA
       int cur_jb = -1;
       bool ok = true;
-      for (int64_t it = blockIdx.x; it < total_items && ok; it += gridDim.x) {
+      for (int64_t it = it_begin; it < it_end && ok; ++it) {
         const Item I = item_of(jobs, njobs, it);
         const FxModesJob& J = jobs[I.jb];
         const CUtensorMap* map = maps + I.jb;
@@ -191,7 +204,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int t = 0; t < kDigits; ++t) idn[t] = tc::idesc_f16_f32_major(128, (uint32_t)(kModesT * (kDigits - t)), 0, 0);
       int64_t g = 0, ch = 0;
       bool ok = true;
-      for (int64_t it = blockIdx.x; it < total_items && ok; it += gridDim.x) {
+      for (int64_t it = it_begin; it < it_end && ok; ++it) {
         const Item I = item_of(jobs, njobs, it);
         for (int k = 0; k < I.nst; ++k, ++g) {
           const int s = (int)(g % kStages);
@@ -238,7 +251,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t off = (uint32_t)(r >> 3) * kSbo + (uint32_t)g8 * kLbo + (uint32_t)(r & 7) * 16;
     int64_t g = 0;
     bool ok = true;
-    for (int64_t it = blockIdx.x; it < total_items && ok; it += gridDim.x) {
+    for (int64_t it = it_begin; it < it_end && ok; ++it) {
       const Item I = item_of(jobs, njobs, it);
       const float2* __restrict__ xsc = jobs[I.jb].xscale;
       for (int k = 0; k < I.nst; ++k, ++g) {
@@ -283,7 +296,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t lanes = (uint32_t)(32 * q) << 16;
     int64_t ch = 0;
     bool ok = true;
-    for (int64_t it = blockIdx.x; it < total_items && ok; it += gridDim.x) {
+    for (int64_t it = it_begin; it < it_end && ok; ++it) {
       const Item I = item_of(jobs, njobs, it);
       const FxModesJob& J = jobs[I.jb];
       const int nchunk = (I.nst + kChunkStages - 1) / kChunkStages;
@@ -323,8 +336,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       if (!ok || abort_flag) break;
       // y = acc 2^(F_c - 37) scale_c in FP32 arithmetic (GB300 runs FP64 at 1/64 of the
-      // FP32 rate): one rounding of the int64 sum, an exact power-of-two scaling
-      // (ldexpf rounds only in the subnormal range) and the FP32 scale
+      // FP32 rate): at most two roundings of the int64 sum, an exact power-of-two
+      // scaling (ldexpf rounds only in the subnormal range) and the FP32 scale
       const int64_t row = I.row0 + 32 * q + lane;
 #pragma unroll
       for (int c = 0; c < 32; ++c) {
@@ -337,7 +350,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         else if (F <= kExpZero)
           y = 0.f;
         else
-          y = ldexpf(__ll2float_rn(acc[c]), F - 37) * J.yscale[col];
+          y = ldexpf(i64_to_f32(acc[c]), F - 37) * J.yscale[col];
         J.Y[(size_t)col * J.ldy + row] = y;
       }
     }
