@@ -469,8 +469,10 @@ def run_form(H, precision, bufs, fro2, steps, warmup, stream, dist_ctx, eps_rel=
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
 
-def kernel_traffic(kernel: str):
-    """(bytes per launch, note) of the last capture of `kernel`, or (None, why)."""
+def kernel_traffic(kernel: str, alg_bytes: float = None):
+    """(DRAM bytes, note) of the last capture of `kernel`, or (None, why).  A record
+    with the capture's algorithmic bytes gives the traffic of `alg_bytes` algorithmic
+    bytes at the captured ratio (the traffic grows in proportion to the units)."""
     import hashlib
 
     try:
@@ -486,6 +488,8 @@ def kernel_traffic(kernel: str):
         return None, "kernel source missing"
     if digest != rec["sha256"]:
         return None, f"{rec['source']} changed since the capture"
+    if alg_bytes is not None and rec.get("alg_bytes_per_launch"):
+        return float(rec["bytes_per_launch"]) / float(rec["alg_bytes_per_launch"]) * alg_bytes, rec["note"]
     return float(rec["bytes_per_launch"]), rec["note"]
 
 
@@ -509,11 +513,12 @@ def roofline(res, precision, H, hbm, dom=None):
     if dom in ("gram", "modes"):
         ach = d["bytes"] / (d["ms"] / 1e3) / 1e9
         kern = GRAM_KERNEL.get(precision, dom) if dom == "gram" else dom
-        traffic, note = kernel_traffic(kern)
+        traffic, note = kernel_traffic(kern, d["bytes"])
         out = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": traffic,
                "traffic_note": note, "kernel": kern,
                "definition": f"achieved = b n m algorithmic bytes per node summed over the {dom} step's nodes, over "
-                             "that step's CUDA-event time (launches on the context stream)",
+                             "that step's CUDA-event time (launches on the context stream); traffic = DRAM bytes "
+                             "of the same step at the ratio of an ncu capture",
                "launches_per_step": d["launches"], "bytes_per_step": d["bytes"], "ms_per_step": d["ms"]}
         if precision == H.HAPOD_FP64_OZAKI and dom == "gram":
             out["digit_tflops"] = 28.0 * d["flops"] / (d["ms"] / 1e3) / 1e12
