@@ -541,6 +541,26 @@ def summarise(r, precision, H, eps_rel, total_cols, hbm, peak_src, world, dom=No
     return out
 
 
+# ----------------------------------------------------------------- autotuner
+def run_autotune(H, device):
+    """hapod_autotune for the fixed-point Gram on the node widths of the headline and
+    streamed workloads (untimed): a generated leaf and a generated matrix as wide as
+    their inner nodes, each in its (m, n) bucket."""
+    import torch
+
+    out = {}
+    for wl, m, what in ((C3, C3["cols"], "leaves"), (C3, 384, "inner nodes (257..512 columns)"),
+                        (C5, C5["cols"], "leaves"), (C5, 192, "inner nodes (129..256 columns)")):
+        X = H.colmajor_empty(wl["n"], m, torch.float32, device)
+        H.hapod_synth_snapshots(c3_params(H, wl), wl["n"], 0, m, X)
+        pct, ms = H.hapod_autotune(X, H.HAPOD_MIXED_FX3)
+        out[f"{wl['name']} {what}: n=2^{wl['n'].bit_length() - 1}, m={m}"] = {
+            "split_factor_pct": pct, "ms_at_50_100_200_400_pct": [round(v, 3) for v in ms]}
+        del X
+    torch.cuda.empty_cache()
+    return out
+
+
 # ----------------------------------------------------------------- oracle (CPU baseline)
 ORACLE_ROWS = (4096, 8192)
 
@@ -813,6 +833,7 @@ def main():
                          "'fx3-node' / 'oz-node' the PODs of four headline leaves and of their level-2 parent, "
                          "each step timed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the Gram planners' own split counts")
     ap.add_argument("--sweep", choices=["omega", "trees"],
                     help="print one JSON line per configuration and exit: 'omega' runs the FP64 workload for "
                          "omega in 0.1 .. 0.999 (Sec. 4.3); 'trees' runs 10^4 advection-diffusion columns in "
@@ -875,6 +896,7 @@ def main():
             host = str(ex)[:120]
 
     fro2 = c3_fro2(H, C3, device, stream)
+    autotune = {} if args.no_autotune else run_autotune(H, device)
     sampler = ClockSampler(dist_ctx.local)
     head = run_waves(H, H.HAPOD_MIXED_FX3, C3, fro2, args.steps, args.warmup, stream, dist_ctx)
     clocks = sampler.stop()
@@ -966,6 +988,7 @@ def main():
         "step_ms": hs["step_ms"],
         "forms": forms,
         "workloads": workloads,
+        "autotune": autotune,
     }
     if dist_ctx.rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, total, wall, cores, sample = time_oracle()

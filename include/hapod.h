@@ -129,8 +129,13 @@ typedef struct {
 } hapod_tol;
 
 /* flags: HAPOD_FLAG_PROFILE records CUDA events on the context's stream around
- * every kernel launch so that hapod_profile can report per-step device time. */
+ * every kernel launch so that hapod_profile can report per-step device time.
+ * HAPOD_FLAG_RIGHT_VECTORS keeps every node's right singular vectors (its Gram
+ * eigenvectors V_N, m_a x N_a FP64 on the device, released at hapod_destroy) and
+ * the position of each child's modes in its parent's input, for
+ * hapod_result_right. */
 #define HAPOD_FLAG_PROFILE 1
+#define HAPOD_FLAG_RIGHT_VECTORS 2
 
 typedef struct hapod_ctx hapod_ctx;
 
@@ -183,6 +188,24 @@ hapod_status hapod_push(hapod_ctx* ctx, int32_t leaf, const void* dev_snapshots,
  */
 hapod_status hapod_result(hapod_ctx* ctx, int64_t* k_out, double* sigma_host, void* dev_modes,
                           int64_t ld_modes);
+
+/*
+ * hapod_result_right -- the right factor of the HAPOD's low-rank approximation of
+ * the snapshot map (Sec. 3.3, Remark "Low-rank approximation of the snapshot
+ * mapping"): Lambda~ (|S| x k, orthonormal columns) with
+ *   || S - U diag(sigma) Lambda~^T ||_F^2 <= sum over all nodes a of eps(a)^2,
+ * U, sigma, k those of hapod_result, S the snapshots as columns.  Rows follow the
+ * leaves in increasing node index, each leaf's snapshots in the order pushed.
+ * Built as Lambda~_a = diag(Lambda~_c over the children c) Lambda_a from the root
+ * down (Def. "Additional notation"), Lambda_a the node's right singular vectors (the
+ * identity at pass-through nodes).  W: device, |S| x k FP64, leading dimension
+ * ldw >= |S|; rows of leaves that kept no mode are zero.  Requires a context
+ * created with HAPOD_FLAG_RIGHT_VECTORS whose hapod_result has returned.  Allocates
+ * the intermediate maps (sum over inner nodes of m_a x k doubles) from the library
+ * pool; synchronises the stream.  Errors: INVALID (null W with k > 0, ldw < |S|),
+ * STATE (flag missing, root not finished, context poisoned), CUDA, OOM.
+ */
+hapod_status hapod_result_right(hapod_ctx* ctx, double* W, int64_t ldw);
 
 /* Per-step accounting of a context created with HAPOD_FLAG_PROFILE.  Index:
  * 0 Gram, 1 eigensolve, 2 truncation, 3 eigenvector gather, 4 modes, 5 copies
@@ -336,6 +359,28 @@ typedef struct {
  */
 hapod_status hapod_synth_snapshots(const hapod_synth_params* p, int64_t n, int64_t col0, int64_t ncols,
                                    int32_t dtype, void* X, int64_t ldx, double* t_out, void* stream);
+
+/*
+ * hapod_autotune -- schedule autotuner for the Gram kernels of the FP64, TF32X3,
+ * BF16X3 and FX3 forms.  The Gram is split over row ranges ("splits") whose
+ * number the library chooses so that the tiles x splits work items fill whole waves
+ * of resident CTAs; this call times the Gram of the caller's node X (device, n x m,
+ * ld ldx, element type of the form) with the split count scaled by 50, 100, 200 and
+ * 400 % (one warm-up and three timed calls each, CUDA events on `stream`) and keeps
+ * the fastest factor (a factor other than 100 % must win by 2 %) in a process-wide
+ * table keyed by (form, ceil(log2 m), ceil(log2 n)).  Every later Gram of a batch
+ * whose widest node falls in that bucket uses the factor (hapod_gram, hapod_pod and
+ * contexts alike).  *pct_out (host, may be NULL) receives the factor in percent,
+ * ms_out (host, 4 doubles or NULL) the mean times of the four candidates.
+ * Allocates an m x m FP64 work matrix from the library pool; synchronises the
+ * stream.  Errors: INVALID (other forms, sizes, ld), and those of hapod_gram; on an
+ * error the bucket's entry is removed.
+ */
+hapod_status hapod_autotune(int32_t precision, int64_t n, int64_t m, const void* X, int64_t ldx, int32_t* pct_out,
+                            double* ms_out, void* stream);
+
+/* Forget every autotuned factor (the planners' own rule applies again). */
+void hapod_autotune_clear(void);
 
 /*
  * hapod_gram_noalloc -- the FP64 Gram G = X^T X of hapod_gram (HAPOD_FP64 form)

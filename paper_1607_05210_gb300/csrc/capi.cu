@@ -17,7 +17,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <new>
 #include <string>
 #include <vector>
@@ -582,6 +584,30 @@ bool step_modes_oz(Env& env, std::vector<Work*>& ws) {
   return ok;
 }
 
+// ------------------------------------------------------------------ autotuned splits
+// Split factor of the Gram planners per (form, m bucket, n bucket), set by
+// hapod_autotune; buckets are ceil(log2) of m and n.  100 = the planner's own rule.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, int> g_tune;
+
+int log2_bucket(int64_t v) {
+  int b = 0;
+  while (b < 62 && ((int64_t)1 << b) < v) ++b;
+  return b;
+}
+
+// The factor for a batch: that of its widest node (the tiles of the widest node
+// dominate the batch's items).
+int split_pct_for(int precision, const std::vector<Work*>& ws) {
+  const Work* wide = nullptr;
+  for (const Work* w : ws)
+    if (!wide || w->m > wide->m) wide = w;
+  if (!wide) return 100;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(std::make_tuple(precision, log2_bucket(wide->m), log2_bucket(wide->n)));
+  return it == g_tune.end() ? 100 : it->second;
+}
+
 // K1, mixed fixed-point form: 128 x 64 tiles of exact digit products.
 bool step_gram_fx3(Env& env, std::vector<Work*>& ws) {
   std::vector<GramJob> jobs(ws.size());
@@ -614,7 +640,7 @@ bool step_gram_fx3(Env& env, std::vector<Work*>& ws) {
   }
   std::vector<int4> items, reduce;
   size_t pbytes = 0;
-  plan_gram_fx3(jobs.data(), (int)jobs.size(), kNumSMs, items, reduce, &pbytes);
+  plan_gram_fx3(jobs.data(), (int)jobs.size(), kNumSMs, items, reduce, &pbytes, split_pct_for(HAPOD_MIXED_FX3, ws));
   GramJob* jobs_d = env.upload(jobs, "upload gram jobs");
   int4* items_d = env.upload(items, "upload gram items");
   int4* red_d = env.upload(reduce, "upload gram reduce");
@@ -747,7 +773,7 @@ bool step_gram(Env& env, int precision, std::vector<Work*>& ws) {
   // concurrent CTAs: four 256-thread FP64 CTAs per SM, one tensor-core CTA per SM;
   // items of at least 256 (FP64) / 2048 (tensor-core) rows
   plan_gram(jobs.data(), (int)jobs.size(), tile, fp64 ? 256 : 2048, fp64 ? 4 * kNumSMs : kNumSMs, &items, &reduce,
-            &plan, !fp64);
+            &plan, !fp64, split_pct_for(precision, ws));
   std::vector<int4> it(items, items + plan.num_items), rd(reduce, reduce + plan.num_reduce);
   free(items);
   std::vector<CUtensorMap> maps;
@@ -1114,6 +1140,11 @@ struct NodeRT {
   std::vector<double> sigma;
   void* stash = nullptr;  // own copy of the output while the parent cannot be sized
   int64_t stash_offset = -1;
+  // right singular vectors (HAPOD_FLAG_RIGHT_VECTORS): V_N (m x k FP64, null at
+  // pass-through nodes: the identity) and the first column of this node's modes in
+  // its parent's input
+  double* rv = nullptr;
+  int64_t pcol = -1;
 };
 
 struct hapod_ctx {
@@ -1129,6 +1160,7 @@ struct hapod_ctx {
   int64_t S = 0;
   double eps_star = 0.0;
   int max_pending = 0;
+  bool keep_rv = false;
   int pending = 0;
   int leaves_total = 0;
   int leaves_pushed = 0;
@@ -1165,6 +1197,7 @@ bool ensure_parent_buffer(hapod_ctx* c, int p) {
                                        cudaMemcpyDeviceToDevice, c->env.s),
                        "copy parked modes"))
         return false;
+      C.pcol = P.pfill;
       P.pfill += C.k;
       c->env.release(C.stash);
       C.stash = nullptr;
@@ -1188,6 +1221,7 @@ void* place_output(hapod_ctx* c, int a, const std::vector<int>& batch_children) 
   if (P.children_done + batch_children[A.parent] == (int)P.children.size()) {
     if (!ensure_parent_buffer(c, A.parent)) return nullptr;
     void* dst = (char*)P.pbuf + (size_t)P.pfill * col_bytes;
+    A.pcol = P.pfill;
     P.pfill += A.k;
     return dst;
   }
@@ -1291,6 +1325,17 @@ bool run_batch(hapod_ctx* c, const std::vector<int>& batch) {
     }
   }
   if (ok) ok = run_pod_back(env, c->precision, compute);
+  if (ok && c->keep_rv) {  // keep V_N of every computed node for hapod_result_right
+    for (size_t i = 0; i < batch.size() && ok; ++i) {
+      NodeRT& A = c->nodes[batch[i]];
+      Work& w = works[i];
+      if (!(A.eps > 0.0 && A.m > 0 && A.k > 0) || !w.Vk) continue;
+      A.rv = (double*)env.alloc(sizeof(double) * (size_t)A.m * (size_t)A.k, "alloc right vectors");
+      ok = A.rv && env.cuda(cudaMemcpyAsync(A.rv, w.Vk, sizeof(double) * (size_t)A.m * (size_t)A.k,
+                                            cudaMemcpyDeviceToDevice, env.s),
+                            "keep right vectors");
+    }
+  }
   if (ok && root_work) {
     NodeRT& R = c->nodes[root_node];
     bool deficient = false;
@@ -1471,6 +1516,7 @@ hapod_status hapod_create(const hapod_tree* tree, const hapod_tol* tol, int64_t 
   c->precision = tol->precision;
   c->esize = elem_size(tol->precision);
   c->max_pending = tol->max_pending_leaves;
+  c->keep_rv = (tol->flags & HAPOD_FLAG_RIGHT_VECTORS) != 0;
   if (tol->flags & HAPOD_FLAG_PROFILE) {
     c->prof = new (std::nothrow) Prof();
     c->env.prof = c->prof;
@@ -1600,11 +1646,107 @@ void hapod_destroy(hapod_ctx* c) {
     if (A.in_owned) env.release(A.in_owned);
     if (A.pbuf) env.release(A.pbuf);
     if (A.stash) env.release(A.stash);
+    if (A.rv) env.release(A.rv);
   }
   env.release(c->result);
   cudaStreamSynchronize(env.s);
   delete c->prof;
   delete c;
+}
+
+hapod_status hapod_result_right(hapod_ctx* c, double* W, int64_t ldw) {
+  if (!c) {
+    g_thread_error = "hapod_result_right: null context";
+    return HAPOD_ERR_INVALID;
+  }
+  if (c->poisoned) return HAPOD_ERR_STATE;
+  if (!c->keep_rv) {
+    c->err = "hapod_result_right: context created without HAPOD_FLAG_RIGHT_VECTORS";
+    return HAPOD_ERR_STATE;
+  }
+  NodeRT& R = c->nodes[c->root];
+  if (R.state != 2) {
+    c->err = "hapod_result_right: root not finished (call hapod_result first)";
+    return HAPOD_ERR_STATE;
+  }
+  const int64_t k = std::max<int64_t>(0, R.k);
+  if (k == 0) return HAPOD_OK;
+  if (!W || ldw < c->S) {
+    c->err = "hapod_result_right: null W or ldw < |S|";
+    return HAPOD_ERR_INVALID;
+  }
+  Env& env = c->env;
+  const int N = (int)c->nodes.size();
+  // row offset of every leaf in the enumeration of S (leaves in node order)
+  std::vector<int64_t> leaf_off(N, -1);
+  int64_t off = 0;
+  for (int a = 0; a < N; ++a)
+    if (c->nodes[a].children.empty()) {
+      leaf_off[a] = off;
+      off += c->nodes[a].leaf_cols;
+    }
+  if (!env.cuda(cudaMemset2DAsync(W, (size_t)ldw * sizeof(double), 0, (size_t)c->S * sizeof(double), (size_t)k,
+                                  env.s),
+                "clear W"))
+    return ctx_fail(c);
+  // T_a (m_a x k): rows of Lambda~ below node a, mapped through a's input; the root's
+  // is its own V_N.  Top-down: T_c = V_c T_a[pcol_c : pcol_c + k_c, :].
+  std::vector<double*> T(N, nullptr);
+  std::vector<int64_t> ldT(N, 0);
+  std::vector<int> order{c->root};
+  bool ok = true;
+  auto place = [&](int a, const double* rows, int64_t ld_rows) -> bool {
+    // a's map T_a = V_a rows (V_a = identity at pass-through nodes); leaves go to W
+    NodeRT& A = c->nodes[a];
+    double* dst;
+    int64_t ldd;
+    if (A.children.empty()) {
+      dst = W + leaf_off[a];
+      ldd = ldw;
+    } else {
+      T[a] = (double*)env.alloc(sizeof(double) * (size_t)A.m * (size_t)k, "alloc right-vector map");
+      if (!T[a]) return false;
+      ldT[a] = A.m;
+      dst = T[a];
+      ldd = A.m;
+    }
+    if (A.rv)
+      return env.cuda(launch_gemm_nn_f64(A.m, k, A.k, A.rv, A.m, rows, ld_rows, dst, ldd, env.s), "right-vector product");
+    return env.cuda(cudaMemcpy2DAsync(dst, (size_t)ldd * sizeof(double), rows, (size_t)ld_rows * sizeof(double),
+                                      (size_t)A.m * sizeof(double), (size_t)k, cudaMemcpyDeviceToDevice, env.s),
+                    "copy right-vector rows");
+  };
+  // root: rows = identity (k x k)
+  {
+    std::vector<double> eye((size_t)k * k, 0.0);
+    for (int64_t j = 0; j < k; ++j) eye[(size_t)j * k + j] = 1.0;
+    double* eye_d = env.upload(eye, "upload identity");
+    ok = eye_d && place(c->root, eye_d, k);
+    ok = ok && env.cuda(cudaStreamSynchronize(env.s), "synchronize");
+    env.release(eye_d);
+  }
+  for (size_t h = 0; h < order.size() && ok; ++h) {
+    const int a = order[h];
+    for (int ch : c->nodes[a].children) {
+      NodeRT& C = c->nodes[ch];
+      if (C.k <= 0) continue;  // no modes reached the parent: its rows of W stay zero
+      if (C.pcol < 0) {
+        c->err = "hapod_result_right: a child's position in its parent's input is unknown";
+        ok = false;
+        break;
+      }
+      ok = place(ch, T[a] + C.pcol, ldT[a]);
+      if (!C.children.empty()) order.push_back(ch);
+      if (!ok) break;
+    }
+  }
+  ok = ok && env.cuda(cudaStreamSynchronize(env.s), "synchronize");
+  for (double* t : T) env.release(t);
+  if (!ok) {
+    if (c->err == "no error" || c->err.empty()) c->err = env.err;
+    return env.code != HAPOD_OK ? ctx_fail(c) : HAPOD_ERR_STATE;
+  }
+  return HAPOD_OK;
 }
 
 hapod_status hapod_trim_pool(void* stream) {
@@ -1893,6 +2035,68 @@ hapod_status hapod_pod(int32_t precision, int64_t n, int64_t m, const void* X, i
   *N_host = w.res.k;
   if (tail_host) *tail_host = w.res.tail;
   return (hapod_status)(w.res.status >= HAPOD_WARN_NOCONVERGE ? w.res.status : HAPOD_OK);
+}
+
+hapod_status hapod_autotune(int32_t precision, int64_t n, int64_t m, const void* X, int64_t ldx, int32_t* pct_out,
+                            double* ms_out, void* stream) {
+  if (!(precision == HAPOD_FP64 || precision == HAPOD_MIXED_TF32X3 || precision == HAPOD_MIXED_BF16X3 ||
+        precision == HAPOD_MIXED_FX3) ||
+      n < 1 || m < 1 || m > kEigMaxM || !X || ldx < n) {
+    g_thread_error = "hapod_autotune: invalid argument (forms FP64, TF32X3, BF16X3, FX3; n, m >= 1, ld >= n)";
+    return HAPOD_ERR_INVALID;
+  }
+  static const int kCand[4] = {50, 100, 200, 400};
+  const auto key = std::make_tuple((int)precision, log2_bucket(m), log2_bucket(n));
+  Env env;
+  if (!init_env(env, stream)) return step_error(env);
+  double* G = (double*)env.alloc(sizeof(double) * (size_t)m * (size_t)m, "alloc Gram");
+  if (!G) return step_error(env);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  bool ok = env.cuda(cudaEventCreate(&e0), "event") && env.cuda(cudaEventCreate(&e1), "event");
+  double best = 1e300;
+  int best_pct = 100;
+  hapod_status st = HAPOD_OK;
+  for (int c = 0; c < 4 && ok; ++c) {
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tune[key] = kCand[c];
+    }
+    st = hapod_gram(precision, n, m, X, ldx, G, stream);  // warm-up (and correctness of the plan)
+    float tot = 0.f;
+    for (int r = 0; r < 3 && st == HAPOD_OK && ok; ++r) {
+      ok = env.cuda(cudaEventRecord(e0, env.s), "event record");
+      st = hapod_gram(precision, n, m, X, ldx, G, stream);
+      float ms = 0.f;
+      ok = ok && env.cuda(cudaEventRecord(e1, env.s), "event record") &&
+           env.cuda(cudaEventSynchronize(e1), "event sync") && env.cuda(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
+      tot += ms;
+    }
+    if (st != HAPOD_OK) break;
+    const double ms = tot / 3.0;
+    if (ms_out) ms_out[c] = ms;
+    if (ms < best * 0.98) {  // a new factor has to win by 2 %
+      best = ms;
+      best_pct = kCand[c];
+    }
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (ok && st == HAPOD_OK) g_tune[key] = best_pct;
+    else g_tune.erase(key);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  env.release(G);
+  cudaStreamSynchronize(env.s);
+  if (st != HAPOD_OK) return st;
+  if (!ok) return step_error(env);
+  if (pct_out) *pct_out = best_pct;
+  return HAPOD_OK;
+}
+
+void hapod_autotune_clear(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune.clear();
 }
 
 }  // extern "C"

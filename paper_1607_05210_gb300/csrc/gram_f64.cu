@@ -15,7 +15,7 @@
 namespace hapod {
 
 void plan_gram(GramJob* jobs, int njobs, int tile, int min_rows_per_split, int target_items, int4** items_out,
-               int4** reduce_out, GramPlan* plan, bool split_major) {
+               int4** reduce_out, GramPlan* plan, bool split_major, int split_pct) {
   int64_t total_tiles = 0;
   for (int j = 0; j < njobs; ++j) {
     const int t = (jobs[j].m + tile - 1) / tile;
@@ -40,6 +40,8 @@ void plan_gram(GramJob* jobs, int njobs, int tile, int min_rows_per_split, int t
       splits = s;
     }
   }
+  // an autotuned factor on the split count (hapod_autotune), 100 = the rule above
+  if (split_pct != 100) splits = std::max<int64_t>(1, splits * split_pct / 100);
   std::vector<int4> items, reduce;
   int64_t item = 0;
   for (int j = 0; j < njobs; ++j) {

@@ -569,7 +569,7 @@ int gram_fx3_a_cols() { return kACols; }
 int gram_fx3_b_cols() { return kBCols; }
 
 void plan_gram_fx3(GramJob* jobs, int njobs, int target_items, std::vector<int4>& items, std::vector<int4>& reduce,
-                   size_t* partial_bytes) {
+                   size_t* partial_bytes, int split_pct) {
   // tiles (I, J), J >= 2 I, of every job; one split count for the batch chosen as in
   // plan_gram: the fewest waves of `target_items` CTAs per unit of work
   int64_t total_tiles = 0, max_n = 1;
@@ -593,6 +593,8 @@ void plan_gram_fx3(GramJob* jobs, int njobs, int target_items, std::vector<int4>
       splits = s;
     }
   }
+  // an autotuned factor on the split count (hapod_autotune), 100 = the rule above
+  if (split_pct != 100) splits = std::max<int64_t>(1, splits * split_pct / 100);
   int64_t slot = 0;
   items.clear();
   reduce.clear();

@@ -59,8 +59,9 @@ struct GramPlan {
 // (job, ti, tj, split) then lives in slot job.item_base + tile_index * splits + split,
 // tile_index the row-major index of (ti, tj) in the upper triangle); otherwise the
 // slot is the item's own index.
+// split_pct scales the split count (autotuned, 100 = the rule above).
 void plan_gram(GramJob* jobs, int njobs, int tile, int min_rows_per_split, int target_items,
-               int4** items, int4** reduce, GramPlan* plan, bool split_major = false);
+               int4** items, int4** reduce, GramPlan* plan, bool split_major = false, int split_pct = 100);
 
 // Sum split partials of each reduce-list tile in split order; both triangles.
 cudaError_t launch_gram_reduce(int tile, const GramJob* jobs_dev, const int4* reduce_dev, int num_reduce,
@@ -85,8 +86,9 @@ int gram_bf3_rows_per_stage();
 // gram_fx3_rows_per_stage() rows x gram_fx3_a_cols() / gram_fx3_b_cols() columns
 // (128-byte swizzle).  plan_gram_fx3 fills the jobs' tiles, splits, rows_per_split,
 // item_base and the item / reduce lists (int4 job, I, J, split).
+// split_pct scales the planner's split count (autotuned, 100 = the planner's rule).
 void plan_gram_fx3(GramJob* jobs, int njobs, int target_items, std::vector<int4>& items, std::vector<int4>& reduce,
-                   size_t* partial_bytes);
+                   size_t* partial_bytes, int split_pct = 100);
 cudaError_t launch_gram_fx3(const GramJob* jobs_dev, const CUtensorMap* maps_dev, const int4* items_dev,
                             int num_items, const int4* reduce_dev, int num_reduce, double* partials, int* err_flag,
                             cudaStream_t s);
@@ -311,6 +313,10 @@ constexpr int kEigF32 = 1;
 cudaError_t launch_eig(int mode, EigJob* jobs_host, EigJob* jobs_dev, int njobs, int max_m, int max_sweeps,
                        EigSync* sync_dev, const int* err, cudaStream_t s);
 constexpr int kEigMaxM = 13000;  // dynamic shared memory bound of the eigensolver
+
+// C (M x N, ldc) = A (M x K, lda) B (K x N, ldb), column-major FP64 (right vectors).
+cudaError_t launch_gemm_nn_f64(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, const double* B,
+                               int64_t ldb, double* C, int64_t ldc, cudaStream_t s);
 
 // ---------------------------------------------------------------- truncation (K3)
 struct TruncJob {

@@ -57,6 +57,7 @@ class hapod_tol(ctypes.Structure):
 
 
 HAPOD_FLAG_PROFILE = 1
+HAPOD_FLAG_RIGHT_VECTORS = 2
 PROFILE_STEPS = ("gram", "eig", "truncate", "gather", "modes", "copy", "digits")
 
 
@@ -108,6 +109,9 @@ def _load() -> ctypes.CDLL:
         "hapod_modes": ([i32, i64, i64, vp, i64, vp, i64, i64, vp, vp, i64, vp], i32),
         "hapod_pod": ([i32, i64, i64, vp, i64, d, pi64, vp, vp, i64, pd, vp], i32),
         "hapod_gram_noalloc": ([i64, i64, vp, i64, vp, vp], i32),
+        "hapod_result_right": ([vp, vp, i64], i32),
+        "hapod_autotune": ([i32, i64, i64, vp, i64, ctypes.POINTER(i32), pd, vp], i32),
+        "hapod_autotune_clear": ([], None),
         "hapod_synth_snapshots": ([ctypes.POINTER(hapod_synth_params), i64, i64, i64, i32, vp, i64, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
@@ -121,7 +125,7 @@ _lib = _load()
 EXPORTED = ("hapod_create", "hapod_push", "hapod_result", "hapod_node_stats", "hapod_profile", "hapod_last_error",
             "hapod_destroy", "hapod_trim_pool",
             "hapod_gram", "hapod_eig", "hapod_truncate", "hapod_modes", "hapod_pod", "hapod_gram_noalloc",
-            "hapod_synth_snapshots")
+            "hapod_synth_snapshots", "hapod_result_right", "hapod_autotune", "hapod_autotune_clear")
 
 
 def _stream(stream: Optional[torch.cuda.Stream]) -> int:
@@ -159,6 +163,11 @@ class Context:
         N = len(parent)
         self._parent = (ctypes.c_int32 * N)(*parent)
         self._cols = (ctypes.c_int64 * N)(*[int(c) for c in leaf_cols])
+        has_child = [False] * N
+        for p_ in parent:
+            if p_ >= 0:
+                has_child[p_] = True
+        self._is_leaf = [not h for h in has_child]
         self._ovr = (ctypes.c_double * N)(*eps_override) if eps_override is not None else None
         tree = hapod_tree(N, self._parent, self._cols)
         tol = hapod_tol(float(eps), float(omega),
@@ -211,6 +220,17 @@ def hapod_result(ctx: Context, device=None):
     st = _check(_lib.hapod_result(ctx.ctx, ctypes.byref(k), sp, ctypes.c_void_p(modes.data_ptr() if kk else 0),
                                   ctx.n), ctx.ctx)
     return sigma, modes, st
+
+
+def hapod_result_right(ctx: Context, k: int, device=None) -> torch.Tensor:
+    """Right factor Lambda~ (|S| x k FP64, column-major CUDA tensor) of the low-rank
+    approximation S ~ U diag(sigma) Lambda~^T (context created with
+    HAPOD_FLAG_RIGHT_VECTORS, after hapod_result)."""
+    S = int(sum(ctx._cols[a] for a in range(len(ctx._cols)) if ctx._is_leaf[a]))
+    device = device or torch.device("cuda", torch.cuda.current_device())
+    W = colmajor_empty(S, max(k, 0), torch.float64, device)
+    _check(_lib.hapod_result_right(ctx.ctx, ctypes.c_void_p(W.data_ptr() if k > 0 else 0), S), ctx.ctx)
+    return W
 
 
 def hapod_node_stats(ctx: Context, node: int) -> dict:
@@ -340,6 +360,22 @@ def hapod_synth_snapshots(params: hapod_synth_params, n: int, col0: int, ncols: 
                                       ctypes.c_void_p(t_out.data_ptr() if t_out is not None else 0),
                                       ctypes.c_void_p(_stream(stream))))
     return out
+
+
+# ------------------------------------------------------------------ autotuner
+def hapod_autotune(X: torch.Tensor, precision: int, stream=None):
+    """Time the Gram of the n x m column-major node X at split factors 50/100/200/400 %
+    and keep the fastest for its (form, m, n) bucket; returns (percent, [ms x 4])."""
+    n, m, ld = _colmajor(X)
+    pct = ctypes.c_int32(0)
+    ms = (ctypes.c_double * 4)()
+    _check(_lib.hapod_autotune(int(precision), n, m, ctypes.c_void_p(X.data_ptr()), ld, ctypes.byref(pct), ms,
+                               ctypes.c_void_p(_stream(stream))))
+    return pct.value, list(ms)
+
+
+def hapod_autotune_clear() -> None:
+    _lib.hapod_autotune_clear()
 
 
 def eps_star_to_global(eps_star: float, num_snapshots: int) -> float:
