@@ -1,7 +1,7 @@
 """The benchmark workload at full size, in the launch configuration bench.py times.
 
 n = 2^20 rows, 64 leaves x 256 advection-diffusion snapshots (137 GB FP64 on the
-device), balanced binary tree L_T = 7, eps = 1e-5 ||X||_F, omega = 0.5, the
+device), balanced binary tree L_T = 7 (and the two-level star), eps = 1e-5 ||X||_F, omega = 0.5, the
 digit-slice FP64 form, every leaf pushed and then processed in one batch, as in
 the bench's timed step.
 
@@ -74,12 +74,15 @@ def _closed_form_check(parent, leaves, cols, C, n, eps, omega, s, stats):
     return ref, children, root
 
 
-def test_bench_workload_against_closed_form_oracle(workload):
+@pytest.mark.parametrize("kind", ["binary", "star"])
+def test_bench_workload_against_closed_form_oracle(workload, kind):
+    """The FP64 workload on both of its trees: the balanced binary tree (L_T = 7) and
+    the two-level star (L_T = 2), whose root sees every leaf's modes at once."""
     from paper_1607_05210_gb300 import hapod as H
 
     bufs, fro2 = workload
     device = bufs[0].device
-    parent, leaves, cols = bench.tree()
+    parent, leaves, cols = bench.tree(kind)
     n, S = bench.N_ROWS, bench.LEAVES * bench.COLS
     eps = bench.EPS_REL * math.sqrt(fro2)
     s, U, stats = _run(H, parent, leaves, cols, bufs, n, eps, bench.OMEGA)
