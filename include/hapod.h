@@ -38,14 +38,15 @@
  *     from the six piece products whose levels add to at most 2 (dropped terms below
  *     2^-26 |x_i x_j|), FP32 tensor-core accumulation over 64-row segments summed in
  *     compensated FP32 pairs and FP64; eigensolve with FP64 rotations.
- *     Mixed fixed-point form (HAPOD_MIXED_FX3): snapshots are IEEE float; in every
- *     64-row block each column is scaled by its block maximum's power of two and
- *     rounded to a 24-bit integer, written as three balanced 8-bit digits; the six
- *     digit pairs of levels 2..4 are summed exactly on the fp16 tensor cores and in
- *     int64, so the Gram carries only the representation error (at most 2^-24 of the
- *     block maximum per value, 2^-22 per row product, unbiased) and one FP64 rounding
- *     per entry and row split; no FP32 overflow.  X V, eigensolve and root as the
- *     split-BF16 form.
+ *     Mixed fixed-point form (HAPOD_MIXED_FX3): snapshots are IEEE float; each
+ *     column is scaled by the power of two of its largest |x| (one read of X before
+ *     the Gram) and every value rounded to a 32-bit integer written as four balanced
+ *     8-bit digits; the thirteen digit pairs of levels 2..6 are summed exactly on the
+ *     fp16 tensor cores over 128-row groups and in int64, so the Gram carries only the
+ *     representation error (at most 2^-32 of the column maximum per value, unbiased)
+ *     and one FP64 rounding per entry and row split.  X V from the same column
+ *     exponents and four digits of V, exact level sums, int64.  Eigensolve with FP64
+ *     rotations, FP64 tails, CholQR2 at the root.
  *     Eigensolve, tail sums and truncation use FP64 arithmetic on FP64 data except
  *     where stated.
  */
@@ -83,9 +84,9 @@ typedef enum {
                                entry, FP32 accumulation over 64-row segments, compensated
                                sums, FP64 over row splits); Jacobi eigensolve with FP64
                                rotations, FP64 truncation, CholQR2 at the root */
-  HAPOD_MIXED_FX3 = 4       /* float snapshots; Gram on the fp16 tensor cores from three
-                               balanced 8-bit digits per value, fixed-point per column and
-                               64-row block (six digit pairs, integer-exact sums, int64
+  HAPOD_MIXED_FX3 = 4       /* float snapshots; Gram on the fp16 tensor cores from four
+                               balanced 8-bit digits per value, fixed-point per column
+                               (thirteen digit pairs, integer-exact sums, int64
                                accumulation, one FP64 rounding per entry and row split);
                                eigensolve, truncation and root as HAPOD_MIXED_BF16X3 */
 } hapod_precision;
@@ -211,8 +212,8 @@ hapod_status hapod_result_right(hapod_ctx* ctx, double* W, int64_t ldw);
  * 0 Gram, 1 eigensolve, 2 truncation, 3 eigenvector gather, 4 modes, 5 copies
  * (pass-through inputs and parked child outputs), 6 digit conversion of the
  * digit-slice form (column exponents and digit planes of the Gram inputs; its Gram
- * step 0 then counts the tensor-core Gram kernels and the split-sum reduce), 7
- * unused.  ms = summed device time between CUDA events recorded on the context
+ * step 0 then counts the tensor-core Gram kernels and the split-sum reduce) and the
+ * column-exponent pass of the fixed-point form (4 n m bytes), 7 unused.  ms = summed device time between CUDA events recorded on the context
  * stream around the step's launches; launches = kernel launches; bytes/flops =
  * algorithmic volume of the step as defined by the method (Gram: b n m bytes and
  * n m (m + 1) flops per node; modes: b n (m + k) bytes and 2 n m k flops; b =

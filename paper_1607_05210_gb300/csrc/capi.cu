@@ -614,14 +614,18 @@ bool step_gram_fx3(Env& env, std::vector<Work*>& ws) {
   std::vector<CUtensorMap> maps(2 * ws.size());
   double bytes = 0, flops = 0;
   for (size_t i = 0; i < ws.size(); ++i) {
-    // column exponents of the node for its X V (filled by the Gram kernel)
+    // column exponents of this X, for its Gram and the X V that follows (one read of
+    // X); always recomputed: a work item may be given another X (CholQR2 passes)
     if (!ws[i]->exps) {
       ws[i]->exps = (int32_t*)env.alloc(sizeof(int32_t) * std::max<int64_t>(1, ws[i]->m), "alloc exponents");
-      if (!ws[i]->exps ||
-          !env.cuda(cudaMemsetAsync(ws[i]->exps, 0x80, sizeof(int32_t) * std::max<int64_t>(1, ws[i]->m), env.s),
-                    "memset exponents"))
-        return false;
+      if (!ws[i]->exps) return false;
     }
+    cudaEvent_t tc0 = env.tic();
+    const bool okx = env.cuda(launch_fx_colexp(static_cast<const float*>(ws[i]->X), ws[i]->ldx, ws[i]->n, ws[i]->m,
+                                               ws[i]->exps, env.s),
+                              "column exponent launch");
+    env.toc(tc0, 6, 1, 4.0 * ws[i]->n * ws[i]->m, 0.0);
+    if (!okx) return false;
     GramJob& J = jobs[i];
     memset(&J, 0, sizeof(J));
     J.col_exp = ws[i]->exps;

@@ -8,29 +8,28 @@
 // every step, unevenly across entries, which leaves noise of that very size on the
 // small eigenvalues.  This form therefore adds nothing inexactly until the very end:
 //
-// Digits: the rows are taken in blocks of 64.  In block b every column j gets the
-// exponent E = E_j^b with max_r |x_rj| < 2^E (computed in the kernel from the block
-// in shared memory), and every value becomes the 32-bit integer A = rint(x 2^(31-E))
-// written as four balanced base-256 digits A = d1 2^24 + d2 2^16 + d3 2^8 + d4,
-// |d_t| <= 128 (round to nearest at each step, so the pieces are unbiased).  The
-// representation error is at most 2^(E-32): every FP32 value within 2^8 of its
-// block maximum is represented exactly.
+// Digits: every column j has the exponent E_j with max_r |x_rj| < 2^E_j over the
+// whole node (a one-read pass before the launch, shared with the X V of the node),
+// and every value becomes the 32-bit integer A = rint(x 2^(31-E)) written as four
+// balanced base-256 digits A = d1 2^24 + d2 2^16 + d3 2^8 + d4, |d_t| <= 128 (round
+// to nearest at each step, so the pieces are unbiased).  The representation error is
+// at most 2^(E-32): every FP32 value within 2^8 of its column maximum is exact.
 // Products: x_i x_j = 2^(E_i+E_j-62) sum_{t,u} d_t d_u 2^(8(8-t-u)); the levels
 // s = t + u = 2..6 are kept (thirteen digit pairs; the dropped ones weigh less than
-// 2^(E_i+E_j-38.9) per row).  Levels 2..5 are summed over the block on the tensor
-// cores as integers, L_s <= 64 * 4 * 2^14 = 2^22, which the FP32 accumulator holds
-// exactly; the three level-6 pairs enter the level-5 accumulator through B digit
-// planes scaled by 2^-8 (exact in fp16), so L'_5 = L_5 + 2^-8 L_6 carries a fraction
-// whose FP32 rounding is below 2^-24 |L'_5| per step.  (Dropping level 6 instead
-// leaves a random error of 2^(E_i+E_j-33.6) per row, which at n ~ 2^10..2^18 rows
-// reaches the tail sums of eps = 1e-5 rel.)
-// Flush: after each block, v = L_2 2^28 + L_3 2^20 + L_4 2^12 + rint(16 L'_5) (exact,
-// |v| < 2^48.1) is added into an int64 fixed-point sum per entry whose unit is
-// 2^(R_i+R_j-42), R the running maximum of the block exponents (rounding shift; the
-// sum is shifted down when R grows); a row split holds at most 2^20 rows, so the sum
-// stays below 2^62.1.  The item writes ldexp(sum, R_i + R_j - 42) in FP64 -- one
-// rounding -- and row splits are summed in FP64 in a fixed order.  Columns holding
-// Inf or NaN give NaN rows and columns of G.
+// 2^(E_i+E_j-38.9) per row).  Levels 2..5 are summed on the tensor cores as integers
+// over a group of 128 rows, L_s <= 128 * 4 * 2^14 = 2^23, which the FP32 accumulator
+// holds exactly; the three level-6 pairs enter the level-5 accumulator through B
+// digit planes scaled by 2^-8 (exact in fp16), so L'_5 = L_5 + 2^-8 L_6 carries a
+// fraction whose FP32 rounding is below 2^-24 |L'_5| per step.  (Dropping level 6
+// instead leaves a random error of 2^(E_i+E_j-33.6) per row, which at n ~ 2^10..2^18
+// rows reaches the tail sums of eps = 1e-5 rel.)
+// Flush: after each group, v = L_2 2^28 + L_3 2^20 + L_4 2^12 + rint(16 L'_5) (exact,
+// |v| < 2^49.1: level 2 is a single pair) is added into an int64 sum per entry whose
+// unit is 2^(E_i+E_j-42) -- every group has the same scales, so the sums are plain
+// additions; a row split holds at most 2^20 rows, so the sum stays below 2^62.1.  The
+// item writes ldexp(sum, E_i + E_j - 42) in FP64 -- one rounding -- and row splits
+// are summed in FP64 in a fixed order.  Columns holding Inf or NaN give NaN rows and
+// columns of G.
 //
 // Work item = one 128 x 64 tile (A columns 128 I.., B columns 64 J.., J >= 2 I) of
 // one node's G over one row split; items are ordered by split first.  One CTA per
@@ -43,9 +42,9 @@
 //                 N = 64 (5 - t)) into the adjacent level accumulators L_{t+1} .. L_5,
 //                 and three (N = 64) of the A digits 2, 3, 4 against the scaled B
 //                 digits 4, 3, 2 into L_5; two accumulator sets (2 x 256 TMEM columns)
-//                 alternate between blocks
-//   warps 2..9    converters: block column maxima, exponents, digits (K-major 8 x 8
-//                 core matrices, no swizzle), 2 stages deep
+//                 alternate between 128-row groups
+//   warps 2..9    converters: digits (K-major 8 x 8 core matrices, no swizzle) with
+//                 the column scales held in shared memory, 2 stages deep
 //   warps 10..17  flushers: int64 sums of 32 entries per thread
 // Every mbarrier wait is bounded: a timeout raises the error flag, the CTA drains
 // its copies and MMAs and frees TMEM.
@@ -61,8 +60,7 @@ namespace hapod {
 namespace {
 
 constexpr int kRows = 32;                              // rows per stage (K of two MMAs)
-constexpr int kBlockStagesDiag = 2;                    // stages per exponent block, B inside A (64 rows)
-constexpr int kBlockStagesOff = 2;                     // stages per exponent block, separate B (64 rows)
+constexpr int kGroupStages = 4;                        // stages per accumulator flush (128 rows)
 constexpr int kACols = 128;
 constexpr int kBCols = 64;
 constexpr int kStA = kRows * kACols * 4;               // FP32 staging of the A panel, 16 KB
@@ -76,7 +74,6 @@ constexpr int kDigits = 4;
 constexpr int kScaled = 3;                             // B digits 2..4 scaled by 2^-8 (level 6 into L_5)
 constexpr int kOpSlot = kDigits * (kPlaneA + kPlaneB) + kScaled * kPlaneB;  // 60 KB
 constexpr int kOpSlots = 2;
-constexpr int kExpSlots = 2;
 constexpr int kSmemBytes = kStRegion + kOpSlots * kOpSlot + 1024;
 constexpr int kThreads = 576;
 constexpr int kConvThreads = 256;
@@ -93,10 +90,8 @@ constexpr int64_t kMaxSplitRows = (int64_t)1 << 20;   // keeps the int64 sums be
 struct Bars {
   uint64_t full[kStSlotsMax];     // TMA -> converters
   uint64_t st_free[kStSlotsMax];  // converters -> TMA
-  uint64_t op_full[kOpSlots];  // converters -> issuer
-  uint64_t op_free[kOpSlots];  // issuer (MMA completion) -> converters
-  uint64_t exp_full[kExpSlots];  // converters -> flushers: block exponents written
-  uint64_t exp_free[kExpSlots];  // flushers -> converters
+  uint64_t op_full[kOpSlots];     // converters -> issuer
+  uint64_t op_free[kOpSlots];     // issuer (MMA completion) -> converters
   uint64_t acc_full[2];
   uint64_t acc_empty[2];
   uint64_t mma_done;
@@ -104,21 +99,11 @@ struct Bars {
 
 struct Shared {
   Bars bars;
-  int exps[kExpSlots][kACols + kBCols];  // block exponents: A columns, then B columns
-  int bad[kACols + kBCols];              // sticky: column held Inf or NaN
-  int colmax[kACols];                    // running maximum of the A columns' block exponents
+  float2 sc[kACols + kBCols];  // scale factors s1 s2 = 2^(31 - E): A columns, then B columns
+  int ex[kACols + kBCols];     // column exponents E (kExpZero zero column, kExpBad Inf / NaN)
   uint32_t tmem_base;
   int abort_flag;
 };
-
-// Exponent E with max |x| < 2^E from the bit pattern of the block maximum.
-__device__ __forceinline__ int exp_of_max(float mx) {
-  if (!(mx <= 3.402823466e38f)) return kExpBad;  // Inf or NaN
-  if (mx == 0.f) return kExpZero;
-  int e;
-  frexpf(mx, &e);  // mx = f 2^e, f in [0.5, 1): mx < 2^e
-  return e;
-}
 
 // Four balanced base-256 digits of rint(x 2^(31 - E)) (as floats holding integers in
 // [-128, 128]): each digit is a round to nearest by adding and subtracting 1.5 2^23
@@ -200,12 +185,6 @@ __device__ __forceinline__ void convert_unit(const uint8_t* __restrict__ st, int
   }
 }
 
-// Round-to-nearest arithmetic right shift of a signed 64-bit value, branch-free.
-__device__ __forceinline__ long long rshift_rn(long long v, int sh) {
-  sh = min(max(sh, 0), 62);  // |v| < 2^61: a shift of 62 leaves 0
-  return (v + ((1LL << sh) >> 1)) >> sh;
-}
-
 __global__ void __launch_bounds__(kThreads, 1)
     gram_fx3_kernel(const GramJob* __restrict__ jobs, const CUtensorMap* __restrict__ maps,
                     const int4* __restrict__ items, double* __restrict__ partials, int* err) {
@@ -225,12 +204,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int64_t r0 = (int64_t)sp * J.rows_per_split;
   const int64_t r1 = min(J.n, r0 + J.rows_per_split);
   const int nst = r1 > r0 ? (int)((r1 - r0 + kRows - 1) / kRows) : 0;
+  const int ngroups = (nst + kGroupStages - 1) / kGroupStages;
   // a tile whose B columns lie inside its A panel stages only the A panel (16 KB per
   // stage, 6 slots); otherwise A and B (24 KB per stage, 4 slots).
-  const int kBlockStages = b_in_a ? kBlockStagesDiag : kBlockStagesOff;
   const int kStSlots = b_in_a ? kStRegion / kStA : kStRegion / kStSlot;
   const int st_bytes = b_in_a ? kStA : kStSlot;
-  const int nblk = (nst + kBlockStages - 1) / kBlockStages;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const tc::WaitBudget wb = tc::wait_budget(err);
   auto st_a = [&](int s) -> uint8_t* { return smem + (size_t)s * st_bytes; };
@@ -248,10 +226,6 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc::mbar_init(&bars.op_full[t], 8);
       tc::mbar_init(&bars.op_free[t], 1);
     }
-    for (int e = 0; e < kExpSlots; ++e) {
-      tc::mbar_init(&bars.exp_full[e], 8);
-      tc::mbar_init(&bars.exp_free[e], 8);
-    }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&bars.acc_full[b], 1);
       tc::mbar_init(&bars.acc_empty[b], 8);
@@ -260,9 +234,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     sh.abort_flag = 0;
     tc::mbar_fence_init();
   }
+  // column exponents of the node (computed before the launch) and the scale factors
   for (int i = tid; i < kACols + kBCols; i += blockDim.x) {
-    sh.bad[i] = 0;
-    if (i < kACols) sh.colmax[i] = kExpZero;
+    const int col = i < kACols ? a0 + i : b0 + (i - kACols);
+    const int E = col < J.m ? J.col_exp[col] : kExpZero;
+    float s1, s2;
+    scales(E, s1, s2);
+    sh.ex[i] = E;
+    sh.sc[i] = make_float2(s1, s2);
   }
   if (warp == 1) tc::tmem_alloc(&sh.tmem_base, kTmemCols);
   tc::tc_fence_before();
@@ -302,12 +281,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int t = 0; t < kDigits; ++t) idn[t] = tc::idesc_f16_f32_major(128, (uint32_t)(kBCols * (kDigits - t)), 0, 0);
       for (int k = 0; k < nst; ++k) {
         const int t = k % kOpSlots;
-        const int blk = k / kBlockStages;
-        const bool blk_first = (k % kBlockStages) == 0;
-        const bool blk_last = (k % kBlockStages) == kBlockStages - 1 || k == nst - 1;
-        const int set = blk & 1;
-        if (blk_first && blk >= 2 &&
-            !tc::mbar_wait(&bars.acc_empty[set], ((blk >> 1) - 1) & 1, abort_flag, err, wb))
+        const int grp = k / kGroupStages;
+        const bool grp_first = (k % kGroupStages) == 0;
+        const bool grp_last = (k % kGroupStages) == kGroupStages - 1 || k == nst - 1;
+        const int set = grp & 1;
+        if (grp_first && grp >= 2 &&
+            !tc::mbar_wait(&bars.acc_empty[set], ((grp >> 1) - 1) & 1, abort_flag, err, wb))
           break;
         if (!tc::mbar_wait(&bars.op_full[t], (k / kOpSlots) & 1, abort_flag, err, wb)) break;
         tc::tc_fence_after();
@@ -321,7 +300,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int tt = 0; tt < kDigits; ++tt)
             tc::umma_f16(d + (uint32_t)(kBCols * tt), tc::ns_desc(pa + (uint32_t)tt * kPlaneA + ko, kLbo, kSbo),
-                         tc::ns_desc(pb + ko, kLbo, kSbo), idn[tt], (blk_first && kk == 0 && tt == 0) ? 0u : 1u);
+                         tc::ns_desc(pb + ko, kLbo, kSbo), idn[tt], (grp_first && kk == 0 && tt == 0) ? 0u : 1u);
           // level 6 into L_5: A digit 2, 3, 4 against the scaled B digit 4, 3, 2
 #pragma unroll
           for (int tt = 1; tt < kDigits; ++tt)
@@ -331,7 +310,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                          idn[kDigits - 1], 1u);
         }
         tc::umma_commit(&bars.op_free[t]);
-        if (blk_last) tc::umma_commit(&bars.acc_full[set]);
+        if (grp_last) tc::umma_commit(&bars.acc_full[set]);
       }
       tc::umma_commit(&bars.mma_done);
       const long long t0 = clock64();
@@ -340,84 +319,35 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp < kFirstFlushWarp) {
     // ------------------------------------------------------------ converters
-    const int cw = warp - 2;  // 0..7
     const int ct = tid - 64;  // 0..255
-    const int ncols = kACols + (b_in_a ? 0 : kBCols);
     bool ok = true;
-    for (int blk = 0; blk < nblk && ok; ++blk) {
-      const int k0 = blk * kBlockStages;
-      const int k1 = min(nst, k0 + kBlockStages);
-      for (int k = k0; k < k1 && ok; ++k)
-        ok = tc::mbar_wait_warp(&bars.full[k % kStSlots], (k / kStSlots) & 1, abort_flag, err, wb);
-      const int es = blk % kExpSlots;
-      if (ok && blk >= kExpSlots)
-        ok = tc::mbar_wait_warp(&bars.exp_free[es], ((blk / kExpSlots) - 1) & 1, abort_flag, err, wb);
+    for (int k = 0; k < nst && ok; ++k) {
+      const int s = k % kStSlots, t = k % kOpSlots;
+      ok = tc::mbar_wait_warp(&bars.full[s], (k / kStSlots) & 1, abort_flag, err, wb);
+      if (ok && k >= kOpSlots) ok = tc::mbar_wait_warp(&bars.op_free[t], ((k / kOpSlots) - 1) & 1, abort_flag, err, wb);
       if (!ok) break;
-      // block maxima: four columns per warp instruction, eight lanes per column
-      // (lane l reads physical chunk l % 8 of column 4 w + l / 8: 512 contiguous bytes)
-      for (int c0 = 4 * cw; c0 < ncols; c0 += 32) {
-        const int c = c0 + (lane >> 3);
-        float mx = 0.f;
-        bool badv = false;
-        for (int k = k0; k < k1; ++k) {
-          const int s = k % kStSlots;
-          const uint8_t* base = c < kACols ? st_a(s) + c * 128 : st_b(s) + (c - kACols) * 128;
-          const float4 v = *reinterpret_cast<const float4*>(base + ((lane & 7) << 4));
-          const float m4 = fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w)));
-          badv |= !(fabsf(v.x) <= 3.402823466e38f && fabsf(v.y) <= 3.402823466e38f &&
-                    fabsf(v.z) <= 3.402823466e38f && fabsf(v.w) <= 3.402823466e38f);  // Inf, or NaN (compares false)
-          mx = fmaxf(mx, m4);
-        }
+      // A panel: 128 columns x 4 octets = 512 units, two per thread
 #pragma unroll
-        for (int o = 1; o < 8; o <<= 1) {
-          mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-          badv |= __shfl_xor_sync(0xffffffffu, (int)badv, o) != 0;
-        }
-        if ((lane & 7) == 0) {
-          const int E = badv ? kExpBad : exp_of_max(mx);
-          sh.exps[es][c] = E;
-          if (E == kExpBad) sh.bad[c] = 1;
-          // column exponents of the whole node, for the X V of the same form: a running
-          // maximum per CTA here, one global atomic per column at the end
-          if (c < kACols) sh.colmax[c] = max(sh.colmax[c], E);
-        }
+      for (int h = 0; h < 2; ++h) {
+        const int u = ct + h * kConvThreads;
+        const int c = u & (kACols - 1), g = u >> 7;
+        const float2 sc = sh.sc[c];
+        const bool dup = b_in_a && c >= b0 - a0 && c < b0 - a0 + kBCols;  // also a B column
+        if (dup)
+          convert_unit<false, true>(st_a(s), c, op_a(t), kPlaneA, c, op_b(t), c - (b0 - a0), g, sc.x, sc.y);
+        else
+          convert_unit<false, false>(st_a(s), c, op_a(t), kPlaneA, c, nullptr, 0, g, sc.x, sc.y);
       }
-      // every converter warp needs the exponents of all columns: arrive on the block's
-      // exponent barrier, which the flushers also wait on, and wait for the others
-      // (a bounded wait: an aborting warp cannot leave the rest stuck)
+      if (!b_in_a) {  // B panel: 64 columns x 4 octets = 256 units, one per thread
+        const int c = ct & (kBCols - 1), g = ct >> 6;
+        const float2 sc = sh.sc[kACols + c];
+        convert_unit<true, false>(st_b(s), c, op_b(t), kPlaneB, c, nullptr, 0, g, sc.x, sc.y);
+      }
+      tc::fence_async_smem();
       __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&bars.exp_full[es]);
-      if (!tc::mbar_wait_warp(&bars.exp_full[es], (blk / kExpSlots) & 1, abort_flag, err, wb)) break;
-      // digits of each stage of the block
-      for (int k = k0; k < k1 && ok; ++k) {
-        const int s = k % kStSlots, t = k % kOpSlots;
-        if (k >= kOpSlots) ok = tc::mbar_wait_warp(&bars.op_free[t], ((k / kOpSlots) - 1) & 1, abort_flag, err, wb);
-        if (!ok) break;
-        // A panel: 128 columns x 4 octets = 512 units, two per thread
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int u = ct + h * kConvThreads;
-          const int c = u & (kACols - 1), g = u >> 7;
-          float s1, s2;
-          scales(sh.exps[es][c], s1, s2);
-          const bool dup = b_in_a && c >= b0 - a0 && c < b0 - a0 + kBCols;  // also a B column
-          if (dup)
-            convert_unit<false, true>(st_a(s), c, op_a(t), kPlaneA, c, op_b(t), c - (b0 - a0), g, s1, s2);
-          else
-            convert_unit<false, false>(st_a(s), c, op_a(t), kPlaneA, c, nullptr, 0, g, s1, s2);
-        }
-        if (!b_in_a) {  // B panel: 64 columns x 4 octets = 256 units, one per thread
-          const int c = ct & (kBCols - 1), g = ct >> 6;
-          float s1, s2;
-          scales(sh.exps[es][kACols + c], s1, s2);
-          convert_unit<true, false>(st_b(s), c, op_b(t), kPlaneB, c, nullptr, 0, g, s1, s2);
-        }
-        tc::fence_async_smem();
-        __syncwarp();
-        if (lane == 0) {
-          tc::mbar_arrive(&bars.st_free[s]);
-          tc::mbar_arrive(&bars.op_full[t]);
-        }
+      if (lane == 0) {
+        tc::mbar_arrive(&bars.st_free[s]);
+        tc::mbar_arrive(&bars.op_full[t]);
       }
     }
   } else {
@@ -433,79 +363,41 @@ __global__ void __launch_bounds__(kThreads, 1)
     long long acc[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) acc[i] = 0;
-    int Ri = kExpZero;                 // running exponent of this lane's row
-    int Rj_l = kExpZero;               // running exponent of column 32 h + lane
     bool ok = true;
-    for (int blk = 0; blk < nblk && ok; ++blk) {
-      const int set = blk & 1, es = blk % kExpSlots;
-      ok = tc::mbar_wait_warp(&bars.acc_full[set], (blk >> 1) & 1, abort_flag, err, wb) &&
-           tc::mbar_wait_warp(&bars.exp_full[es], (blk / kExpSlots) & 1, abort_flag, err, wb);
+    for (int grp = 0; grp < ngroups && ok; ++grp) {
+      const int set = grp & 1;
+      ok = tc::mbar_wait_warp(&bars.acc_full[set], (grp >> 1) & 1, abort_flag, err, wb);
       if (!ok) break;
       tc::tc_fence_after();
-      if (below_diag) {
-        __syncwarp();
-        if (lane == 0) {
-          tc::mbar_arrive(&bars.acc_empty[set]);
-          tc::mbar_arrive(&bars.exp_free[es]);
-        }
-        continue;
-      }
-      const int Ei = sh.exps[es][ai];
-      const int Ej_l = b_in_a ? sh.exps[es][b0 - a0 + 32 * h + lane] : sh.exps[es][kACols + 32 * h + lane];
-      const bool vi = Ei > kExpZero && Ei < kExpBad;
-      const bool vj_l = Ej_l > kExpZero && Ej_l < kExpBad;
-      const int Rinew = vi ? max(Ri, Ei) : Ri;
-      const int Rjnew_l = vj_l ? max(Rj_l, Ej_l) : Rj_l;
-      // per column (one per lane): growth of its running exponent, and the distance of
-      // this block's exponent below the new running one (64: not added)
-      const int grow_l = (Rj_l > kExpZero) ? Rjnew_l - Rj_l : 0;
-      const int below_l = vj_l ? Rjnew_l - Ej_l : 64;
-      const int grow_i = (Ri > kExpZero) ? Rinew - Ri : 0;
-      const int below_i = vi ? Rinew - Ei : 64;
-      Ri = Rinew;
-      Rj_l = Rjnew_l;
-      // the common case, warp-uniform: nothing to shift for any entry of the warp
-      const bool plain = __all_sync(0xffffffffu, grow_l == 0 && below_l == 0 && grow_i == 0 && below_i == 0);
+      if (!below_diag) {
 #pragma unroll
-      for (int g = 0; g < 4; ++g) {  // 8 columns at a time
-        const uint32_t col = (uint32_t)set * kSetCols + (uint32_t)(32 * h + 8 * g);
-        uint32_t l2[8], l3[8], l4[8], l5[8];
-        tc::tmem_ld8_raw(tbase + lanes + col, l2);
-        tc::tmem_ld8_raw(tbase + lanes + col + kBCols, l3);
-        tc::tmem_ld8_raw(tbase + lanes + col + 2 * kBCols, l4);
-        tc::tmem_ld8_raw(tbase + lanes + col + 3 * kBCols, l5);
-        tc::tmem_wait_ld();
-        tc::reg_barrier8(l2);
-        tc::reg_barrier8(l3);
-        tc::reg_barrier8(l4);
-        tc::reg_barrier8(l5);
+        for (int g = 0; g < 4; ++g) {  // 8 columns at a time
+          const uint32_t col = (uint32_t)set * kSetCols + (uint32_t)(32 * h + 8 * g);
+          uint32_t l2[8], l3[8], l4[8], l5[8];
+          tc::tmem_ld8_raw(tbase + lanes + col, l2);
+          tc::tmem_ld8_raw(tbase + lanes + col + kBCols, l3);
+          tc::tmem_ld8_raw(tbase + lanes + col + 2 * kBCols, l4);
+          tc::tmem_ld8_raw(tbase + lanes + col + 3 * kBCols, l5);
+          tc::tmem_wait_ld();
+          tc::reg_barrier8(l2);
+          tc::reg_barrier8(l3);
+          tc::reg_barrier8(l4);
+          tc::reg_barrier8(l5);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int jj = 8 * g + i;  // column within the warp's 32
-          const long long v = (long long)__float2int_rn(__uint_as_float(l2[i])) * 268435456LL +
+          for (int i = 0; i < 8; ++i)  // every group carries the same column scales: plain sums
+            acc[8 * g + i] += (long long)__float2int_rn(__uint_as_float(l2[i])) * 268435456LL +
                               (long long)__float2int_rn(__uint_as_float(l3[i])) * 1048576LL +
                               (long long)__float2int_rn(__uint_as_float(l4[i])) * 4096LL +
                               (long long)__float2int_rn(__uint_as_float(l5[i]) * 16.0f);
-          if (plain) {  // no exponent moved and every block exponent is the running one
-            acc[jj] += v;
-          } else {
-            const int grow = grow_i + __shfl_sync(0xffffffffu, grow_l, jj);
-            const int below = below_i + __shfl_sync(0xffffffffu, below_l, jj);
-            if (grow > 0) acc[jj] = rshift_rn(acc[jj], grow);  // the unit of the sum grew
-            if (below < 64) acc[jj] += rshift_rn(v, below);
-          }
         }
       }
       tc::tc_fence_before();
       __syncwarp();
-      if (lane == 0) {
-        tc::mbar_arrive(&bars.acc_empty[set]);
-        tc::mbar_arrive(&bars.exp_free[es]);
-      }
+      if (lane == 0) tc::mbar_arrive(&bars.acc_empty[set]);
     }
     if (__all_sync(0xffffffffu, ok && !*abort_flag) && !below_diag) {
       const int gi = a0 + ai;
-      const bool bad_i = sh.bad[ai] != 0;
+      const int Ei = sh.ex[ai];
       const int jmax = (J.m + kBCols - 1) / kBCols;
       const int tile_idx = I * jmax - I * (I - 1) + (Jt - 2 * I);
       double* out = J.splits > 1 ? partials + ((size_t)J.item_base + (size_t)tile_idx * J.splits + sp) *
@@ -513,17 +405,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                                  : nullptr;
 #pragma unroll
       for (int jj = 0; jj < 32; ++jj) {
-        const int Rj = __shfl_sync(0xffffffffu, Rj_l, jj);
         const int bj = 32 * h + jj;  // column within the B panel
         const int gj = b0 + bj;
-        const bool bad_j = b_in_a ? sh.bad[gj - a0] != 0 : sh.bad[kACols + bj] != 0;
+        const int Ej = b_in_a ? sh.ex[gj - a0] : sh.ex[kACols + bj];
         double v;
-        if (bad_i || bad_j)
+        if (Ei >= kExpBad || Ej >= kExpBad)
           v = __longlong_as_double(0x7FF8000000000000LL);
-        else if (Ri <= kExpZero || Rj <= kExpZero)
+        else if (Ei <= kExpZero || Ej <= kExpZero)
           v = 0.0;
         else
-          v = ldexp((double)acc[jj], Ri + Rj - 42);
+          v = ldexp((double)acc[jj], Ei + Ej - 42);
         if (out) {
           out[(size_t)ai * kBCols + bj] = v;
         } else if (gi < J.m && gj < J.m && gj >= gi) {
@@ -536,9 +427,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
-  if (J.col_exp && Jt == 2 * I)  // one tile per A panel and split reports its columns
-    for (int c = tid; c < kACols && a0 + c < J.m; c += blockDim.x)
-      if (sh.colmax[c] > kExpZero) atomicMax(&J.col_exp[a0 + c], sh.colmax[c]);
   if (warp == 1) tc::tmem_dealloc(tbase, kTmemCols);
 }
 

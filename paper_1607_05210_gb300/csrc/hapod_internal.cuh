@@ -38,7 +38,7 @@ struct GramJob {
   int64_t rows_per_split;
   double* G;        // m x m, ld = m
   int64_t item_base;
-  int32_t* col_exp; // fixed-point form: receives max over blocks of the column exponents (or null)
+  const int32_t* col_exp; // fixed-point form: exponents of the node's columns (launch_fx_colexp)
   int32_t m;
   int32_t tiles;    // tiles per dimension
   int32_t splits;

@@ -32,6 +32,7 @@
 // its copies and MMAs and frees TMEM.
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "hapod_internal.cuh"
@@ -454,16 +455,43 @@ __global__ void __launch_bounds__(256) modes_fx_vsplit(const FxVSplitJob* __rest
 }
 
 // Column exponents of FP32 X (max |x_rj| < 2^E_j; kExpZero for a zero column, kExpBad
-// for a column holding Inf or NaN): one block per column.
+// for a column holding Inf or NaN): one block per (column, chunk of 2^16 rows), four
+// independent float4 loads in flight per thread, one atomicMax per block (the array
+// starts below kExpZero).
+constexpr int64_t kColexpRows = 1 << 16;
+
 __global__ void __launch_bounds__(256) fx_colexp(const float* __restrict__ X, int64_t ldx, int64_t n, int* exps) {
-  const int j = blockIdx.x;
+  const int j = blockIdx.y;
   const float* x = X + (size_t)j * ldx;
+  const int64_t r0 = (int64_t)blockIdx.x * kColexpRows, r1 = min(n, r0 + kColexpRows);
   float mx = 0.f;
   int bad = 0;
-  for (int64_t r = threadIdx.x; r < n; r += blockDim.x) {
-    const float v = fabsf(x[r]);
-    bad |= !(v <= 3.402823466e38f);
-    mx = fmaxf(mx, v);
+  if ((reinterpret_cast<uintptr_t>(x) & 15) == 0) {
+    const int64_t q0 = r0 / 4, q1 = r1 / 4;  // whole float4s, r0 is a multiple of 4
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    for (int64_t q = q0 + threadIdx.x; q < q1; q += 4 * blockDim.x) {
+      float4 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = q + u * blockDim.x < q1 ? x4[q + u * blockDim.x] : make_float4(0, 0, 0, 0);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float m4 = fmaxf(fmaxf(fabsf(v[u].x), fabsf(v[u].y)), fmaxf(fabsf(v[u].z), fabsf(v[u].w)));
+        bad |= !(m4 <= 3.402823466e38f) | (v[u].x != v[u].x) | (v[u].y != v[u].y) | (v[u].z != v[u].z) |
+               (v[u].w != v[u].w);
+        mx = fmaxf(mx, m4);
+      }
+    }
+    for (int64_t r = 4 * q1 + threadIdx.x; r < r1; r += blockDim.x) {  // ragged tail
+      const float v = fabsf(x[r]);
+      bad |= !(v <= 3.402823466e38f);
+      mx = fmaxf(mx, v);
+    }
+  } else {
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+      const float v = fabsf(x[r]);
+      bad |= !(v <= 3.402823466e38f);
+      mx = fmaxf(mx, v);
+    }
   }
   __shared__ float s_m[8];
   __shared__ int s_b[8];
@@ -489,7 +517,7 @@ __global__ void __launch_bounds__(256) fx_colexp(const float* __restrict__ X, in
       e = kExpBad;
     else if (m > 0.f)
       frexpf(m, &e);
-    exps[j] = e;
+    atomicMax(&exps[j], e);
   }
 }
 
@@ -503,7 +531,11 @@ size_t fx_vdig_bytes(int64_t m, int64_t k) {
 }
 
 cudaError_t launch_fx_colexp(const float* X, int64_t ldx, int64_t n, int64_t m, int* exps, cudaStream_t s) {
-  if (m > 0) fx_colexp<<<(unsigned)m, 256, 0, s>>>(X, ldx, n, exps);
+  if (m <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(exps, 0x80, sizeof(int) * (size_t)m, s);  // below kExpZero
+  if (e != cudaSuccess) return e;
+  const unsigned chunks = (unsigned)std::max<int64_t>(1, (n + kColexpRows - 1) / kColexpRows);
+  fx_colexp<<<dim3(chunks, (unsigned)m), 256, 0, s>>>(X, ldx, n, exps);
   return cudaGetLastError();
 }
 

@@ -1,18 +1,17 @@
 """Mixed fixed-point form (FP32 snapshots; tcgen05 Gram from four balanced 8-bit
-digits per value, fixed-point per column and 64-row block, integer-exact sums) versus
-the CPU FP64 oracle run on the same FP32 values.
+digits per value, fixed-point per column, integer-exact sums) versus the CPU FP64
+oracle run on the same FP32 values.
 
 Tolerances, derived from the arithmetic of gram_fx3.cu:
-  * Gram: in a 64-row exponent block b column j is represented as an integer
-    multiple of 2^(E_j - 31) with |x - x~| <= 2^(E_j - 32), 2^(E_j - 1) <= M_j^b < 2^E_j
-    (M the block maximum of |x|); the thirteen kept digit pairs (levels 2..6) leave out
-    less than 2^(E_i + E_j - 38.9) per row; the level sums 2..4 are exact integers,
-    the FP32 rounding of L'_5 = L_5 + 2^-8 L_6 (28 steps per 64-row block, each below
-    2^-24 |L'_5| <= 2^-2 of its unit) adds less than 2^(E_i + E_j - 41) per row, and the
-    int64 sums lose at most half a unit of 2^(R_i + R_j - 42) per shift.  Per row:
-    |x_i x_j - p| <= (2^-31 + 2^-38.9 + 2^-41) 2^(E_i + E_j) <= 2^-27 M_i^b M_j^b, so
-    |G - G_ref| <= 2^-27 sum_r M_i^b(r) M_j^b(r) + the oracle's FP64 rounding
-    (1e-13 sqrt(n) sqrt(G_ii G_jj)).
+  * Gram: column j is represented as an integer multiple of 2^(E_j - 31) with
+    |x - x~| <= 2^(E_j - 32), 2^(E_j - 1) <= M_j < 2^E_j (M the column maximum of
+    |x|); the thirteen kept digit pairs (levels 2..6) leave out less than
+    2^(E_i + E_j - 38.9) per row; the level sums 2..4 are exact integers, the FP32
+    rounding of L'_5 = L_5 + 2^-8 L_6 (56 steps per 128-row group, each below
+    2^-24 |L'_5| <= 2^-1 of its unit) adds less than 2^(E_i + E_j - 40) per row, and
+    the int64 sums are exact.  Per row: |x_i x_j - p| <= (2^-31 + 2^-38.9 + 2^-40)
+    2^(E_i + E_j) <= 2^-27 M_i M_j, so |G - G_ref| <= 2^-27 n M_i M_j + the oracle's
+    FP64 rounding (1e-13 sqrt(n) sqrt(G_ii G_jj)).
   * exact case: small integers are represented exactly and every sum is an exact
     integer, so G equals the oracle's bit for bit.
   * the precision workload's leaf tolerance (eps = 1e-4 rel, quaternary tree of depth
@@ -48,19 +47,10 @@ def _gram(H, X, ld=None):
     return H.hapod_gram(to_dev(X, dtype=torch.float32, ld=ld), H.HAPOD_MIXED_FX3).cpu().numpy()
 
 
-def _block_bound(X):
-    """2^-27 sum_r M_i(r) M_j(r), M(r) the maximum of |x| over the 64-row exponent block
-    that holds row r (blocks start at multiples of 64 rows of a row split; bounded here
-    by the 64-row blocks b - 1, b, b + 1 around r)."""
-    n, m = X.shape
-    nb = (n + 63) // 64
-    Xp = np.zeros((nb * 64, m))
-    Xp[:n] = np.abs(X)
-    M = Xp.reshape(nb, 64, m).max(axis=1)  # nb x m maxima of the 64-row blocks
-    Mn = M.copy()
-    Mn[1:] = np.maximum(Mn[1:], M[:-1])
-    Mn[:-1] = np.maximum(Mn[:-1], M[1:])
-    return 2.0 ** -27 * 64 * (Mn.T @ Mn)
+def _column_bound(X):
+    """2^-27 n M_i M_j, M the column maxima of |x|."""
+    M = np.max(np.abs(X), axis=0)
+    return 2.0 ** -27 * X.shape[0] * np.outer(M, M)
 
 
 @pytest.mark.parametrize("n,m,ld,kind", [(1000, 1, 1000, "gauss"), (10000, 100, 10000, "gauss"),
@@ -83,7 +73,7 @@ def test_gram_fx3(H, n, m, ld, kind):
     G = _gram(H, X, ld)
     ref = oracle.gram(X)
     d = np.sqrt(np.diag(ref))
-    bound = _block_bound(X) + 1e-13 * math.sqrt(n) * np.outer(d, d)
+    bound = _column_bound(X) + 1e-13 * math.sqrt(n) * np.outer(d, d)
     rel = np.abs(G - ref) / np.maximum(np.outer(d, d), 1e-300)
     print(f"gram fx3 n={n} m={m} {kind}: max {rel.max():.3e} rms {np.sqrt(np.mean(rel ** 2)):.3e}")
     assert np.all(np.abs(G - ref) <= bound)
