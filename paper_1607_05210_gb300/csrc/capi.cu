@@ -693,7 +693,8 @@ bool step_modes_fx(Env& env, std::vector<Work*>& ws) {
     uint16_t* vdig = (uint16_t*)env.alloc(fx_vdig_bytes(w->m, k), "alloc V digits");
     int32_t* fexp = (int32_t*)env.alloc(sizeof(int32_t) * mode_tiles * MT, "alloc mode exponents");
     float2* xscale = (float2*)env.alloc(fx_xscale_bytes(w->m), "alloc column scales");
-    float* yscale = (float*)env.alloc(sizeof(float) * mode_tiles * MT, "alloc mode scales");
+    float* yscale = (float*)env.alloc(sizeof(float) * mode_tiles * MT * 2, "alloc mode scales");
+    float* ymul = yscale ? yscale + mode_tiles * MT : nullptr;
     bufs.push_back(vdig);
     bufs.push_back(fexp);
     bufs.push_back(xscale);
@@ -710,6 +711,7 @@ bool step_modes_fx(Env& env, std::vector<Work*>& ws) {
     V.xscale = xscale;
     V.scale = w->scale;
     V.yscale = yscale;
+    V.ymul = ymul;
     V.m = (int32_t)w->m;
     V.k = k;
     V.kpad = mode_tiles * MT;
@@ -721,6 +723,7 @@ bool step_modes_fx(Env& env, std::vector<Work*>& ws) {
     M.exps = w->exps;
     M.xscale = xscale;
     M.yscale = yscale;
+    M.ymul = ymul;
     M.vdig = vdig;
     M.fexp = fexp;
     M.scale = w->scale;

@@ -111,6 +111,7 @@ struct FxVSplitJob {
   float2* xscale;  // per column j (padded to whole stages): s1 s2 = 2^(30 - E_j)
   const double* scale;  // k or null: scale of mode c
   float* yscale;        // kpad: FP32 scale of mode c (1 without a scale)
+  float* ymul;          // kpad: output factor 2^(F_c - 37) yscale_c (0 zero, NaN bad, -1 not a normal float)
   int32_t m;
   int32_t k;
   int32_t kpad;  // k rounded up to whole mode tiles
@@ -127,6 +128,7 @@ struct FxModesJob {
   const int32_t* fexp;
   const double* scale;  // k or null
   const float* yscale;  // kpad: FP32 scale of mode c
+  const float* ymul;    // kpad: output factor of mode c (see FxVSplitJob)
   float* Y;
   int64_t ldy;
   int64_t n;

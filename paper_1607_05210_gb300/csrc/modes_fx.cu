@@ -337,22 +337,23 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       if (!ok || abort_flag) break;
       // y = acc 2^(F_c - 37) scale_c in FP32 arithmetic (GB300 runs FP64 at 1/64 of the
-      // FP32 rate): at most two roundings of the int64 sum, an exact power-of-two
-      // scaling (ldexpf rounds only in the subnormal range) and the FP32 scale
+      // FP32 rate): at most two roundings of the int64 sum times the mode's factor
+      // 2^(F_c - 37) scale_c (exact when it is a normal float; ldexpf otherwise)
       const int64_t row = I.row0 + 32 * q + lane;
+      float* __restrict__ ycol = J.Y + (size_t)(I.mt * kModesT + 32 * h) * J.ldy + row;
 #pragma unroll
       for (int c = 0; c < 32; ++c) {
         const int col = I.mt * kModesT + 32 * h + c;
         if (col >= J.k || row >= J.n) continue;
-        const int F = J.fexp[col];
+        const float f = J.ymul[col];  // > 0 factor, 0 zero mode, NaN bad mode, -1 out of range
         float y;
-        if (F >= kExpBad)
-          y = __int_as_float(0x7FC00000);
-        else if (F <= kExpZero)
-          y = 0.f;
+        if (f > 0.f)
+          y = i64_to_f32(acc[c]) * f;
+        else if (f == 0.f || f != f)
+          y = f;
         else
-          y = ldexpf(i64_to_f32(acc[c]), F - 37) * J.yscale[col];
-        J.Y[(size_t)col * J.ldy + row] = y;
+          y = ldexpf(i64_to_f32(acc[c]), J.fexp[col] - 37) * J.yscale[col];
+        ycol[(size_t)c * J.ldy] = y;
       }
     }
   }
@@ -408,7 +409,19 @@ __global__ void __launch_bounds__(256) modes_fx_vsplit(const FxVSplitJob* __rest
   const int F = s_max[0];
   if (tid == 0) {
     J.fexp[c] = F;
-    J.yscale[c] = c < J.k && J.scale ? (float)J.scale[c] : 1.0f;
+    const float ys = c < J.k && J.scale ? (float)J.scale[c] : 1.0f;
+    J.yscale[c] = ys;
+    // one FP32 factor 2^(F - 37) ys for the output, when it is a normal float
+    float f;
+    if (F >= kExpBad) {
+      f = __int_as_float(0x7FC00000);
+    } else if (F <= kExpZero || ys == 0.f) {
+      f = 0.f;
+    } else {
+      const double fd = ldexp((double)ys, F - 37);
+      f = (fabs(fd) >= 0x1.0p-126 && fabs(fd) < 0x1.0p+127 && ys > 0.f) ? (float)fd : -1.f;
+    }
+    J.ymul[c] = f;
   }
   // the block of mode 0 also writes the X scale pairs s1 s2 = 2^(30 - E_j) of the
   // converters (zero for zero or non-finite columns and for the padding up to whole
