@@ -45,8 +45,11 @@
  *     fp16 tensor cores over 128-row groups and in int64, so the Gram carries only the
  *     representation error (at most 2^-32 of the column maximum per value, unbiased)
  *     and one FP64 rounding per entry and row split.  X V from the same column
- *     exponents and four digits of V, exact level sums, int64.  Eigensolve with FP64
- *     rotations, FP64 tails, CholQR2 at the root.
+ *     exponents and four digits of V: the leading digit pair summed exactly (int32
+ *     across groups of 2048 columns), the nine next pairs (weights 2^-8 .. 2^-24 of
+ *     it) summed by the tensor cores in FP32, one FP32 rounding per entry; at most
+ *     245760 snapshot columns.  Eigensolve with FP64 rotations, FP64 tails, CholQR2
+ *     at the root.
  *     Eigensolve, tail sums and truncation use FP64 arithmetic on FP64 data except
  *     where stated.
  */
@@ -304,9 +307,10 @@ hapod_status hapod_truncate(int64_t m, const double* lambda, double eps, int64_t
  * doubles or NULL; Y: device n x N (ld ldy), same type as X.  The digit-slice form
  * computes Y from exact digit products (X as for hapod_gram, V column c against a
  * power-of-two bound of max_j 2^E_j |V_jc|), rounds once per entry and 128-column
- * block of X and sums the blocks in FP64, synchronises the stream, and returns NaN
- * columns if X or V holds Inf or NaN; TIMEOUT if a bounded device-side wait ran
- * out.
+ * block of X and sums the blocks in FP64; the fixed-point form as described for
+ * HAPOD_MIXED_FX3 (m <= 245760, else ERR_INVALID).  Both synchronise the stream and
+ * return NaN columns if X or V holds Inf or NaN; TIMEOUT if a bounded device-side
+ * wait ran out.
  */
 hapod_status hapod_modes(int32_t precision, int64_t n, int64_t m, const void* X, int64_t ldx, const double* V,
                          int64_t ldv, int64_t N, const double* scale, void* Y, int64_t ldy, void* stream);

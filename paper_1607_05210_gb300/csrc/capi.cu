@@ -671,7 +671,6 @@ bool step_gram_fx3(Env& env, std::vector<Work*>& ws) {
 bool step_modes_fx(Env& env, std::vector<Work*>& ws) {
   if (ws.empty()) return true;
   const int nw = (int)ws.size();
-  const int MT = fx_modes_tile();
   std::vector<FxVSplitJob> vj(nw);
   std::vector<FxModesJob> mj(nw);
   std::vector<CUtensorMap> maps(nw);
@@ -689,17 +688,27 @@ bool step_modes_fx(Env& env, std::vector<Work*>& ws) {
       if (!ok) break;
     }
     const int k = w->res.k;
-    const int mode_tiles = (k + MT - 1) / MT;
+    if (w->m > fx_modes_max_m()) {
+      ok = env.fail(HAPOD_ERR_INVALID, "fixed-point X V: more snapshot columns than the form supports");
+      break;
+    }
+    const int mode_tiles = fx_mode_tiles(k), MT = fx_mode_width(k);
     uint16_t* vdig = (uint16_t*)env.alloc(fx_vdig_bytes(w->m, k), "alloc V digits");
     int32_t* fexp = (int32_t*)env.alloc(sizeof(int32_t) * mode_tiles * MT, "alloc mode exponents");
     float2* xscale = (float2*)env.alloc(fx_xscale_bytes(w->m), "alloc column scales");
     float* yscale = (float*)env.alloc(sizeof(float) * mode_tiles * MT * 2, "alloc mode scales");
     float* ymul = yscale ? yscale + mode_tiles * MT : nullptr;
+    int32_t* Z = nullptr;
+    if (fx_modes_needs_scratch(w->m)) {
+      Z = (int32_t*)env.alloc(sizeof(int32_t) * (size_t)w->n * mode_tiles * MT, "alloc X V partial sums");
+      bufs.push_back(Z);
+      ok = Z != nullptr;
+    }
     bufs.push_back(vdig);
     bufs.push_back(fexp);
     bufs.push_back(xscale);
     bufs.push_back(yscale);
-    ok = vdig && fexp && xscale && yscale;
+    ok = ok && vdig && fexp && xscale && yscale;
     if (!ok) break;
     FxVSplitJob& V = vj[i];
     memset(&V, 0, sizeof(V));
@@ -715,6 +724,7 @@ bool step_modes_fx(Env& env, std::vector<Work*>& ws) {
     V.m = (int32_t)w->m;
     V.k = k;
     V.kpad = mode_tiles * MT;
+    V.nt = MT;
     max_kpad = std::max(max_kpad, V.kpad);
     FxModesJob& M = mj[i];
     memset(&M, 0, sizeof(M));
@@ -735,6 +745,9 @@ bool step_modes_fx(Env& env, std::vector<Work*>& ws) {
     M.k = k;
     M.row_tiles = (int32_t)((w->n + 127) / 128);
     M.mode_tiles = mode_tiles;
+    M.nt = MT;
+    M.Z = Z;
+    M.ldz = w->n;
     items += (int64_t)M.row_tiles * mode_tiles;
     if (!encode_colmajor_f32(&maps[i], w->X, w->n, w->m, w->ldx, 128, 16, false))
       ok = env.fail(HAPOD_ERR_CUDA, "cuTensorMapEncodeTiled failed for an X V input");

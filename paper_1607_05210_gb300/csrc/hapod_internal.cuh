@@ -99,9 +99,12 @@ constexpr int kFxExpZero = -4000;
 constexpr int kFxExpBad = 4000;
 
 // X V of the fixed-point form.  V_k digits (modes_fx_vsplit): per mode c the exponent
-// F_c (fexp, kpad entries) and four digit planes in the operand layout (vdig,
+// F_c (fexp, kpad entries) and six digit planes in the operand layout (vdig,
 // fx_vdig_bytes(m, k) bytes); X columns need their exponents (exps, m entries: from
-// the Gram's col_exp or launch_fx_colexp).
+// the Gram's col_exp or launch_fx_colexp).  Modes are tiled fx_mode_tiles(k) x
+// fx_mode_width(k) (kpad = their product, at most 128 modes a tile); m at most
+// fx_modes_max_m(); for fx_modes_needs_scratch(m) the kernel keeps int32 partial sums
+// in Z (n x kpad, leading dimension ldz).
 struct FxVSplitJob {
   const double* V;
   int64_t ldv;
@@ -111,13 +114,13 @@ struct FxVSplitJob {
   float2* xscale;  // per column j (padded to whole stages): s1 s2 = 2^(30 - E_j)
   const double* scale;  // k or null: scale of mode c
   float* yscale;        // kpad: FP32 scale of mode c (1 without a scale)
-  float* ymul;          // kpad: output factor 2^(F_c - 37) yscale_c (0 zero, NaN bad, -1 not a normal float)
+  float* ymul;          // kpad: output factor 2^(F_c - 21) yscale_c (0 zero, NaN bad, -1 not a normal float)
   int32_t m;
   int32_t k;
   int32_t kpad;  // k rounded up to whole mode tiles
-  int32_t pad;
+  int32_t nt;    // modes per tile (fx_mode_width(k))
 };
-// Items (row tile, mode tile) of 128 rows x 64 modes of one node; maps_dev[j]: X of job j
+// Items (row tile, mode tile) of 128 rows x nt modes of one node; maps_dev[j]: X of job j
 // (encode_colmajor_f32, box 128 rows x 16 columns, no swizzle).
 struct FxModesJob {
   const float* X;
@@ -131,14 +134,21 @@ struct FxModesJob {
   const float* ymul;    // kpad: output factor of mode c (see FxVSplitJob)
   float* Y;
   int64_t ldy;
+  int32_t* Z;  // fx_modes_needs_scratch(m): int32 partial sums, n x kpad; else null
+  int64_t ldz;
   int64_t n;
   int64_t item_base;
   int32_t m;
   int32_t k;
   int32_t row_tiles;
   int32_t mode_tiles;
+  int32_t nt;
+  int32_t pad;
 };
-int fx_modes_tile();
+int fx_mode_tiles(int64_t k);
+int fx_mode_width(int64_t k);
+int64_t fx_modes_max_m();
+bool fx_modes_needs_scratch(int64_t m);
 size_t fx_vdig_bytes(int64_t m, int64_t k);
 size_t fx_xscale_bytes(int64_t m);
 cudaError_t launch_fx_colexp(const float* X, int64_t ldx, int64_t n, int64_t m, int* exps, cudaStream_t s);
