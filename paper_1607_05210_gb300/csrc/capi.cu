@@ -838,7 +838,10 @@ bool step_gram(Env& env, int precision, std::vector<Work*>& ws) {
 
 // Eigensolver variant of a form: FP32 rotations for the mixed TF32 form, FP64 rotations
 // for every other form.
-int eig_mode(int precision) { return precision == HAPOD_MIXED_TF32X3 ? kEigF32 : kEigF64; }
+// FP64-data forms rotate in FP64; the mixed forms with FP64 eigenvectors in double-float
+int eig_mode(int precision) {
+  return precision == HAPOD_MIXED_TF32X3 ? kEigF32 : f64_data(precision) ? kEigF64 : kEigDF;
+}
 // Relative level of a form's Gram error (the pivoted Cholesky does not factor below it).
 double gram_floor_rel(int precision) {
   return precision == HAPOD_MIXED_BF16X3 ? 1e-10 : precision == HAPOD_MIXED_FX3 ? 1e-13 : 0.0;

@@ -319,6 +319,7 @@ struct EigJob {
 // Rotation precision: FP64 (V in FP64) or FP32 (V in FP32).
 constexpr int kEigF64 = 0;
 constexpr int kEigF32 = 1;
+constexpr int kEigDF = 2;  // double-float rotations (FP32 pairs), FP64 eigenvectors
 // Cooperative launches over the jobs, several CTAs per job.  jobs_host is completed
 // (cta0, ncta, sync) and copied to jobs_dev (njobs entries); sync_dev: njobs entries.
 // err: the bounded-wait flag block (err[1] = debug wait budget) or null.

@@ -13,7 +13,12 @@
 //    from the right make the columns mutually orthogonal, L J = W, so L L^T = W W^T and
 //    the eigenvectors are u_j = w_j / ||w_j|| (no rotation matrix is accumulated);
 //    pairs in the round-robin ("circle") order, rotated while
-//    |w_p . w_q| > m u ||w_p|| ||w_q||, u the unit roundoff of T;
+//    |w_p . w_q| > m u ||w_p|| ||w_q||, u the unit roundoff of T.  T is FP64, FP32 or
+//    the double-float DF (a pair of FP32 values, hi + lo, about 47 bits: Dekker's
+//    exact product via FMA and Knuth's two-sum), which keeps near-FP64 accuracy on the
+//    FP32 pipe (GB300 runs FP64 at 1/64 of the FP32 rate); with DF the columns are
+//    scaled by a power of two near 1/sqrt(trace G) so that every square stays in the
+//    FP32 range, and the rotation angle is formed in FP64 once per pair;
 // 3. lambda_j = u_j^T G u_j in FP64 (Rayleigh quotients against the original G: second
 //    order in the eigenvector error), sorted descending, clamped >= 0, zero beyond r.
 // GB300 executes FP64 at about two fused multiply-adds per clock and SM, so one CTA
@@ -26,6 +31,7 @@
 // runs out of its budget raises the node's abort word and error status
 // HAPOD_ERR_TIMEOUT; every CTA of the node then leaves.
 #include <algorithm>
+#include <type_traits>
 
 #include "hapod_internal.cuh"
 #include "tc_common.cuh"
@@ -35,6 +41,11 @@ namespace {
 
 constexpr int kThreads = 128;
 constexpr int kWarps = kThreads / 32;
+
+// double-float: value hi + lo, |lo| <= ulp(hi) / 2
+struct DF {
+  float hi, lo;
+};
 
 template <typename T>
 struct Unit;
@@ -46,6 +57,80 @@ template <>
 struct Unit<float> {
   static __device__ float eps() { return 5.9604645e-08f; }
 };
+template <>
+struct Unit<DF> {
+  static __device__ double eps() { return 7.105427357601002e-15; }  // 2^-47
+};
+
+// FP64 value -> rotation storage, and back.
+template <typename T>
+__device__ __forceinline__ T to_rot(double v) {
+  return (T)v;
+}
+template <>
+__device__ __forceinline__ DF to_rot<DF>(double v) {
+  DF r;
+  r.hi = __double2float_rn(v);
+  r.lo = __double2float_rn(v - (double)r.hi);
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ double from_rot(T v) {
+  return (double)v;
+}
+template <>
+__device__ __forceinline__ double from_rot<DF>(DF v) {
+  return (double)v.hi + (double)v.lo;
+}
+
+// s + e = a + b exactly (two-sum, no ordering assumption)
+__device__ __forceinline__ float two_sum(float a, float b, float& e) {
+  const float s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+  return s;
+}
+// (S, C) += x y for double-floats: the product hi hi exactly (p + fma residual), the
+// cross terms hi lo and lo hi in FP32, lo lo (2^-48 relative) dropped; C collects
+// the rounding errors of the running sum S
+__device__ __forceinline__ void df_dot_acc(float& S, float& C, DF x, DF y) {
+  const float p = x.hi * y.hi;
+  float t = fmaf(x.hi, y.hi, -p);
+  t = fmaf(x.hi, y.lo, t);
+  t = fmaf(x.lo, y.hi, t);
+  float e;
+  S = two_sum(S, p, e);
+  C += e + t;
+}
+// a x + b y for double-floats, renormalised
+__device__ __forceinline__ DF df_lin2(DF a, DF x, DF b, DF y) {
+  const float p1 = a.hi * x.hi;
+  float e1 = fmaf(a.hi, x.hi, -p1);
+  e1 = fmaf(a.hi, x.lo, e1);
+  e1 = fmaf(a.lo, x.hi, e1);
+  const float p2 = b.hi * y.hi;
+  float e2 = fmaf(b.hi, y.hi, -p2);
+  e2 = fmaf(b.hi, y.lo, e2);
+  e2 = fmaf(b.lo, y.hi, e2);
+  float e;
+  const float h = two_sum(p1, p2, e);
+  const float l = e + (e1 + e2);
+  DF r;
+  r.hi = h + l;
+  r.lo = l - (r.hi - h);
+  return r;
+}
+// warp sum of a running double-float sum (S, C), as FP64
+__device__ __forceinline__ double warp_sum_df(float S, float C) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oS = __shfl_xor_sync(0xffffffffu, S, o), oC = __shfl_xor_sync(0xffffffffu, C, o);
+    float e;
+    S = two_sum(S, oS, e);
+    C += oC + e;
+  }
+  return (double)S + (double)C;
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -270,12 +355,15 @@ __global__ void __launch_bounds__(kThreads) eig_coop_kernel(const EigJob* __rest
     // ---------------- one-sided Jacobi on the r columns (precision T)
     // W held the odd steps' diagonal: every CTA must be done with its last pivot search
     if (P > 1 && !bar.sync()) goto timeout;
+    // DF: columns scaled by 2^-e, 2^e near sqrt(trace G) (exact; the eigenvectors and
+    // the convergence test do not depend on it)
+    const double wscale = std::is_same<T, DF>::value && trace > 0.0 ? ldexp(1.0, -ilogb(sqrt(trace))) : 1.0;
     for (int j = 0; j < r; ++j)
-      for (int i = i0 + tid; i < i1; i += blockDim.x) W[(size_t)j * m + i] = (T)L[(size_t)j * m + i];
+      for (int i = i0 + tid; i < i1; i += blockDim.x) W[(size_t)j * m + i] = to_rot<T>(L[(size_t)j * m + i] * wscale);
     if (!bar.sync()) goto timeout;
     const int rp = r + (r & 1), npairs = rp / 2;
     const int nw = P * kWarps, wg = c * kWarps + warp;
-    const T rtol = (T)m * Unit<T>::eps();
+    const auto rtol = m * Unit<T>::eps();
     int sweeps = 0;
     bool converged = (r <= 1);
     volatile int* rot_sweep = &J.sync->rot_sweep;
@@ -288,6 +376,29 @@ __global__ void __launch_bounds__(kThreads) eig_coop_kernel(const EigJob* __rest
           if (p >= r || q >= r) continue;
           T* wp = W + (size_t)p * m;
           T* wq = W + (size_t)q * m;
+          if constexpr (std::is_same<T, DF>::value) {
+            float aS = 0.f, aC = 0.f, bS = 0.f, bC = 0.f, gS = 0.f, gC = 0.f;
+            for (int i = lane; i < m; i += 32) {
+              const DF x = wp[i], y = wq[i];
+              df_dot_acc(aS, aC, x, x);
+              df_dot_acc(bS, bC, y, y);
+              df_dot_acc(gS, gC, x, y);
+            }
+            const double al = warp_sum_df(aS, aC), be = warp_sum_df(bS, bC), ga = warp_sum_df(gS, gC);
+            if (ga == 0.0 || !(fabs(ga) > rtol * sqrt(al * be))) continue;
+            if (lane == 0 && *rot_sweep < sweeps) atomicMax(&J.sync->rot_sweep, sweeps);
+            const double zeta = (be - al) / (2.0 * ga);
+            const double tt = fabs(zeta) > 1e15 ? 0.5 / zeta
+                                                : (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            const double cs = 1.0 / sqrt(1.0 + tt * tt);
+            const DF c = to_rot<DF>(cs), sn = to_rot<DF>(cs * tt), msn = to_rot<DF>(-(cs * tt));
+            for (int i = lane; i < m; i += 32) {
+              const DF x = wp[i], y = wq[i];
+              wp[i] = df_lin2(c, x, msn, y);
+              wq[i] = df_lin2(sn, x, c, y);
+            }
+            continue;
+          } else {
           T al = 0, be = 0, ga = 0;
           for (int i = lane; i < m; i += 32) {
             const T x = wp[i], y = wq[i];
@@ -310,6 +421,7 @@ __global__ void __launch_bounds__(kThreads) eig_coop_kernel(const EigJob* __rest
             wp[i] = cs * x - sn * y;
             wq[i] = sn * x + cs * y;
           }
+          }
         }
         if (!bar.sync()) goto timeout;
       }
@@ -317,16 +429,23 @@ __global__ void __launch_bounds__(kThreads) eig_coop_kernel(const EigJob* __rest
     }
 
     // ---------------- u_j = w_j / ||w_j|| and FP64 Rayleigh quotients against G
+    // (DF columns become FP64 columns in place: element i of both occupies the same 8 bytes)
+    using Out = typename std::conditional<std::is_same<T, DF>::value, double, T>::type;
     for (int j = wg; j < m; j += nw) {
-      T* wj = W + (size_t)j * m;
+      Out* wj = reinterpret_cast<Out*>(W + (size_t)j * m);
       double acc = 0.0;
       if (j < r) {
+        if constexpr (std::is_same<T, DF>::value) {
+          const DF* wdf = W + (size_t)j * m;
+          for (int i = lane; i < m; i += 32) wj[i] = from_rot(wdf[i]);
+          __syncwarp();
+        }
         double s = 0.0;
         for (int i = lane; i < m; i += 32) s += (double)wj[i] * (double)wj[i];
         s = warp_sum(s);
         if (s > 0.0) {
           const double inv = 1.0 / sqrt(s);
-          for (int i = lane; i < m; i += 32) wj[i] = (T)((double)wj[i] * inv);
+          for (int i = lane; i < m; i += 32) wj[i] = (Out)((double)wj[i] * inv);
         }
         __syncwarp();
         for (int i = lane; i < m; i += 32) {
@@ -336,7 +455,7 @@ __global__ void __launch_bounds__(kThreads) eig_coop_kernel(const EigJob* __rest
         }
         acc = warp_sum(acc);
       } else {
-        for (int i = lane; i < m; i += 32) wj[i] = T(0);
+        for (int i = lane; i < m; i += 32) wj[i] = Out(0);
       }
       if (lane == 0) d[j] = acc;  // d now holds the unsorted eigenvalues
     }
@@ -373,7 +492,9 @@ size_t eig_smem_bytes(int m) { return (size_t)std::max(m, 1) * sizeof(double); }
 cudaError_t launch_eig(int mode, EigJob* jobs_host, EigJob* jobs_dev, int njobs, int max_m, int max_sweeps,
                        EigSync* sync_dev, const int* err, cudaStream_t s) {
   if (njobs <= 0) return cudaSuccess;
-  const void* fn = mode == kEigF32 ? (const void*)eig_coop_kernel<float> : (const void*)eig_coop_kernel<double>;
+  const void* fn = mode == kEigF32  ? (const void*)eig_coop_kernel<float>
+                   : mode == kEigDF ? (const void*)eig_coop_kernel<DF>
+                                    : (const void*)eig_coop_kernel<double>;
   const size_t smem = eig_smem_bytes(max_m);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -68,8 +68,10 @@ def leaf_split(X: np.ndarray, parent, cols):
 
 
 def max_angle_sin(U1: np.ndarray, U2: np.ndarray) -> float:
-    """sin of the largest principal angle between span(U1) and span(U2) (both orthonormal)."""
+    """sin of the largest principal angle between span(U1) and span(U2) (both orthonormal):
+    the 2-norm of the part of U1 outside span(U2).  (sqrt(1 - cos^2) from the singular
+    values of U1^T U2 would turn an orthonormality defect d of the columns into an
+    apparent angle of sqrt(2 d).)"""
     if U1.shape[1] == 0:
         return 0.0
-    s = np.linalg.svd(U1.T @ U2, compute_uv=False)
-    return math.sqrt(max(0.0, 1.0 - float(np.min(s)) ** 2))
+    return float(np.linalg.norm(U1 - U2 @ (U2.T @ U1), 2))
