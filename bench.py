@@ -48,6 +48,7 @@ import statistics
 import subprocess
 import sys
 import tempfile
+import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -274,26 +275,33 @@ def c3_fro2(H, wl, device, stream):
     return tot
 
 
-def run_waves(H, precision, wl, fro2, steps, warmup, stream, dist_ctx, host=None):
+E2E_CHUNK = 64 << 20  # bytes per upload command in the end-to-end leg
+
+
+def run_waves(H, precision, wl, fro2, steps, warmup, stream, dist_ctx, host=None, batch=None, copy_streams=1):
     """The headline HAPOD: per wave, generate its leaves (untimed), then push them
     (timed).  With ``host`` (pinned host buffers, one wave), the generated leaves are
-    first copied to the host (untimed) and the timed interval holds their uploads."""
+    first copied to the host (untimed) and the timed interval holds their uploads:
+    each leaf in ``copy_streams`` column slices on as many copy streams, and with
+    ``batch`` (max_pending_leaves, default the wave) the context processes every
+    ``batch`` pushed leaves while the next leaves are still uploading."""
     import torch
 
     parent, leaves, cols = c3_tree(wl)
     dtype = H.DTYPE[precision]
     device = torch.device("cuda", torch.cuda.current_device())
     W = wl["wave"]
+    B = batch or W
     gen = make_generator(H, wl, dtype, device, W)
     eps = wl["eps_rel"] * math.sqrt(fro2)
-    copy_stream = torch.cuda.Stream(device) if host is not None else None
+    copy_ss = [torch.cuda.Stream(device) for _ in range(max(1, copy_streams))] if host is not None else None
     info = {}
     launches = [0]
     gen_ms = [0.0]
 
     def step(profile, timed):
         ctx = H.hapod_create(parent, cols, eps, wl["omega"], wl["n"], precision, stream=stream,
-                             max_pending_leaves=W, flags=H.HAPOD_FLAG_PROFILE if profile else 0)
+                             max_pending_leaves=B, flags=H.HAPOD_FLAG_PROFILE if profile else 0)
         ms = 0.0
         d2h = 0
         for w0 in range(0, len(leaves), W):
@@ -312,17 +320,24 @@ def run_waves(H, precision, wl, fro2, steps, warmup, stream, dist_ctx, host=None
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             if host is not None:
-                copy_stream.wait_event(e0)
                 done = []
-                with torch.cuda.stream(copy_stream):
-                    for i in range(w0, min(len(leaves), w0 + W)):
-                        views[i].copy_(host[i - w0][:views[i].shape[0]], non_blocking=True)
-                        ev = torch.cuda.Event()
-                        ev.record(copy_stream)
-                        done.append(ev)
+                for cs in copy_ss:
+                    cs.wait_event(e0)
+                for i in range(w0, min(len(leaves), w0 + W)):
+                    mi = views[i].shape[0]
+                    cuts = [mi * q // len(copy_ss) for q in range(len(copy_ss) + 1)]
+                    evs = []
+                    for q, cs in enumerate(copy_ss):
+                        with torch.cuda.stream(cs):
+                            views[i][cuts[q]:cuts[q + 1]].copy_(host[i - w0][cuts[q]:cuts[q + 1]], non_blocking=True)
+                            ev = torch.cuda.Event()
+                            ev.record(cs)
+                            evs.append(ev)
+                    done.append(evs)
             for i in range(w0, min(len(leaves), w0 + W)):
                 if host is not None:
-                    stream.wait_event(done[i - w0])
+                    for ev in done[i - w0]:
+                        stream.wait_event(ev)
                 H.hapod_push(ctx, leaves[i], views[i].t())
             if w0 + W >= len(leaves):
                 s, U, st = H.hapod_result(ctx, device=device)
@@ -370,6 +385,122 @@ def run_waves(H, precision, wl, fro2, steps, warmup, stream, dist_ctx, host=None
     torch.cuda.empty_cache()
     return res
 
+
+
+def run_waves_e2e(H, precision, wl, fro2, steps, warmup, stream, dist_ctx, host):
+    """End-to-end leg of the headline: the snapshots come from pinned host memory and
+    every upload lies inside a timed interval.  ``host``: two wave buffers of pinned
+    host memory.  Wave w is pushed (and processed: max_pending_leaves = the wave)
+    while wave w + 1 uploads on a copy stream into the other device wave buffer; an
+    interval ends when both are done.  Between intervals (untimed) the device
+    generator writes wave w + 2 and it is copied to the host buffer wave w used --
+    the stand-in for snapshots that are already in host memory.  The first wave's
+    upload is timed on its own; the last interval holds hapod_result and the read
+    back of the root's modes and sigma."""
+    import torch
+
+    parent, leaves, cols = c3_tree(wl)
+    dtype = H.DTYPE[precision]
+    device = torch.device("cuda", torch.cuda.current_device())
+    W = wl["wave"]
+    gen = make_generator(H, wl, dtype, device, 2 * W)
+    eps = wl["eps_rel"] * math.sqrt(fro2)
+    cstream = torch.cuda.Stream(device)
+    waves = list(range(0, len(leaves), W))
+
+    def stage(wi):  # untimed: generate wave wi into device buffers (wi % 2), copy to host buffers (wi % 2)
+        w0 = waves[wi]
+        views = {}
+        with torch.cuda.stream(stream):
+            for i in range(w0, min(len(leaves), w0 + W)):
+                views[i] = gen.gen(i, (i - w0) + W * (wi % 2), stream)
+                host[wi % 2][i - w0][:views[i].shape[0]].copy_(views[i], non_blocking=True)
+                views[i].fill_(float("nan"))  # only the upload brings the snapshots back
+        stream.synchronize()
+        return views
+
+    def upload(wi, views):
+        """Wave wi's uploads on the copy stream, fed by a host thread in chunks of
+        E2E_CHUNK bytes with at most two in flight: the copy engine's queue stays
+        short, so the library's own small uploads (job tables) are not queued behind
+        32 GiB of snapshots.  Returns (thread, event list); the last event marks the end."""
+        w0 = waves[wi]
+        cstream.wait_stream(stream)
+        done = []
+
+        def pump():
+            with torch.cuda.stream(cstream):
+                inflight = []
+                for i in range(w0, min(len(leaves), w0 + W)):
+                    src = host[wi % 2][i - w0][:views[i].shape[0]].reshape(-1)
+                    dst = views[i].reshape(-1)
+                    step_ = E2E_CHUNK // src.element_size()
+                    for a in range(0, src.numel(), step_):
+                        dst[a:a + step_].copy_(src[a:a + step_], non_blocking=True)
+                        ev = torch.cuda.Event()
+                        ev.record(cstream)
+                        inflight.append(ev)
+                        if len(inflight) > 2:
+                            inflight.pop(0).synchronize()
+                done.extend(inflight[-1:])
+
+        th = threading.Thread(target=pump)
+        th.start()
+        return th, done
+
+    def step():
+        ctx = H.hapod_create(parent, cols, eps, wl["omega"], wl["n"], precision, stream=stream,
+                             max_pending_leaves=W, flags=0)
+        ms, d2h, st = 0.0, 0, -1
+        views = {0: stage(0)}
+        if len(waves) > 1:
+            views[1] = stage(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        th, evs = upload(0, views[0])
+        th.join()
+        for ev in evs:
+            stream.wait_event(ev)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+        for wi in range(len(waves)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            th, nxt = upload(wi + 1, views[wi + 1]) if wi + 1 < len(waves) else (None, [])
+            for i, v in views[wi].items():
+                H.hapod_push(ctx, leaves[i], v.t())
+            if wi + 1 == len(waves):
+                s_, U, st = H.hapod_result(ctx, device=device)
+                st = int(st)
+                Uh = U.cpu()
+                d2h = Uh.numel() * Uh.element_size() + s_.numel() * 8
+            if th is not None:
+                th.join()
+            for ev in nxt:
+                stream.wait_event(ev)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            del views[wi]
+            if wi + 2 < len(waves):
+                views[wi + 2] = stage(wi + 2)
+        H.hapod_destroy(ctx)
+        return ms, d2h, st
+
+    for _ in range(warmup):
+        step()
+    dist_ctx.barrier()
+    tot, d2h, st = 0.0, 0, -1
+    for _ in range(steps):
+        ms, d2h, st = step()
+        tot += ms
+    dist_ctx.barrier()
+    es = 4 if dtype == torch.float32 else 8
+    res = {"ms": dist_ctx.max(tot / steps), "h2d_bytes": sum(cols) * wl["n"] * es, "d2h_bytes": d2h, "status": st}
+    del gen
+    torch.cuda.empty_cache()
+    return res
 
 def _rank_summary(parent, nodes):
     return {"max_inner_k": max([st_["k"] for a, st_ in enumerate(nodes) if st_["level"] > 1 and parent[a] >= 0]
@@ -890,8 +1021,8 @@ def main():
     host = None
     if not args.no_e2e:
         try:
-            host = [torch.empty((C3["cols"], C3["n"]), dtype=torch.float32, pin_memory=True)
-                    for _ in range(C3["wave"])]
+            host = [[torch.empty((C3["cols"], C3["n"]), dtype=torch.float32, pin_memory=True)
+                     for _ in range(C3["wave"])] for _ in range(2)]
         except (RuntimeError, MemoryError) as ex:
             host = str(ex)[:120]
 
@@ -905,12 +1036,16 @@ def main():
     e2e = None
     if not args.no_e2e:
         if isinstance(host, list):
-            r = run_waves(H, H.HAPOD_MIXED_FX3, C3, fro2, args.steps, 1, stream, dist_ctx, host=host)
+            r = run_waves_e2e(H, H.HAPOD_MIXED_FX3, C3, fro2, args.steps, 1, stream, dist_ctx, host)
             e2e = {"value": total_c3 / (r["ms"] / 1e3), "unit": UNIT, "h2d_bytes_per_step": r["h2d_bytes"],
                    "d2h_bytes_per_step": r["d2h_bytes"], "ms_per_step": r["ms"], "form": head_key,
-                   "steps": args.steps, "note": "per wave: uploads of the 16 leaves from pinned host memory on a copy "
-                                               "stream, each push waiting for its leaf, then the wave's processing; "
-                                               "the root's modes and sigma read back"}
+                   "steps": args.steps, "status": r["status"],
+                   "note": "snapshots from pinned host memory (device wave buffers NaN-filled after their copy "
+                           "to the host, so only the uploads restore them), two wave buffers: wave w + 1 (16 leaves, "
+                           "32 GiB) uploads on a copy stream, fed in 64 MiB commands by a host thread, while wave w "
+                           "is pushed and processed, each interval ending when both are done; the first upload "
+                           "timed alone; generating the next wave on the device and copying it to the host between "
+                           "intervals is untimed; the root's modes and sigma read back"}
         else:
             e2e = {"value": None, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
                    "note": f"pinned host buffers unavailable: {host}"}
