@@ -48,7 +48,6 @@ import statistics
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -275,9 +274,6 @@ def c3_fro2(H, wl, device, stream):
     return tot
 
 
-E2E_CHUNK = 64 << 20  # bytes per upload command in the end-to-end leg
-
-
 def run_waves(H, precision, wl, fro2, steps, warmup, stream, dist_ctx, host=None, batch=None, copy_streams=1):
     """The headline HAPOD: per wave, generate its leaves (untimed), then push them
     (timed).  With ``host`` (pinned host buffers, one wave), the generated leaves are
@@ -419,34 +415,17 @@ def run_waves_e2e(H, precision, wl, fro2, steps, warmup, stream, dist_ctx, host)
         stream.synchronize()
         return views
 
-    def upload(wi, views):
-        """Wave wi's uploads on the copy stream, fed by a host thread in chunks of
-        E2E_CHUNK bytes with at most two in flight: the copy engine's queue stays
-        short, so the library's own small uploads (job tables) are not queued behind
-        32 GiB of snapshots.  Returns (thread, event list); the last event marks the end."""
+    def upload(wi, views):  # on the copy stream, after `stream`'s work so far; one event per leaf
         w0 = waves[wi]
         cstream.wait_stream(stream)
-        done = []
-
-        def pump():
-            with torch.cuda.stream(cstream):
-                inflight = []
-                for i in range(w0, min(len(leaves), w0 + W)):
-                    src = host[wi % 2][i - w0][:views[i].shape[0]].reshape(-1)
-                    dst = views[i].reshape(-1)
-                    step_ = E2E_CHUNK // src.element_size()
-                    for a in range(0, src.numel(), step_):
-                        dst[a:a + step_].copy_(src[a:a + step_], non_blocking=True)
-                        ev = torch.cuda.Event()
-                        ev.record(cstream)
-                        inflight.append(ev)
-                        if len(inflight) > 2:
-                            inflight.pop(0).synchronize()
-                done.extend(inflight[-1:])
-
-        th = threading.Thread(target=pump)
-        th.start()
-        return th, done
+        evs = []
+        with torch.cuda.stream(cstream):
+            for i in range(w0, min(len(leaves), w0 + W)):
+                views[i].copy_(host[wi % 2][i - w0][:views[i].shape[0]], non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(cstream)
+                evs.append(ev)
+        return evs
 
     def step():
         ctx = H.hapod_create(parent, cols, eps, wl["omega"], wl["n"], precision, stream=stream,
@@ -457,8 +436,7 @@ def run_waves_e2e(H, precision, wl, fro2, steps, warmup, stream, dist_ctx, host)
             views[1] = stage(1)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        th, evs = upload(0, views[0])
-        th.join()
+        evs = upload(0, views[0])
         for ev in evs:
             stream.wait_event(ev)
         e1.record(stream)
@@ -467,7 +445,7 @@ def run_waves_e2e(H, precision, wl, fro2, steps, warmup, stream, dist_ctx, host)
         for wi in range(len(waves)):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            th, nxt = upload(wi + 1, views[wi + 1]) if wi + 1 < len(waves) else (None, [])
+            nxt = upload(wi + 1, views[wi + 1]) if wi + 1 < len(waves) else []
             for i, v in views[wi].items():
                 H.hapod_push(ctx, leaves[i], v.t())
             if wi + 1 == len(waves):
@@ -475,8 +453,6 @@ def run_waves_e2e(H, precision, wl, fro2, steps, warmup, stream, dist_ctx, host)
                 st = int(st)
                 Uh = U.cpu()
                 d2h = Uh.numel() * Uh.element_size() + s_.numel() * 8
-            if th is not None:
-                th.join()
             for ev in nxt:
                 stream.wait_event(ev)
             e1.record(stream)
@@ -1042,7 +1018,7 @@ def main():
                    "steps": args.steps, "status": r["status"],
                    "note": "snapshots from pinned host memory (device wave buffers NaN-filled after their copy "
                            "to the host, so only the uploads restore them), two wave buffers: wave w + 1 (16 leaves, "
-                           "32 GiB) uploads on a copy stream, fed in 64 MiB commands by a host thread, while wave w "
+                           "32 GiB) uploads on a copy stream while wave w "
                            "is pushed and processed, each interval ending when both are done; the first upload "
                            "timed alone; generating the next wave on the device and copying it to the host between "
                            "intervals is untimed; the root's modes and sigma read back"}

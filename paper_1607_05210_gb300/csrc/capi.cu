@@ -98,6 +98,7 @@ struct Prof {
 
 struct Env {
   Prof* prof = nullptr;
+  HostStage* stage = nullptr;  // contexts: staged uploads (see HostStage)
   int* err_dev = nullptr;  // bounded-wait error flag of the tensor-core kernels (per batch)
   int dev = 0;
   cudaStream_t s = nullptr;
@@ -152,7 +153,7 @@ struct Env {
   T* upload(const std::vector<T>& v, const char* what) {
     T* d = static_cast<T*>(alloc(sizeof(T) * std::max<size_t>(1, v.size()), what));
     if (!d) return nullptr;
-    if (!v.empty() && !cuda(cudaMemcpyAsync(d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, s), what)) {
+    if (!v.empty() && !cuda(staged_upload(stage, d, v.data(), sizeof(T) * v.size(), s), what)) {
       release(d);
       return nullptr;
     }
@@ -178,6 +179,36 @@ bool init_err_flag(Env& env, int* err) {
   if (budget <= 0) return true;
   return env.cuda(cudaMemcpyAsync(err + 1, &budget, sizeof(int), cudaMemcpyHostToDevice, env.s), "set wait budget");
 }
+
+__global__ void staged_copy_kernel(uint4* __restrict__ dst, const uint4* __restrict__ src, size_t n16,
+                                   uint8_t* __restrict__ dtail, const uint8_t* __restrict__ stail, int ntail) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+  if (blockIdx.x == 0 && (int)threadIdx.x < ntail) dtail[threadIdx.x] = stail[threadIdx.x];
+}
+
+}  // namespace
+
+cudaError_t hapod::staged_upload(HostStage* st, void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) return cudaSuccess;
+  if (!st || !st->base || bytes > st->cap || (reinterpret_cast<uintptr_t>(dst) & 15))
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+  if (st->used + bytes > st->cap) {  // every earlier copy kernel has read its bytes once s is idle
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    st->used = 0;
+  }
+  uint8_t* h = st->base + st->used;
+  memcpy(h, src, bytes);
+  st->used += (bytes + 15) & ~size_t(15);
+  const size_t n16 = bytes / 16;
+  const unsigned blocks = (unsigned)std::min<size_t>(64, n16 / 256 + 1);
+  staged_copy_kernel<<<blocks, 256, 0, s>>>(static_cast<uint4*>(dst), reinterpret_cast<const uint4*>(h), n16,
+                                            static_cast<uint8_t*>(dst) + n16 * 16, h + n16 * 16, (int)(bytes % 16));
+  return cudaGetLastError();
+}
+
+namespace {
 
 bool init_env(Env& env, void* stream) {
   env.s = static_cast<cudaStream_t>(stream);
@@ -876,7 +907,7 @@ bool step_eig(Env& env, int precision, std::vector<Work*>& ws, NodeResult* res_d
   bool ok = jobs_d && sync_d;
   cudaEvent_t t0 = env.tic();
   ok = ok && env.cuda(launch_eig(eig_mode(precision), jobs.data(), jobs_d, (int)jobs.size(), max_m, kMaxSweeps,
-                                 sync_d, env.err_dev, env.s),
+                                 sync_d, env.err_dev, env.s, env.stage),
                       "eigensolver launch");
   env.toc(t0, 1, 1, 0.0, 0.0);
   env.release(jobs_d);
@@ -1170,8 +1201,11 @@ struct NodeRT {
   int64_t pcol = -1;
 };
 
+constexpr size_t kStageBytes = (size_t)8 << 20;  // pinned staging arena of a context
+
 struct hapod_ctx {
   Env env;
+  HostStage stage;
   Prof* prof = nullptr;
   int64_t n = 0;
   int64_t ldn = 0;  // leading dimension of library-owned node buffers (n rounded up to 32)
@@ -1551,6 +1585,15 @@ hapod_status hapod_create(const hapod_tree* tree, const hapod_tol* tol, int64_t 
     delete c;
     return st;
   }
+  // staging arena for the job tables (without it uploads use cudaMemcpyAsync)
+  void* stage = nullptr;
+  if (cudaHostAlloc(&stage, kStageBytes, cudaHostAllocMapped | cudaHostAllocPortable) == cudaSuccess) {
+    c->stage.base = static_cast<uint8_t*>(stage);
+    c->stage.cap = kStageBytes;
+    c->env.stage = &c->stage;
+  } else {
+    cudaGetLastError();
+  }
   *out = c;
   return HAPOD_OK;
 }
@@ -1673,6 +1716,7 @@ void hapod_destroy(hapod_ctx* c) {
   }
   env.release(c->result);
   cudaStreamSynchronize(env.s);
+  if (c->stage.base) cudaFreeHost(c->stage.base);
   delete c->prof;
   delete c;
 }

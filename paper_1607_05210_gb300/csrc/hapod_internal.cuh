@@ -323,8 +323,20 @@ constexpr int kEigDF = 2;  // double-float rotations (FP32 pairs), FP64 eigenvec
 // Cooperative launches over the jobs, several CTAs per job.  jobs_host is completed
 // (cta0, ncta, sync) and copied to jobs_dev (njobs entries); sync_dev: njobs entries.
 // err: the bounded-wait flag block (err[1] = debug wait budget) or null.
+// Pinned, mapped host arena for the small host-to-device uploads of job tables: the
+// bytes are staged here and copied by a kernel instead of a copy engine, so they never
+// queue behind large transfers the caller runs on other streams (snapshot uploads).
+// Bump-allocated; once full, the stream is synchronised and the arena reused.
+struct HostStage {
+  uint8_t* base = nullptr;
+  size_t cap = 0;
+  size_t used = 0;
+};
+// dst (device) <- src (host), bytes; through `st` when it is set and dst is 16-byte
+// aligned, else a plain cudaMemcpyAsync.
+cudaError_t staged_upload(HostStage* st, void* dst, const void* src, size_t bytes, cudaStream_t s);
 cudaError_t launch_eig(int mode, EigJob* jobs_host, EigJob* jobs_dev, int njobs, int max_m, int max_sweeps,
-                       EigSync* sync_dev, const int* err, cudaStream_t s);
+                       EigSync* sync_dev, const int* err, cudaStream_t s, HostStage* stage = nullptr);
 constexpr int kEigMaxM = 13000;  // dynamic shared memory bound of the eigensolver
 
 // C (M x N, ldc) = A (M x K, lda) B (K x N, ldb), column-major FP64 (right vectors).

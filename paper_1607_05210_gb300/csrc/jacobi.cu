@@ -490,7 +490,7 @@ size_t eig_smem_bytes(int m) { return (size_t)std::max(m, 1) * sizeof(double); }
 // Per-job CTA counts: one warp per Jacobi pair (m / 8 CTAs of 4 warps, at most 128),
 // scaled down to what the GPU keeps resident; jobs beyond that go to further launches.
 cudaError_t launch_eig(int mode, EigJob* jobs_host, EigJob* jobs_dev, int njobs, int max_m, int max_sweeps,
-                       EigSync* sync_dev, const int* err, cudaStream_t s) {
+                       EigSync* sync_dev, const int* err, cudaStream_t s, HostStage* stage) {
   if (njobs <= 0) return cudaSuccess;
   const void* fn = mode == kEigF32  ? (const void*)eig_coop_kernel<float>
                    : mode == kEigDF ? (const void*)eig_coop_kernel<DF>
@@ -539,7 +539,7 @@ cudaError_t launch_eig(int mode, EigJob* jobs_host, EigJob* jobs_dev, int njobs,
         t += jobs_host[j].ncta;
       }
     }
-    e = cudaMemcpyAsync(jobs_dev + j0, jobs_host + j0, sizeof(EigJob) * (size_t)(j1 - j0), cudaMemcpyHostToDevice, s);
+    e = staged_upload(stage, jobs_dev + j0, jobs_host + j0, sizeof(EigJob) * (size_t)(j1 - j0), s);
     if (e != cudaSuccess) return e;
     const EigJob* jd = jobs_dev + j0;
     int nj = j1 - j0;
