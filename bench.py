@@ -993,14 +993,26 @@ def main():
     total_c3 = C3["leaves"] * C3["cols"] * world
     forms = {}
 
-    # pinned host buffers for one wave (end-to-end leg), before device work
+    # pinned host buffers for two waves (end-to-end leg), before device work; every
+    # rank runs the leg only if every rank got its buffers (the leg has barriers)
     host = None
     if not args.no_e2e:
+        need = 2 * C3["wave"] * C3["cols"] * C3["n"] * 4 * dist_ctx.world
         try:
-            host = [[torch.empty((C3["cols"], C3["n"]), dtype=torch.float32, pin_memory=True)
-                     for _ in range(C3["wave"])] for _ in range(2)]
-        except (RuntimeError, MemoryError) as ex:
-            host = str(ex)[:120]
+            phys = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES")
+        except (ValueError, OSError, AttributeError):
+            phys = 0
+        if dist_ctx.world > 1 and phys and need > phys // 2:
+            host = (f"skipped: {dist_ctx.world} rank(s) x {need // dist_ctx.world >> 30} GiB of pinned host memory "
+                    f"exceed half of the host's {phys >> 30} GiB")
+        else:
+            try:
+                host = [[torch.empty((C3["cols"], C3["n"]), dtype=torch.float32, pin_memory=True)
+                         for _ in range(C3["wave"])] for _ in range(2)]
+            except (RuntimeError, MemoryError) as ex:
+                host = str(ex)[:120]
+        if dist_ctx.max(0.0 if isinstance(host, list) else 1.0) > 0.0 and isinstance(host, list):
+            host = "pinned host buffers unavailable on another rank"
 
     fro2 = c3_fro2(H, C3, device, stream)
     autotune = {} if args.no_autotune else run_autotune(H, device)
