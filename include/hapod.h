@@ -158,7 +158,11 @@ typedef struct {
 /*
  * hapod_create -- validate the tree, compute levels, |S~_a| and eps(a)
  * (Thm. cor:hapod_bound) and return a context bound to `stream` and the current
- * device.  n_rows is the snapshot length n (dim V).  No device compute.
+ * device.  n_rows is the snapshot length n (dim V).  No device compute.  The
+ * context keeps an 8 MiB pinned, device-mapped host buffer through which its small
+ * job tables reach the device by a copy kernel (so they never wait behind large
+ * transfers the caller queues on other streams); without it (the allocation
+ * failed) they are copied with cudaMemcpyAsync.  hapod_destroy frees it.
  * Errors: INVALID (null pointers, n_rows < 1, eps < 0, omega outside [0, 1],
  * unknown precision), TREE, CUDA, OOM.  *out is NULL on error.
  */
